@@ -1,0 +1,416 @@
+#!/usr/bin/env python3
+"""Benchmark of the connected-components hot path on GB300.
+
+One step = one full computation (root selection by exact max degree, init,
+edge pass, flatten to min-id labels) on each graph of the workload, through
+the C ABI (cc_run), with the edge lists resident in HBM. The default workload
+is the pair of single graphs R-MAT scale 24 / edge factor 16 (2^24 vertices,
+2^28 edges, scrambled ids) and the 8192 x 8192 grid with each 4-neighbour edge
+kept with p = 0.9 (~120.8M edges).
+
+Prints ONE JSON line (rank 0): GTEPS over the timed steps, the roofline of the
+edge-pass kernel against the measured HBM copy bandwidth, the end-to-end rate
+through cc_run_host with pinned host buffers (copies inside the timed region),
+the CPU oracle's rate on a bounded sample of the same workload, clocks sampled
+during the run, and the number of kernels launched.
+
+With --gpus N under torchrun every rank runs its own replica (the path does
+not shard across GPUs; no collective is on the data path); the time is the
+max over ranks and the value counts the edges of all ranks.
+
+--impl reference times the CPU oracle as it stands on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# Launch configuration the benchmark times (and the full-size tests check):
+# f = R of Eq. 1 with the exact maximum-degree vertex, min-id labels.
+BENCH_OPTIONS = dict(mode=1, root_select=0, label_space=0)
+
+WORKLOADS = {
+    "rmat24+grid8192": ["rmat24_ef16", "grid8192x8192_p0.9"],
+    "rmat24": ["rmat24_ef16"],
+    "grid8192": ["grid8192x8192_p0.9"],
+    "rmat28": ["rmat28_ef16"],
+    "rmat16": ["rmat16_ef16"],
+}
+
+EDGE_PASS_BYTES_PER_EDGE = 8  # one streamed read of the (u, v) pair
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat24+grid8192")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-fraction", type=float, default=1 / 8,
+                   help="share of each graph's edges in the CPU oracle sample")
+    return p.parse_args(argv)
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2507_03695_gb300", "csrc")
+    for name in ("cc_device.cuh", "cc_kernels.cu"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per edge-pass launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"edge_pass_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_sha()
+    with open(path) as f:
+        for line in f:
+            if line.startswith("traffic_per_launch:"):
+                parts = dict(kv.split("=") for kv in line.split(":", 1)[1].split())
+                if parts.get("source_sha") == src:
+                    return {k: float(v) for k, v in parts.items() if k != "source_sha"}
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling in the background."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.tmp.read().splitlines():
+            cols = [c.strip() for c in line.split(",")]
+            if len(cols) < 9:
+                continue
+            try:
+                sm.append(float(cols[1]))
+                smax.append(float(cols[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, cols[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.tmp.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def replica_summary(elapsed_ms_local: float, edges_per_step: int, steps: int, world: int, max_fn):
+    """Whole-job rate of N independent replicas: the timed region is the
+    slowest rank's, and every rank processed edges_per_step per step.
+    Returns (max elapsed ms, GTEPS)."""
+    elapsed_ms = max_fn(float(elapsed_ms_local))
+    return elapsed_ms, world * edges_per_step * steps / (elapsed_ms * 1e-3) / 1e9
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_sample(host_graphs, fraction: float):
+    """The oracle as it stands (one host core) on the first `fraction` of each
+    graph's edges, with each graph's full vertex count."""
+    import oracle
+    edges_done, t = 0, 0.0
+    for n, e in host_graphs:
+        k = max(1, int(len(e) * fraction))
+        sample = e[:k]
+        t0 = time.perf_counter()
+        oracle.min_labels(n, sample)
+        t += time.perf_counter() - t0
+        edges_done += k
+    return edges_done, t
+
+
+# --------------------------------------------------------------- reference
+
+def run_reference(args):
+    """The CPU oracle as it stands, on a bounded prefix of each graph's edges
+    (full vertex counts); the prefix shrinks so the whole run stays within
+    about two minutes."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import graphgen
+    names = WORKLOADS[args.workload]
+
+    def prefix(frac):
+        out = []
+        for nm in names:
+            w = graphgen.WORKLOADS[nm]
+            if w.kind == "rmat":
+                k = max(1, int(w.n_edges * frac))
+                out.append((w.n_vertices, graphgen.rmat(w.scale, w.n_edges, w.seed, w.scramble, 0, k)))
+            else:
+                full = w.host_edges()
+                out.append((w.n_vertices, full[: max(1, int(len(full) * frac))].copy()))
+        return out
+
+    frac = 1 / 16
+    graphs = prefix(frac)
+    _, t_cal = cpu_oracle_sample(graphs, 1.0)  # calibration (also the first warm-up)
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    if t_cal > budget:
+        frac = max(1 / 1024, frac * budget / t_cal)
+        graphs = prefix(frac)
+    for _ in range(max(0, args.warmup - 1)):
+        cpu_oracle_sample(graphs, 1.0)
+    t_total, e_total = 0.0, 0
+    for _ in range(args.steps):
+        e_done, t = cpu_oracle_sample(graphs, 1.0)
+        t_total += t
+        e_total += e_done
+    value = e_total / t_total / 1e9
+    per_step = e_total // max(args.steps, 1)
+    sample = (f"first {frac:.4g} of each graph's edges ({per_step} edges per step) with full vertex "
+              f"counts; one host core")
+    line = {
+        "impl": "reference", "metric": "GTEPS", "value": value, "unit": "GTEPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_total / max(args.steps, 1) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": {"workload": args.workload, "graphs": names, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import graphgen
+    import paper_2507_03695_gb300 as cc
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    names = WORKLOADS[args.workload]
+    ws = [graphgen.WORKLOADS[nm] for nm in names]
+    graphs = []
+    for w in ws:
+        e = w.device_edges()
+        graphs.append((w, e, int(e.shape[0])))
+    torch.cuda.synchronize()
+    E_total = sum(E for _, _, E in graphs)
+    n_total = sum(w.n_vertices for w, _, _ in graphs)
+
+    handles = [cc.Graph(w.n_vertices, **BENCH_OPTIONS, timing=1) for w, _, _ in graphs]
+    labels = [torch.empty(w.n_vertices, dtype=torch.int32, device=dev) for w, _, _ in graphs]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for h, (w, e, E), L in zip(handles, graphs, labels):
+            cc.cc_run(h.h, e, E, L, stream)
+
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = None
+    sampler = ClockSampler(gpu_id)
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    for h in handles:
+        h.sync()
+        cc.cc_phase_times_total(h.h)  # discard warm-up timings
+    launches0 = cc.cc_kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = cc.cc_kernel_launches() - launches0
+    clocks = sampler.stop()
+    elapsed_ms, value = replica_summary(ev0.elapsed_time(ev1), E_total, args.steps, world, max_over_ranks)
+    for h in handles:
+        h.sync()
+
+    # per-phase device times over the timed region
+    phase_ms = []
+    for h in handles:
+        tot, runs = cc.cc_phase_times_total(h.h)
+        phase_ms.append([x / max(runs, 1) for x in tot])
+    edge_ms = [p[2] for p in phase_ms]
+    edge_bytes = [EDGE_PASS_BYTES_PER_EDGE * E for _, _, E in graphs]
+    achieved = sum(edge_bytes) / (sum(edge_ms) * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = profiled_traffic(args.workload)
+
+    ms_per_step = elapsed_ms / args.steps
+    path_bytes = sum(8 * E + 12 * w.n_vertices + 8 * E + 4 * w.n_vertices for w, _, E in graphs)
+
+    # ---------------- end to end: host buffers through cc_run_host
+    e2e = None
+    if not args.no_e2e:
+        host_e = [torch.empty(e.shape, dtype=torch.int32, pin_memory=True) for _, e, _ in graphs]
+        for h_e, (_, e, _) in zip(host_e, graphs):
+            h_e.copy_(e)
+        host_L = [torch.empty(w.n_vertices, dtype=torch.int32, pin_memory=True) for w, _, _ in graphs]
+        e2e_handles = [cc.Graph(w.n_vertices, E, **BENCH_OPTIONS) for w, _, E in graphs]
+
+        def e2e_step():
+            for h, h_e, h_l, (_, _, E) in zip(e2e_handles, host_e, host_L, graphs):
+                cc.cc_run_host(h.h, h_e, E, h_l, stream)
+
+        for _ in range(max(1, min(args.warmup, 3))):
+            e2e_step()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k_e2e = max(1, min(args.steps, 10))
+        for _ in range(k_e2e):
+            e2e_step()
+        torch.cuda.synchronize()
+        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        barrier()
+        # the host labels must equal the device-resident run's labels
+        for h_l, L in zip(host_L, labels):
+            if not torch.equal(h_l, L.cpu()):
+                raise RuntimeError("cc_run_host labels differ from cc_run labels")
+        e2e = {"value": world * E_total * k_e2e / t_e2e / 1e9, "unit": "GTEPS",
+               "h2d_bytes_per_step": int(sum(8 * E for _, _, E in graphs)),
+               "d2h_bytes_per_step": int(sum(4 * w.n_vertices for w, _, _ in graphs)),
+               "steps": k_e2e, "api": "cc_run_host (pinned host buffers)"}
+        for h in e2e_handles:
+            h.close()
+        del host_e, host_L
+
+    # ---------------- CPU baseline: the oracle on a bounded sample (rank 0, N=1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        host_graphs = []
+        for w, e, E in graphs:
+            k = max(1, int(E * args.cpu_fraction))
+            host_graphs.append((w.n_vertices, e[:k].cpu().numpy().view(np.uint32)))
+        e_done, t_cpu = cpu_oracle_sample(host_graphs, 1.0)
+        cpu = {"value": e_done / t_cpu / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": f"first {args.cpu_fraction:g} of each graph's edges ({e_done} edges) with full "
+                         f"vertex counts; {t_cpu:.1f} s single-threaded"}
+
+    for h in handles:
+        h.close()
+    if rank == 0:
+        line = {
+            "metric": "GTEPS", "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic: seeded R-MAT (a,b,c,d)=(.57,.19,.19,.05) with scrambled ids and 4-neighbour "
+                    "grid kept with p=0.9, generated in HBM",
+            "config": {"workload": args.workload, "graphs": names,
+                       "n_vertices": [w.n_vertices for w, _, _ in graphs],
+                       "n_edges": [E for _, _, E in graphs],
+                       "root_function": "R of Eq. 1 (max-degree vertex planted as 0)",
+                       "root_select": "exact degree histogram", "labels": "min vertex id",
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (edge arrays of 2.1 GB and 0.97 GB vs 129 MB L2)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic["dram_bytes"] if traffic else None,
+                         "kernel": "edge pass (k_edge_pass_*)", "peak_source": peak_kind,
+                         "algorithmic_bytes": "8 B per edge per launch"},
+            "phases_ms": {nm: {"root_select": p[0], "init": p[1], "edge_pass": p[2], "flatten": p[3],
+                               "total": p[4]} for nm, p in zip(names, phase_ms)},
+            "path_algorithmic_gbs": path_bytes / (ms_per_step * 1e-3) / 1e9,
+            "gteps_without_root_select": E_total / (sum(p[4] - p[0] for p in phase_ms) * 1e-3) / 1e9,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": int(launches),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

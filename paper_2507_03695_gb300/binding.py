@@ -1,0 +1,298 @@
+"""ctypes binding of libcc.so (include/cc.h): same names as the C ABI,
+argument marshalling only. Every step of the computation runs in the CUDA
+kernels of the library; there is no Python or CPU fallback. If the library is
+not built, the first call raises.
+
+Buffers may be torch tensors (device pointers are taken with ``data_ptr()``;
+edge tensors of shape (E, 2) give ``n_edges = E``) or plain integers
+(addresses). ``stream=None`` means torch's current stream on the current
+device.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+_u64, _u32, _i32, _ptr = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_void_p
+CC_ROOT_AUTO = 0xFFFFFFFFFFFFFFFF
+
+# cc_status
+CC_OK = 0
+CC_ERR_INVALID_ARGUMENT = 1
+CC_ERR_TOO_LARGE = 2
+CC_ERR_OOM = 3
+CC_ERR_OUT_OF_RANGE = 4
+CC_ERR_TIMEOUT = 5
+CC_ERR_CUDA = 6
+CC_ERR_INTERNAL = 7
+CC_ERR_NOT_READY = 8
+# cc_root_mode / cc_root_select / cc_filter / cc_label_space
+CC_ROOT_IDENTITY, CC_ROOT_MAXDEG = 0, 1
+CC_ROOT_SELECT_EXACT, CC_ROOT_SELECT_SAMPLED = 0, 1
+CC_FILTER_AUTO, CC_FILTER_ON, CC_FILTER_OFF = 0, 1, 2
+CC_LABEL_MIN_ID, CC_LABEL_ROOT_VALUE = 0, 1
+
+
+class cc_options(ctypes.Structure):
+    _fields_ = [
+        ("mode", _i32), ("root_select", _i32), ("root_hint", _u64), ("filter", _i32),
+        ("label_space", _i32), ("block_size", _i32), ("edges_per_thread", _i32),
+        ("sample_stride", _i32), ("timing", _i32), ("hbm_budget_bytes", _u64),
+        ("reserved", _u64 * 4),
+    ]
+
+
+class CCError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {cc_status_string(status)}")
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libcc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"{_build.LIB} is not built: run paper_2507_03695_gb300.build.build() "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(_build.LIB)
+        P = ctypes.POINTER
+        sigs = {
+            "cc_options_init": (None, [P(cc_options)]),
+            "cc_create": (_i32, [_u64, _u64, P(cc_options), P(_ptr)]),
+            "cc_run": (_i32, [_ptr, _ptr, _u64, _ptr, _ptr]),
+            "cc_run_host": (_i32, [_ptr, _ptr, _u64, _ptr, _ptr]),
+            "cc_stream_insert": (_i32, [_ptr, _ptr, _u64, _ptr]),
+            "cc_labels": (_i32, [_ptr, _ptr, _ptr]),
+            "cc_connected": (_i32, [_ptr, _ptr, _u64, _ptr, _ptr]),
+            "cc_connected1": (_i32, [_ptr, _u64, _u64, P(ctypes.c_int)]),
+            "cc_num_components": (_i32, [_ptr, P(_u64)]),
+            "cc_root_vertex": (_i32, [_ptr, P(_u64)]),
+            "cc_sync": (_i32, [_ptr]),
+            "cc_phase_times": (_i32, [_ptr, P(ctypes.c_float)]),
+            "cc_phase_times_total": (_i32, [_ptr, P(ctypes.c_float), P(_u64)]),
+            "cc_kernel_launches": (_u64, []),
+            "cc_checkpoint_size": (_i32, [_ptr, P(_u64)]),
+            "cc_checkpoint": (_i32, [_ptr, _ptr, _u64]),
+            "cc_restore": (_i32, [_ptr, _ptr, _u64]),
+            "cc_device_bytes": (_i32, [_ptr, P(_u64)]),
+            "cc_destroy": (None, [_ptr]),
+            "cc_status_string": (ctypes.c_char_p, [_i32]),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int, what: str) -> None:
+    if st != CC_OK:
+        raise CCError(st, what)
+
+
+def _addr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if hasattr(x, "ctypes"):
+        return int(x.ctypes.data)
+    raise TypeError(f"cannot take the address of {type(x)!r}")
+
+
+def _count_pairs(x, n) -> int:
+    if n is not None:
+        return int(n)
+    if hasattr(x, "numel"):
+        return int(x.numel()) // 2
+    if hasattr(x, "size"):
+        return int(x.size) // 2
+    raise TypeError("pass the number of pairs explicitly")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def cc_status_string(status: int) -> str:
+    s = lib().cc_status_string(int(status))
+    return s.decode() if s else f"status {status}"
+
+
+def cc_options_init(**overrides) -> cc_options:
+    o = cc_options()
+    lib().cc_options_init(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise AttributeError(f"cc_options has no field {k!r}")
+        setattr(o, k, v)
+    return o
+
+
+def cc_create(n_vertices: int, n_edges_capacity: int = 0, opt: cc_options | None = None) -> int:
+    h = _ptr()
+    _check(lib().cc_create(n_vertices, n_edges_capacity, ctypes.byref(opt) if opt is not None else None,
+                           ctypes.byref(h)), "cc_create")
+    return h.value
+
+
+def cc_run(g: int, edges, n_edges: int | None = None, L_out=None, stream=None) -> None:
+    _check(lib().cc_run(g, _addr(edges), _count_pairs(edges, n_edges), _addr(L_out), _stream(stream)),
+           "cc_run")
+
+
+def cc_run_host(g: int, edges_host, n_edges: int | None = None, L_out_host=None, stream=None) -> None:
+    _check(lib().cc_run_host(g, _addr(edges_host), _count_pairs(edges_host, n_edges), _addr(L_out_host),
+                             _stream(stream)), "cc_run_host")
+
+
+def cc_stream_insert(g: int, edges, n_edges: int | None = None, stream=None) -> None:
+    _check(lib().cc_stream_insert(g, _addr(edges), _count_pairs(edges, n_edges), _stream(stream)),
+           "cc_stream_insert")
+
+
+def cc_labels(g: int, L_out, stream=None) -> None:
+    _check(lib().cc_labels(g, _addr(L_out), _stream(stream)), "cc_labels")
+
+
+def cc_connected(g: int, pairs, out, n_pairs: int | None = None, stream=None) -> None:
+    _check(lib().cc_connected(g, _addr(pairs), _count_pairs(pairs, n_pairs), _addr(out), _stream(stream)),
+           "cc_connected")
+
+
+def cc_connected1(g: int, u: int, v: int) -> bool:
+    r = ctypes.c_int(0)
+    _check(lib().cc_connected1(g, u, v, ctypes.byref(r)), "cc_connected1")
+    return bool(r.value)
+
+
+def cc_num_components(g: int) -> int:
+    r = _u64(0)
+    _check(lib().cc_num_components(g, ctypes.byref(r)), "cc_num_components")
+    return int(r.value)
+
+
+def cc_root_vertex(g: int) -> int:
+    r = _u64(0)
+    _check(lib().cc_root_vertex(g, ctypes.byref(r)), "cc_root_vertex")
+    return int(r.value)
+
+
+def cc_sync(g: int) -> None:
+    _check(lib().cc_sync(g), "cc_sync")
+
+
+def cc_sync_status(g: int) -> int:
+    """cc_sync returning the status instead of raising."""
+    return int(lib().cc_sync(g))
+
+
+def cc_phase_times(g: int) -> list[float]:
+    ms = (ctypes.c_float * 5)()
+    _check(lib().cc_phase_times(g, ms), "cc_phase_times")
+    return list(ms)
+
+
+def cc_phase_times_total(g: int) -> tuple[list[float], int]:
+    """Summed per-phase times since the previous call, and the run count."""
+    ms = (ctypes.c_float * 5)()
+    runs = _u64(0)
+    _check(lib().cc_phase_times_total(g, ms, ctypes.byref(runs)), "cc_phase_times_total")
+    return list(ms), int(runs.value)
+
+
+def cc_kernel_launches() -> int:
+    return int(lib().cc_kernel_launches())
+
+
+def cc_checkpoint_size(g: int) -> int:
+    r = _u64(0)
+    _check(lib().cc_checkpoint_size(g, ctypes.byref(r)), "cc_checkpoint_size")
+    return int(r.value)
+
+
+def cc_checkpoint(g: int) -> bytearray:
+    buf = bytearray(cc_checkpoint_size(g))
+    c = (ctypes.c_char * len(buf)).from_buffer(buf)
+    _check(lib().cc_checkpoint(g, ctypes.addressof(c), len(buf)), "cc_checkpoint")
+    return buf
+
+
+def cc_restore(g: int, buf) -> None:
+    b = bytes(buf)
+    _check(lib().cc_restore(g, b, len(b)), "cc_restore")
+
+
+def cc_device_bytes(g: int) -> int:
+    r = _u64(0)
+    _check(lib().cc_device_bytes(g, ctypes.byref(r)), "cc_device_bytes")
+    return int(r.value)
+
+
+def cc_destroy(g: int) -> None:
+    if g:
+        lib().cc_destroy(g)
+
+
+class Graph:
+    """Owning wrapper of a cc_graph handle (context manager)."""
+
+    def __init__(self, n_vertices: int, n_edges_capacity: int = 0, **options):
+        self.n = n_vertices
+        self.opt = cc_options_init(**options)
+        self.h = cc_create(n_vertices, n_edges_capacity, self.opt)
+
+    def run(self, edges, L_out=None, stream=None):
+        cc_run(self.h, edges, None, L_out, stream)
+        return L_out
+
+    def labels(self, L_out, stream=None):
+        cc_labels(self.h, L_out, stream)
+        return L_out
+
+    def insert(self, edges, stream=None):
+        cc_stream_insert(self.h, edges, None, stream)
+
+    def connected(self, pairs, out, stream=None):
+        cc_connected(self.h, pairs, out, None, stream)
+        return out
+
+    def num_components(self) -> int:
+        return cc_num_components(self.h)
+
+    def root_vertex(self) -> int:
+        return cc_root_vertex(self.h)
+
+    def sync(self):
+        cc_sync(self.h)
+
+    def close(self):
+        if self.h:
+            cc_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,613 @@
+// cc_api.cu - host runtime and C ABI (include/cc.h) of the connected-components
+// library: the handle, its device memory (parent array P, root-select
+// histogram, control block, staging), argument checks, HBM budget, error
+// reporting, checkpoints, and the order in which the kernels of
+// cc_kernels.cu are enqueued.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <array>
+#include <new>
+#include <vector>
+
+#include "../../include/cc.h"
+#include "cc_internal.h"
+
+using cc::Ctrl;
+
+struct cc_graph {
+  int device = 0;
+  uint64_t n = 0;
+  cc_options opt{};
+  bool rf = false;
+  uint32_t *P = nullptr;
+  void *cnt = nullptr;  // root-select histogram (uint32 or uint64 per vertex)
+  size_t cnt_bytes = 0;
+  Ctrl *ctrl = nullptr;
+  Ctrl *host_ctrl = nullptr;  // pinned mirror
+  uint32_t *staging = nullptr;
+  uint64_t capacity = 0;
+  uint32_t *label_dev = nullptr;  // cc_run_host labels
+  cudaStream_t last = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_ev = nullptr;
+  std::vector<std::array<cudaEvent_t, 5>> evsets;  // one set per timed run
+  size_t ev_used = 0;                                // sets filled since the last total
+  size_t ev_cur = 0;                                 // set of the current run
+  bool timed_run = false;
+  bool ncomp_fresh = false;
+  uint64_t owned = 0;
+};
+
+namespace {
+
+constexpr uint64_t kMaxVertices = 0x7FFFFFFFULL;
+constexpr uint64_t kHostChunk = 1ULL << 24;  // edges per cc_run_host copy chunk
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int d) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != d) {
+      prev = cur;
+      cudaSetDevice(d);
+    }
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+cc_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return CC_OK;
+  if (e == cudaErrorMemoryAllocation) return CC_ERR_OOM;
+  return CC_ERR_CUDA;
+}
+
+#define CC_TRY(expr)                          \
+  do {                                        \
+    cudaError_t e_ = (expr);                  \
+    if (e_ != cudaSuccess) return from_cuda(e_); \
+  } while (0)
+
+bool opts_valid(const cc_options &o) {
+  if (o.mode != CC_ROOT_IDENTITY && o.mode != CC_ROOT_MAXDEG) return false;
+  if (o.root_select != CC_ROOT_SELECT_EXACT && o.root_select != CC_ROOT_SELECT_SAMPLED) return false;
+  if (o.filter < CC_FILTER_AUTO || o.filter > CC_FILTER_OFF) return false;
+  if (o.label_space != CC_LABEL_MIN_ID && o.label_space != CC_LABEL_ROOT_VALUE) return false;
+  if (o.block_size != 0 && o.block_size != 128 && o.block_size != 256 && o.block_size != 512)
+    return false;
+  if (o.edges_per_thread != 0 && o.edges_per_thread != 2 && o.edges_per_thread != 4 &&
+      o.edges_per_thread != 8)
+    return false;
+  if (o.sample_stride < 0) return false;
+  for (uint64_t r : o.reserved)
+    if (r) return false;
+  return true;
+}
+
+int eff_filter(const cc_graph *g) {
+  if (g->opt.filter == CC_FILTER_ON) return 1;
+  if (g->opt.filter == CC_FILTER_OFF) return 0;
+  return 1;
+}
+int eff_ept(const cc_graph *g) { return g->opt.edges_per_thread ? g->opt.edges_per_thread : 4; }
+int eff_block(const cc_graph *g) { return g->opt.block_size ? g->opt.block_size : 256; }
+
+cudaError_t dev_alloc(cc_graph *g, void **p, size_t bytes) {
+  if (g->opt.hbm_budget_bytes && g->owned + bytes > g->opt.hbm_budget_bytes)
+    return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e == cudaSuccess) g->owned += bytes;
+  return e;
+}
+
+void dev_free(cc_graph *g, void *p, size_t bytes) {
+  if (p) {
+    cudaFree(p);
+    g->owned -= bytes;
+  }
+}
+
+size_t p_bytes(uint64_t n) { return (size_t)((n + 3) / 4 * 4) * sizeof(uint32_t); }
+
+// Copies the control block to the pinned mirror, waits, then turns and clears
+// the sticky device error bits.
+cc_status fetch_ctrl(cc_graph *g, cudaStream_t s) {
+  CC_TRY(cudaMemcpyAsync(g->host_ctrl, g->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  CC_TRY(cudaStreamSynchronize(s));
+  const uint32_t err = g->host_ctrl->err;
+  if (err) {
+    CC_TRY(cudaMemsetAsync(&g->ctrl->err, 0, sizeof(uint32_t), s));
+    CC_TRY(cudaStreamSynchronize(s));
+    if (err & cc::kErrInternal) return CC_ERR_INTERNAL;
+    if (err & cc::kErrTimeout) return CC_ERR_TIMEOUT;
+    if (err & cc::kErrRange) return CC_ERR_OUT_OF_RANGE;
+  }
+  return CC_OK;
+}
+
+bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
+// Root selection (f = R with no hint): degree histogram over all edges, or
+// over the sampled groups, then the argmax with ties to the smaller id.
+// Returns the init kernel's source of m.
+cc_status root_select(cc_graph *g, const uint32_t *edges, uint64_t n_edges, const cc::EdgeSpan &span,
+                      cudaStream_t s, int *m_src) {
+  const uint32_t n = (uint32_t)g->n;
+  const uint32_t stride = g->opt.sample_stride ? (uint32_t)g->opt.sample_stride : 16u;
+  const bool sampled = g->opt.root_select == CC_ROOT_SELECT_SAMPLED && stride > 1;
+  const bool wide = !sampled && n_edges >= (1ULL << 31);
+  const size_t need = (size_t)n * (wide ? 8 : 4);
+  if (g->cnt_bytes < need) {
+    CC_TRY(cudaStreamSynchronize(s));
+    dev_free(g, g->cnt, g->cnt_bytes);
+    g->cnt = nullptr;
+    g->cnt_bytes = 0;
+    CC_TRY(dev_alloc(g, &g->cnt, need));
+    g->cnt_bytes = need;
+  }
+  CC_TRY(cudaMemsetAsync(g->cnt, 0, need, s));
+  if (wide) {
+    CC_TRY(cudaMemsetAsync(&g->ctrl->maxcnt, 0, sizeof(unsigned long long), s));
+    CC_TRY(cudaMemsetAsync(&g->ctrl->m_sel, 0xFF, sizeof(uint32_t), s));
+    CC_TRY(cc::launch_degree_u64(span, (unsigned long long *)g->cnt, n, s));
+    CC_TRY(cc::launch_argmax_u64((const unsigned long long *)g->cnt, n, g->ctrl, s));
+    *m_src = cc::kMFromSelected;
+  } else {
+    CC_TRY(cudaMemsetAsync(&g->ctrl->maxkey, 0, sizeof(unsigned long long), s));
+    if (sampled)
+      CC_TRY(cc::launch_degree_sampled_u32(reinterpret_cast<const uint2 *>(edges), n_edges, 0, stride,
+                                           (uint32_t *)g->cnt, n, s));
+    else
+      CC_TRY(cc::launch_degree_u32(span, (uint32_t *)g->cnt, n, s));
+    CC_TRY(cc::launch_argmax_u32((const uint32_t *)g->cnt, n, g->ctrl, s));
+    *m_src = cc::kMFromPackedMax;
+  }
+  return CC_OK;
+}
+
+constexpr size_t kMaxEventSets = 4096;
+
+// Picks the event set of a timed run (false when timing is off or the pool is full).
+bool begin_timed_run(cc_graph *g) {
+  g->timed_run = false;
+  if (!g->opt.timing) return false;
+  if (g->ev_used == g->evsets.size()) {
+    if (g->evsets.size() >= kMaxEventSets) return false;
+    std::array<cudaEvent_t, 5> set{};
+    for (auto &ev : set)
+      if (cudaEventCreate(&ev) != cudaSuccess) return false;
+    g->evsets.push_back(set);
+  }
+  g->ev_cur = g->ev_used++;
+  g->timed_run = true;
+  return true;
+}
+
+void record(cc_graph *g, int i, cudaStream_t s) {
+  if (g->timed_run) cudaEventRecord(g->evsets[g->ev_cur][i], s);
+}
+
+// gmin <- m and ncomp <- 0 ahead of a flatten that is not preceded by init.
+__global__ void k_prep_flatten(Ctrl *ctrl) {
+  ctrl->gmin = ctrl->m;
+  ctrl->ncomp = 0ULL;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cc_options_init(cc_options *opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->mode = CC_ROOT_MAXDEG;
+  opt->root_select = CC_ROOT_SELECT_EXACT;
+  opt->root_hint = CC_ROOT_AUTO;
+  opt->filter = CC_FILTER_AUTO;
+  opt->label_space = CC_LABEL_MIN_ID;
+}
+
+const char *cc_status_string(cc_status s) {
+  switch (s) {
+    case CC_OK: return "CC_OK: success";
+    case CC_ERR_INVALID_ARGUMENT: return "CC_ERR_INVALID_ARGUMENT: invalid argument";
+    case CC_ERR_TOO_LARGE: return "CC_ERR_TOO_LARGE: size exceeds a limit";
+    case CC_ERR_OOM: return "CC_ERR_OOM: device memory or HBM budget exhausted";
+    case CC_ERR_OUT_OF_RANGE: return "CC_ERR_OUT_OF_RANGE: vertex id >= n_vertices";
+    case CC_ERR_TIMEOUT: return "CC_ERR_TIMEOUT: bounded wait expired";
+    case CC_ERR_CUDA: return "CC_ERR_CUDA: CUDA runtime error";
+    case CC_ERR_INTERNAL: return "CC_ERR_INTERNAL: internal invariant failed";
+    case CC_ERR_NOT_READY: return "CC_ERR_NOT_READY: request not complete";
+  }
+  return "unknown cc_status";
+}
+
+cc_status cc_create(uint64_t n_vertices, uint64_t n_edges_capacity, const cc_options *opt,
+                    cc_graph **out) {
+  if (!out) return CC_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  cc_options o;
+  if (opt)
+    o = *opt;
+  else
+    cc_options_init(&o);
+  if (!opts_valid(o)) return CC_ERR_INVALID_ARGUMENT;
+  if (n_vertices > kMaxVertices) return CC_ERR_TOO_LARGE;
+  if (o.mode == CC_ROOT_MAXDEG && o.root_hint != CC_ROOT_AUTO && o.root_hint >= n_vertices &&
+      n_vertices > 0)
+    return CC_ERR_INVALID_ARGUMENT;
+  if (n_edges_capacity > (1ULL << 40)) return CC_ERR_TOO_LARGE;
+
+  // host-side checks first: they need no device
+  const bool rf = o.mode == CC_ROOT_MAXDEG;
+  const size_t need = p_bytes(n_vertices) + (rf ? (size_t)n_vertices * 4 : 0) + sizeof(Ctrl) +
+                      (size_t)n_edges_capacity * 8;
+  if (o.hbm_budget_bytes && need > o.hbm_budget_bytes) return CC_ERR_OOM;
+
+  cc_graph *g = new (std::nothrow) cc_graph();
+  if (!g) return CC_ERR_OOM;
+  g->n = n_vertices;
+  g->opt = o;
+  g->rf = rf;
+  if (cudaGetDevice(&g->device) != cudaSuccess) {
+    delete g;
+    return CC_ERR_CUDA;
+  }
+  cc_status st = CC_OK;
+  cudaError_t e = cudaSuccess;
+  do {
+    size_t free_b = 0, total_b = 0;
+    if ((e = cudaMemGetInfo(&free_b, &total_b)) != cudaSuccess) break;
+    if (need > free_b) {
+      st = CC_ERR_OOM;
+      break;
+    }
+    if ((e = dev_alloc(g, (void **)&g->P, p_bytes(n_vertices))) != cudaSuccess) break;
+    if ((e = dev_alloc(g, (void **)&g->ctrl, sizeof(Ctrl))) != cudaSuccess) break;
+    if ((e = cudaMallocHost((void **)&g->host_ctrl, sizeof(Ctrl))) != cudaSuccess) break;
+    memset(g->host_ctrl, 0, sizeof(Ctrl));
+    if (g->rf && n_vertices) {
+      if ((e = dev_alloc(g, &g->cnt, (size_t)n_vertices * 4)) != cudaSuccess) break;
+      g->cnt_bytes = (size_t)n_vertices * 4;
+    }
+    if (n_edges_capacity) {
+      if ((e = dev_alloc(g, (void **)&g->staging, (size_t)n_edges_capacity * 8)) != cudaSuccess) break;
+      g->capacity = n_edges_capacity;
+    }
+    if ((e = cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking)) != cudaSuccess) break;
+    if ((e = cudaEventCreateWithFlags(&g->copy_ev, cudaEventDisableTiming)) != cudaSuccess) break;
+    if ((e = cudaMemset(g->ctrl, 0, sizeof(Ctrl))) != cudaSuccess) break;
+    // the edgeless graph: P_v = f(v) with m = hint (or 0)
+    const uint32_t hint =
+        (g->rf && o.root_hint != CC_ROOT_AUTO) ? (uint32_t)o.root_hint : 0u;
+    if ((e = cc::launch_init(g->rf, g->P, (uint32_t)n_vertices, g->ctrl, cc::kMFromHint, hint, 0)) !=
+        cudaSuccess)
+      break;
+    if ((e = cudaStreamSynchronize(0)) != cudaSuccess) break;
+    g->ncomp_fresh = false;
+  } while (0);
+  if (st == CC_OK && e != cudaSuccess) st = from_cuda(e);
+  if (st != CC_OK) {
+    cc_destroy(g);
+    return st;
+  }
+  *out = g;
+  return CC_OK;
+}
+
+void cc_destroy(cc_graph *g) {
+  if (!g) return;
+  DeviceGuard dg(g->device);
+  cudaDeviceSynchronize();
+  dev_free(g, g->P, p_bytes(g->n));
+  dev_free(g, g->cnt, g->cnt_bytes);
+  dev_free(g, g->ctrl, sizeof(Ctrl));
+  dev_free(g, g->staging, (size_t)g->capacity * 8);
+  dev_free(g, g->label_dev, (size_t)g->n * 4);
+  if (g->host_ctrl) cudaFreeHost(g->host_ctrl);
+  if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
+  if (g->copy_ev) cudaEventDestroy(g->copy_ev);
+  for (auto &set : g->evsets)
+    for (auto ev : set)
+      if (ev) cudaEventDestroy(ev);
+  delete g;
+}
+
+cc_status cc_run(cc_graph *g, const uint32_t *edges_dev, uint64_t n_edges, uint32_t *L_out_dev,
+                 cc_stream_t stream) {
+  if (!g) return CC_ERR_INVALID_ARGUMENT;
+  if (n_edges && (!edges_dev || !aligned(edges_dev, 8))) return CC_ERR_INVALID_ARGUMENT;
+  if (L_out_dev && !aligned(L_out_dev, 4)) return CC_ERR_INVALID_ARGUMENT;
+  DeviceGuard dg(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  g->last = s;
+  if (g->n == 0) return CC_OK;
+  const uint32_t n = (uint32_t)g->n;
+  const cc::EdgeSpan span = cc::split_edges(edges_dev, n_edges);
+  begin_timed_run(g);
+  record(g, 0, s);
+  int m_src = cc::kMFromHint;
+  uint32_t hint = 0;
+  if (g->rf) {
+    if (g->opt.root_hint != CC_ROOT_AUTO) {
+      hint = (uint32_t)g->opt.root_hint;
+    } else {
+      cc_status st = root_select(g, edges_dev, n_edges, span, s, &m_src);
+      if (st != CC_OK) return st;
+    }
+  }
+  record(g, 1, s);
+  CC_TRY(cc::launch_init(g->rf, g->P, n, g->ctrl, m_src, hint, s));
+  record(g, 2, s);
+  CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), span, g->P, n, g->ctrl,
+                              false, s));
+  record(g, 3, s);
+  CC_TRY(cc::launch_flatten(g->rf, g->opt.label_space, g->P, n, L_out_dev, g->ctrl, s));
+  record(g, 4, s);
+  g->ncomp_fresh = true;
+  return CC_OK;
+}
+
+cc_status cc_run_host(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges, uint32_t *L_out_host,
+                      cc_stream_t stream) {
+  if (!g) return CC_ERR_INVALID_ARGUMENT;
+  if (n_edges && !edges_host) return CC_ERR_INVALID_ARGUMENT;
+  if (n_edges > g->capacity) return CC_ERR_TOO_LARGE;
+  DeviceGuard dg(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  g->last = s;
+  if (g->n == 0) return CC_OK;
+  const uint32_t n = (uint32_t)g->n;
+  if (L_out_host && !g->label_dev) CC_TRY(dev_alloc(g, (void **)&g->label_dev, (size_t)n * 4));
+  const bool select = g->rf && g->opt.root_hint == CC_ROOT_AUTO;
+  const uint32_t stride = g->opt.sample_stride ? (uint32_t)g->opt.sample_stride : 16u;
+  const bool sampled = g->opt.root_select == CC_ROOT_SELECT_SAMPLED && stride > 1;
+  const bool wide = select && !sampled && n_edges >= (1ULL << 31);
+  int m_src = cc::kMFromHint;
+  const uint32_t hint = (g->rf && !select) ? (uint32_t)g->opt.root_hint : 0u;
+  if (select) {
+    const size_t need = (size_t)n * (wide ? 8 : 4);
+    if (g->cnt_bytes < need) {
+      CC_TRY(cudaStreamSynchronize(s));
+      dev_free(g, g->cnt, g->cnt_bytes);
+      g->cnt = nullptr;
+      g->cnt_bytes = 0;
+      CC_TRY(dev_alloc(g, &g->cnt, need));
+      g->cnt_bytes = need;
+    }
+    CC_TRY(cudaMemsetAsync(g->cnt, 0, need, s));
+    if (wide) {
+      CC_TRY(cudaMemsetAsync(&g->ctrl->maxcnt, 0, sizeof(unsigned long long), s));
+      CC_TRY(cudaMemsetAsync(&g->ctrl->m_sel, 0xFF, sizeof(uint32_t), s));
+      m_src = cc::kMFromSelected;
+    } else {
+      CC_TRY(cudaMemsetAsync(&g->ctrl->maxkey, 0, sizeof(unsigned long long), s));
+      m_src = cc::kMFromPackedMax;
+    }
+  } else {
+    CC_TRY(cc::launch_init(g->rf, g->P, n, g->ctrl, m_src, hint, s));
+  }
+  // the copy stream starts after everything already enqueued on s
+  CC_TRY(cudaEventRecord(g->copy_ev, s));
+  CC_TRY(cudaStreamWaitEvent(g->copy_stream, g->copy_ev, 0));
+  for (uint64_t off = 0; off < n_edges; off += kHostChunk) {
+    const uint64_t cnt = (n_edges - off) < kHostChunk ? (n_edges - off) : kHostChunk;
+    CC_TRY(cudaMemcpyAsync(g->staging + 2 * off, edges_host + 2 * off, cnt * 8, cudaMemcpyHostToDevice,
+                           g->copy_stream));
+    CC_TRY(cudaEventRecord(g->copy_ev, g->copy_stream));
+    CC_TRY(cudaStreamWaitEvent(s, g->copy_ev, 0));
+    const cc::EdgeSpan span = cc::split_edges(g->staging + 2 * off, cnt);
+    if (select) {
+      if (wide)
+        CC_TRY(cc::launch_degree_u64(span, (unsigned long long *)g->cnt, n, s));
+      else if (sampled)
+        CC_TRY(cc::launch_degree_sampled_u32(reinterpret_cast<const uint2 *>(g->staging + 2 * off), cnt,
+                                             off, stride, (uint32_t *)g->cnt, n, s));
+      else
+        CC_TRY(cc::launch_degree_u32(span, (uint32_t *)g->cnt, n, s));
+    } else {
+      CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), span, g->P, n, g->ctrl,
+                                  false, s));
+    }
+  }
+  if (select) {
+    if (wide)
+      CC_TRY(cc::launch_argmax_u64((const unsigned long long *)g->cnt, n, g->ctrl, s));
+    else
+      CC_TRY(cc::launch_argmax_u32((const uint32_t *)g->cnt, n, g->ctrl, s));
+    CC_TRY(cc::launch_init(g->rf, g->P, n, g->ctrl, m_src, hint, s));
+    const cc::EdgeSpan all = cc::split_edges(g->staging, n_edges);
+    CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), all, g->P, n, g->ctrl,
+                                false, s));
+  }
+  CC_TRY(cc::launch_flatten(g->rf, g->opt.label_space, g->P, n, L_out_host ? g->label_dev : nullptr,
+                            g->ctrl, s));
+  if (L_out_host)
+    CC_TRY(cudaMemcpyAsync(L_out_host, g->label_dev, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+  g->ncomp_fresh = true;
+  return fetch_ctrl(g, s);
+}
+
+cc_status cc_stream_insert(cc_graph *g, const uint32_t *edges_dev, uint64_t n_edges, cc_stream_t stream) {
+  if (!g) return CC_ERR_INVALID_ARGUMENT;
+  if (n_edges && (!edges_dev || !aligned(edges_dev, 8))) return CC_ERR_INVALID_ARGUMENT;
+  DeviceGuard dg(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  g->last = s;
+  if (g->n == 0 || n_edges == 0) return CC_OK;
+  const cc::EdgeSpan span = cc::split_edges(edges_dev, n_edges);
+  CC_TRY(cudaMemsetAsync(&g->ctrl->reject, 0, sizeof(uint32_t), s));
+  CC_TRY(cc::launch_validate(span, (uint32_t)g->n, g->ctrl, s));
+  CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), span, g->P,
+                              (uint32_t)g->n, g->ctrl, true, s));
+  g->ncomp_fresh = false;
+  return CC_OK;
+}
+
+cc_status cc_labels(cc_graph *g, uint32_t *L_out_dev, cc_stream_t stream) {
+  if (!g) return CC_ERR_INVALID_ARGUMENT;
+  if (!L_out_dev || !aligned(L_out_dev, 4)) return CC_ERR_INVALID_ARGUMENT;
+  DeviceGuard dg(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  g->last = s;
+  if (g->n == 0) return CC_OK;
+  k_prep_flatten<<<1, 1, 0, s>>>(g->ctrl); cc::note_launch();
+  CC_TRY(cudaGetLastError());
+  CC_TRY(cc::launch_flatten(g->rf, g->opt.label_space, g->P, (uint32_t)g->n, L_out_dev, g->ctrl, s));
+  g->ncomp_fresh = true;
+  return CC_OK;
+}
+
+cc_status cc_connected(cc_graph *g, const uint32_t *pairs_dev, uint64_t n_pairs, uint8_t *out_dev,
+                       cc_stream_t stream) {
+  if (!g) return CC_ERR_INVALID_ARGUMENT;
+  if (n_pairs && (!pairs_dev || !out_dev || !aligned(pairs_dev, 8))) return CC_ERR_INVALID_ARGUMENT;
+  DeviceGuard dg(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  g->last = s;
+  if (n_pairs == 0) return CC_OK;
+  CC_TRY(cc::launch_connected(g->rf, g->P, (uint32_t)g->n, reinterpret_cast<const uint2 *>(pairs_dev),
+                              n_pairs, out_dev, g->ctrl, s));
+  return CC_OK;
+}
+
+cc_status cc_connected1(cc_graph *g, uint64_t u, uint64_t v, int *out) {
+  if (!g || !out) return CC_ERR_INVALID_ARGUMENT;
+  if (u >= g->n || v >= g->n) return CC_ERR_OUT_OF_RANGE;
+  DeviceGuard dg(g->device);
+  cudaStream_t s = g->last;
+  g->host_ctrl->q_u = (uint32_t)u;
+  g->host_ctrl->q_v = (uint32_t)v;
+  CC_TRY(cudaMemcpyAsync(&g->ctrl->q_u, &g->host_ctrl->q_u, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+  CC_TRY(cudaMemsetAsync(&g->ctrl->q_out, 0, sizeof(uint32_t), s));
+  CC_TRY(cc::launch_connected(g->rf, g->P, (uint32_t)g->n, reinterpret_cast<const uint2 *>(&g->ctrl->q_u),
+                              1, reinterpret_cast<uint8_t *>(&g->ctrl->q_out), g->ctrl, s));
+  cc_status st = fetch_ctrl(g, s);
+  *out = (int)(g->host_ctrl->q_out & 0xFFu);
+  return st;
+}
+
+cc_status cc_num_components(cc_graph *g, uint64_t *out) {
+  if (!g || !out) return CC_ERR_INVALID_ARGUMENT;
+  DeviceGuard dg(g->device);
+  cudaStream_t s = g->last;
+  if (g->n == 0) {
+    *out = 0;
+    return CC_OK;
+  }
+  if (!g->ncomp_fresh) {
+    CC_TRY(cudaMemsetAsync(&g->ctrl->ncomp, 0, sizeof(unsigned long long), s));
+    CC_TRY(cc::launch_count_roots(g->rf, g->P, (uint32_t)g->n, g->ctrl, s));
+  }
+  cc_status st = fetch_ctrl(g, s);
+  *out = g->host_ctrl->ncomp;
+  if (st == CC_OK) g->ncomp_fresh = true;
+  return st;
+}
+
+cc_status cc_root_vertex(cc_graph *g, uint64_t *m) {
+  if (!g || !m) return CC_ERR_INVALID_ARGUMENT;
+  DeviceGuard dg(g->device);
+  cc_status st = fetch_ctrl(g, g->last);
+  *m = g->rf ? (uint64_t)g->host_ctrl->m : CC_ROOT_AUTO;
+  return st;
+}
+
+cc_status cc_sync(cc_graph *g) {
+  if (!g) return CC_ERR_INVALID_ARGUMENT;
+  DeviceGuard dg(g->device);
+  return fetch_ctrl(g, g->last);
+}
+
+cc_status cc_phase_times(cc_graph *g, float ms[5]) {
+  if (!g || !ms) return CC_ERR_INVALID_ARGUMENT;
+  if (!g->timed_run) return CC_ERR_INVALID_ARGUMENT;
+  DeviceGuard dg(g->device);
+  const auto &ev = g->evsets[g->ev_cur];
+  CC_TRY(cudaEventSynchronize(ev[4]));
+  for (int i = 0; i < 4; ++i) CC_TRY(cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]));
+  CC_TRY(cudaEventElapsedTime(&ms[4], ev[0], ev[4]));
+  return CC_OK;
+}
+
+cc_status cc_phase_times_total(cc_graph *g, float ms[5], uint64_t *runs) {
+  if (!g || !ms || !runs) return CC_ERR_INVALID_ARGUMENT;
+  DeviceGuard dg(g->device);
+  for (int i = 0; i < 5; ++i) ms[i] = 0.f;
+  for (size_t k = 0; k < g->ev_used; ++k) {
+    const auto &ev = g->evsets[k];
+    CC_TRY(cudaEventSynchronize(ev[4]));
+    for (int i = 0; i < 4; ++i) {
+      float t = 0.f;
+      CC_TRY(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+      ms[i] += t;
+    }
+    float t = 0.f;
+    CC_TRY(cudaEventElapsedTime(&t, ev[0], ev[4]));
+    ms[4] += t;
+  }
+  *runs = g->ev_used;
+  g->ev_used = 0;
+  g->timed_run = false;
+  return CC_OK;
+}
+
+uint64_t cc_kernel_launches(void) { return cc::launch_count(); }
+
+struct CkptHeader {
+  uint32_t magic;    // 'JTCC'
+  uint32_t version;  // 1
+  uint32_t mode;
+  uint32_t m;
+  uint64_t n;
+};
+static const uint32_t kCkptMagic = 0x4343544Au;
+
+cc_status cc_checkpoint_size(const cc_graph *g, uint64_t *bytes) {
+  if (!g || !bytes) return CC_ERR_INVALID_ARGUMENT;
+  *bytes = sizeof(CkptHeader) + g->n * 4;
+  return CC_OK;
+}
+
+cc_status cc_checkpoint(cc_graph *g, void *host_buf, uint64_t bytes) {
+  if (!g || !host_buf || bytes < sizeof(CkptHeader) + g->n * 4) return CC_ERR_INVALID_ARGUMENT;
+  DeviceGuard dg(g->device);
+  cudaStream_t s = g->last;
+  cc_status st = fetch_ctrl(g, s);
+  if (st != CC_OK) return st;
+  CkptHeader h{kCkptMagic, 1u, (uint32_t)g->opt.mode, g->host_ctrl->m, g->n};
+  memcpy(host_buf, &h, sizeof(h));
+  if (g->n) {
+    CC_TRY(cudaMemcpyAsync((char *)host_buf + sizeof(h), g->P, g->n * 4, cudaMemcpyDeviceToHost, s));
+    CC_TRY(cudaStreamSynchronize(s));
+  }
+  return CC_OK;
+}
+
+cc_status cc_restore(cc_graph *g, const void *host_buf, uint64_t bytes) {
+  if (!g || !host_buf || bytes < sizeof(CkptHeader)) return CC_ERR_INVALID_ARGUMENT;
+  CkptHeader h;
+  memcpy(&h, host_buf, sizeof(h));
+  if (h.magic != kCkptMagic || h.version != 1u || h.n != g->n || h.mode != (uint32_t)g->opt.mode ||
+      bytes < sizeof(h) + h.n * 4 || (h.n && h.m >= h.n))
+    return CC_ERR_INVALID_ARGUMENT;
+  DeviceGuard dg(g->device);
+  cudaStream_t s = g->last;
+  CC_TRY(cudaStreamSynchronize(s));
+  if (g->n) CC_TRY(cudaMemcpy(g->P, (const char *)host_buf + sizeof(h), g->n * 4, cudaMemcpyHostToDevice));
+  g->host_ctrl->m = h.m;
+  CC_TRY(cudaMemcpy(&g->ctrl->m, &g->host_ctrl->m, sizeof(uint32_t), cudaMemcpyHostToDevice));
+  g->ncomp_fresh = false;
+  return CC_OK;
+}
+
+cc_status cc_device_bytes(const cc_graph *g, uint64_t *bytes) {
+  if (!g || !bytes) return CC_ERR_INVALID_ARGUMENT;
+  *bytes = g->owned;
+  return CC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,193 @@
+// cc_device.cuh - device primitives of Root-Function JT union-find.
+//
+// The parent array P holds, for every vertex x, a root value: x is a root iff
+// P[x] == f(x); otherwise f^-1(P[x]) is an ancestor of x (Algorithm 3). Two
+// root functions are provided: f(v) = v (Algorithm 1) and f = R of Eq. 1
+// (R(m) = 0, R(v) = v + 1 otherwise) with its inverse from Eq. 2.
+//
+// Facts the kernels rely on (all follow from the hooking rule "the root of
+// larger f gets the smaller f as parent value"):
+//  * P values only decrease, and every non-root x has f(parent) < f(x), so
+//    every walk up the parents ends, and any value P[x] ever held names an
+//    ancestor of x for the rest of the run. A stale read of P is therefore
+//    still a correct (if older) ancestor, and two endpoints that ever showed
+//    the same P value are in the same tree.
+//  * The vertex of root value 0 (m under R, vertex 0 under the identity) can
+//    never be hooked, so reading 0 ends a root search at once.
+//  * Only roots are ever CAS targets; path splitting rewrites only non-roots,
+//    and always to an ancestor's value, so it never changes a component.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cc_internal.h"
+
+namespace cc {
+
+// f(v) = v (Algorithm 1; Algorithm 3 with the identity, Section IV).
+struct RootId {
+  static constexpr bool kRF = false;
+  __device__ __forceinline__ static RootId load(const Ctrl *) { return RootId{}; }
+  __device__ __forceinline__ uint32_t f(uint32_t x) const { return x; }
+  __device__ __forceinline__ uint32_t finv(uint32_t c) const { return c; }
+};
+
+// f = R (Eq. 1), f^-1 = R^-1 (Eq. 2).
+struct RootR {
+  static constexpr bool kRF = true;
+  uint32_t m;
+  __device__ __forceinline__ static RootR load(const Ctrl *ctrl) {
+    return RootR{*(const volatile uint32_t *)&ctrl->m};
+  }
+  __device__ __forceinline__ uint32_t f(uint32_t x) const { return x == m ? 0u : x + 1u; }
+  __device__ __forceinline__ uint32_t finv(uint32_t c) const { return c == 0u ? m : c - 1u; }
+};
+
+// ------------------------------------------------------------ memory access
+
+// L2 policy for data read exactly once (the edge stream): evict first, so the
+// parent array keeps the cache.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// 128-bit streaming load of two edges: non-coherent path, no L1 allocation.
+__device__ __forceinline__ uint4 ld_edges(const uint4 *a, uint64_t pol) {
+  uint4 r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+      : "l"(a), "l"(pol));
+  return r;
+}
+
+__device__ __forceinline__ uint2 ld_edge(const uint2 *a) {
+  uint2 r;
+  asm("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(a));
+  return r;
+}
+
+// Parent-array load. A weak load may be served from this SM's L1 and so be
+// stale; by the facts above a stale value is an older ancestor, which keeps
+// every search correct. (CAS results always come from L2.)
+__device__ __forceinline__ uint32_t ldP(const uint32_t *p) {
+  uint32_t r;
+  asm volatile("ld.global.u32 %0, [%1];" : "=r"(r) : "l"(p) : "memory");
+  return r;
+}
+
+__device__ __forceinline__ uint32_t ldP_strong(const uint32_t *p) {
+  uint32_t r;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(r) : "l"(p) : "memory");
+  return r;
+}
+
+__device__ __forceinline__ void stP(uint32_t *p, uint32_t v) {
+  asm volatile("st.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t *p) {
+  return *(const volatile uint32_t *)p;
+}
+
+__device__ __forceinline__ void set_err(Ctrl *ctrl, uint32_t bit) { atomicOr(&ctrl->err, bit); }
+
+// ------------------------------------------------------------------ searches
+
+// Root value of x, given px = a value P[x] has held. Walks with path splitting
+// (each visited non-root x gets its grandparent's value). The walk is at most
+// n steps because f strictly decreases along parents.
+template <class F>
+__device__ __forceinline__ uint32_t find_root_value(uint32_t *P, const F fn, uint32_t x, uint32_t px) {
+  while (px != fn.f(x)) {
+    if (px == 0u) return 0u;  // the value-0 vertex is a permanent root
+    const uint32_t w = fn.finv(px);
+    const uint32_t pw = ldP(P + w);
+    if (pw != px) stP(P + x, pw);  // w is not a root: split x past it
+    x = w;
+    px = pw;
+  }
+  return px;
+}
+
+// Same, without writes (queries that must not touch P).
+template <class F>
+__device__ __forceinline__ uint32_t find_root_value_ro(const uint32_t *P, const F fn, uint32_t x,
+                                                       uint32_t px) {
+  while (px != fn.f(x)) {
+    if (px == 0u) return 0u;
+    x = fn.finv(px);
+    px = ldP(P + x);
+  }
+  return px;
+}
+
+// One edge of the hooking pass (Algorithm 3): pu and pv are values P[u] and
+// P[v] have held. Repeats { find both roots; equal -> done; CAS the root of
+// larger f from f(root) to the other root's f } until a CAS succeeds. A
+// failed CAS returns the root's new parent value, and the search resumes from
+// that root (the current roots, not the original endpoints). Any moment at
+// which both sides show the same parent value proves a common tree and ends
+// the edge, which includes the case of both endpoints already holding 0.
+template <class F>
+__device__ __forceinline__ void unite(uint32_t *P, const F fn, uint32_t u, uint32_t pu, uint32_t v,
+                                      uint32_t pv) {
+  while (true) {
+    if (pu == pv) return;
+    while (pu != fn.f(u)) {
+      if (pu == 0u) {
+        u = fn.finv(0u);
+        break;
+      }
+      const uint32_t w = fn.finv(pu);
+      const uint32_t pw = ldP(P + w);
+      if (pw != pu) stP(P + u, pw);
+      u = w;
+      pu = pw;
+      if (pu == pv) return;
+    }
+    while (pv != fn.f(v)) {
+      if (pv == 0u) {
+        v = fn.finv(0u);
+        break;
+      }
+      const uint32_t w = fn.finv(pv);
+      const uint32_t pw = ldP(P + w);
+      if (pw != pv) stP(P + v, pw);
+      v = w;
+      pv = pw;
+      if (pu == pv) return;
+    }
+    if (pu == pv) return;  // same root
+    if (pu < pv) {
+      const uint32_t old = atomicCAS(P + v, pv, pu);
+      if (old == pv) return;
+      pv = old;  // v was hooked meanwhile: continue from v
+    } else {
+      const uint32_t old = atomicCAS(P + u, pu, pv);
+      if (old == pu) return;
+      pu = old;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- reductions
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    x = y > x ? y : x;
+  }
+  return x;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+  return x;
+}
+
+}  // namespace cc

@@ -1,0 +1,74 @@
+// cc_internal.h - state shared by the kernels and the host runtime of the
+// connected-components library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cc {
+
+// Device error bits (sticky until a synchronising call reports them).
+enum : uint32_t {
+  kErrRange = 1u,     // a vertex id >= n reached a kernel
+  kErrTimeout = 2u,   // a bounded wait expired
+  kErrInternal = 4u,  // an invariant failed (a root search longer than n)
+};
+
+// Where the init kernel takes the planted vertex m from.
+enum : int { kMFromHint = 0, kMFromPackedMax = 1, kMFromSelected = 2 };
+
+// Per-handle control block in device memory (one cache line or two).
+struct alignas(128) Ctrl {
+  unsigned long long maxkey;  // root select, u32 counts: (deg << 32) | ~v, atomicMax
+  unsigned long long maxcnt;  // root select, u64 counts: max degree
+  unsigned long long ncomp;   // roots counted by the last flatten / count pass
+  uint32_t m_sel;             // root select, u64 counts: smallest v with deg == maxcnt
+  uint32_t m;                 // planted vertex in use (written by init)
+  uint32_t gmin;              // smallest vertex of m's component (min-id labels, f = R)
+  uint32_t err;               // kErr* bits
+  uint32_t reject;            // the insert batch being applied failed validation
+  uint32_t q_u, q_v, q_out;   // cc_connected1 scratch
+  unsigned long long stats[4];  // optional edge-pass counters
+};
+
+// Label spaces (cc_label_space).
+enum : int { kLabelMinId = 0, kLabelRootValue = 1 };
+
+struct LaunchCfg {
+  int block = 256;
+  int grid = 0;
+};
+
+// Kernel launchers (cc_kernels.cu). Each returns cudaGetLastError().
+struct EdgeSpan {
+  const uint4 *quads = nullptr;  // 16-byte aligned body: 2 edges per uint4
+  uint64_t n_quads = 0;
+  const uint2 *head = nullptr;   // at most one edge before the aligned body
+  const uint2 *tail = nullptr;   // at most one edge after it
+};
+EdgeSpan split_edges(const uint32_t *edges, uint64_t n_edges);
+
+int num_sms();
+
+// Process-wide count of kernel launches issued by the library.
+void note_launch();
+unsigned long long launch_count();
+
+cudaError_t launch_init(bool rf, uint32_t *P, uint32_t n, Ctrl *ctrl, int m_src, uint32_t m_hint,
+                        cudaStream_t s);
+cudaError_t launch_degree_u32(const EdgeSpan &e, uint32_t *cnt, uint32_t n, cudaStream_t s);
+cudaError_t launch_degree_u64(const EdgeSpan &e, unsigned long long *cnt, uint32_t n, cudaStream_t s);
+cudaError_t launch_degree_sampled_u32(const uint2 *edges, uint64_t n_edges, uint64_t edge_base,
+                                      uint32_t stride, uint32_t *cnt, uint32_t n, cudaStream_t s);
+cudaError_t launch_argmax_u32(const uint32_t *cnt, uint32_t n, Ctrl *ctrl, cudaStream_t s);
+cudaError_t launch_argmax_u64(const unsigned long long *cnt, uint32_t n, Ctrl *ctrl, cudaStream_t s);
+cudaError_t launch_edge_pass(bool rf, int filter, int ept, int block, const EdgeSpan &e, uint32_t *P,
+                             uint32_t n, Ctrl *ctrl, bool check_reject, cudaStream_t s);
+cudaError_t launch_validate(const EdgeSpan &e, uint32_t n, Ctrl *ctrl, cudaStream_t s);
+cudaError_t launch_flatten(bool rf, int label_space, uint32_t *P, uint32_t n, uint32_t *L, Ctrl *ctrl,
+                           cudaStream_t s);
+cudaError_t launch_count_roots(bool rf, const uint32_t *P, uint32_t n, Ctrl *ctrl, cudaStream_t s);
+cudaError_t launch_connected(bool rf, uint32_t *P, uint32_t n, const uint2 *pairs, uint64_t n_pairs,
+                             uint8_t *out, Ctrl *ctrl, cudaStream_t s);
+
+}  // namespace cc

@@ -1,0 +1,627 @@
+// cc_kernels.cu - CUDA kernels of the connected-components hot path for
+// sm_103a and their launchers:
+//   root selection  degree histogram + argmax (Algorithm 4, max_degree())
+//   init            P_v = f(v)                 (Algorithm 3, initialisation)
+//   edge pass       one hooking pass           (Algorithm 3, hooking)
+//   min-id probe    smallest vertex of m's component (min-id labels under R)
+//   flatten         labels + compression       (Algorithm 3, pointer jumping)
+//   count, connected, validate                 (queries and insert checks)
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "cc_device.cuh"
+#include "cc_internal.h"
+
+namespace cc {
+
+namespace {
+
+int g_num_sms = 0;
+
+inline unsigned clamp_grid(uint64_t want, uint64_t cap) {
+  if (want == 0) want = 1;
+  return (unsigned)(want < cap ? want : cap);
+}
+
+inline uint64_t persistent_cap(const void *kernel, int block, size_t smem) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, smem) != cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  return (uint64_t)num_sms() * (uint64_t)occ;
+}
+
+// ------------------------------------------------------------------- init
+
+template <class F>
+__global__ void __launch_bounds__(256) k_init(uint32_t *__restrict__ P, uint32_t n, Ctrl *ctrl,
+                                              int m_src, uint32_t m_hint) {
+  uint32_t m = 0;
+  if (F::kRF) {
+    if (m_src == kMFromHint)
+      m = m_hint;
+    else if (m_src == kMFromPackedMax)
+      m = ~(uint32_t)(*(volatile unsigned long long *)&ctrl->maxkey);
+    else
+      m = *(volatile uint32_t *)&ctrl->m_sel;
+    if (m >= n) m = 0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctrl->m = m;
+    ctrl->gmin = m;
+    ctrl->ncomp = 0ULL;
+  }
+  const uint64_t n4 = n / 4u;
+  uint4 *P4 = reinterpret_cast<uint4 *>(P);
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n4;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t v = (uint32_t)(4 * i);
+    uint4 r;
+    if (F::kRF) {
+      r = make_uint4(v + 1u, v + 2u, v + 3u, v + 4u);
+      if (m - v < 4u) {
+        if (m == v) r.x = 0u;
+        if (m == v + 1u) r.y = 0u;
+        if (m == v + 2u) r.z = 0u;
+        if (m == v + 3u) r.w = 0u;
+      }
+    } else {
+      r = make_uint4(v, v + 1u, v + 2u, v + 3u);
+    }
+    P4[i] = r;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < (n & 3u)) {
+    const uint32_t v = (uint32_t)(4 * n4) + threadIdx.x;
+    P[v] = F::kRF ? (v == m ? 0u : v + 1u) : v;
+  }
+}
+
+// ------------------------------------------------------------ root select
+
+template <typename C>
+__device__ __forceinline__ void count_edge(C *cnt, uint32_t n, uint32_t a, uint32_t b) {
+  if (a < n) atomicAdd(cnt + a, (C)1);
+  if (b < n) atomicAdd(cnt + b, (C)1);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_degree(const uint4 *__restrict__ e4, uint64_t n_quads,
+                                                const uint2 *head, const uint2 *tail,
+                                                C *__restrict__ cnt, uint32_t n) {
+  const uint64_t pol = policy_evict_first();
+  const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (t == 0 && head) {
+    uint2 e = ld_edge(head);
+    count_edge(cnt, n, e.x, e.y);
+  }
+  if (t == 1 % T && tail) {
+    uint2 e = ld_edge(tail);
+    count_edge(cnt, n, e.x, e.y);
+  }
+  for (uint64_t q = t; q < n_quads; q += T) {
+    const uint4 e = ld_edges(e4 + q, pol);
+    count_edge(cnt, n, e.x, e.y);
+    count_edge(cnt, n, e.z, e.w);
+  }
+}
+
+// Sampled histogram: edge i (global index edge_base + i) is counted iff
+// ((edge_base + i) / 1024) % stride == 0.
+__global__ void __launch_bounds__(256) k_degree_sampled(const uint2 *__restrict__ e, uint64_t n_edges,
+                                                        uint64_t edge_base, uint32_t stride,
+                                                        uint32_t *__restrict__ cnt, uint32_t n) {
+  const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+  // iterate over sampled global indices only
+  const uint64_t g_first = edge_base / 1024u;
+  const uint64_t g_last = (edge_base + n_edges + 1023u) / 1024u;  // exclusive
+  uint64_t g0 = (g_first + stride - 1) / stride * stride;          // first sampled group
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;; k += T) {
+    const uint64_t grp = g0 + (k / 1024u) * stride;
+    if (grp >= g_last) break;
+    const uint64_t gi = grp * 1024u + (k % 1024u);
+    if (gi < edge_base || gi >= edge_base + n_edges) continue;
+    const uint2 x = ld_edge(e + (gi - edge_base));
+    count_edge(cnt, n, x.x, x.y);
+  }
+}
+
+__device__ __forceinline__ void block_max_u64(unsigned long long key, unsigned long long *target) {
+  __shared__ unsigned long long sm[32];
+  key = warp_max_u64(key);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sm[wid] = key;
+  __syncthreads();
+  if (wid == 0) {
+    key = lane < (int)(blockDim.x >> 5) ? sm[lane] : 0ULL;
+    key = warp_max_u64(key);
+    if (lane == 0 && key) atomicMax(target, key);
+  }
+}
+
+// Packed key (deg << 32) | ~v: the largest key has the largest degree and,
+// among equal degrees, the smallest v.
+__global__ void __launch_bounds__(256) k_argmax_u32(const uint32_t *__restrict__ cnt, uint32_t n,
+                                                    Ctrl *ctrl) {
+  unsigned long long best = 0;
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+       v += (uint64_t)gridDim.x * blockDim.x) {
+    const unsigned long long key = ((unsigned long long)cnt[v] << 32) | (uint32_t)~(uint32_t)v;
+    best = key > best ? key : best;
+  }
+  block_max_u64(best, &ctrl->maxkey);
+}
+
+__global__ void __launch_bounds__(256) k_maxcnt_u64(const unsigned long long *__restrict__ cnt,
+                                                    uint32_t n, Ctrl *ctrl) {
+  unsigned long long best = 0;
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+       v += (uint64_t)gridDim.x * blockDim.x)
+    best = cnt[v] > best ? cnt[v] : best;
+  block_max_u64(best, &ctrl->maxcnt);
+}
+
+__global__ void __launch_bounds__(256) k_minid_u64(const unsigned long long *__restrict__ cnt,
+                                                   uint32_t n, Ctrl *ctrl) {
+  const unsigned long long mx = *(volatile unsigned long long *)&ctrl->maxcnt;
+  uint32_t best = 0xFFFFFFFFu;
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+       v += (uint64_t)gridDim.x * blockDim.x)
+    if (cnt[v] == mx && (uint32_t)v < best) best = (uint32_t)v;
+  best = __reduce_min_sync(0xFFFFFFFFu, best);
+  if ((threadIdx.x & 31) == 0 && best != 0xFFFFFFFFu) atomicMin(&ctrl->m_sel, best);
+}
+
+// --------------------------------------------------------------- edge pass
+
+// Range check of one edge; an out-of-range id flags the error and turns the
+// edge into the no-op self-loop (0, 0).
+__device__ __forceinline__ void guard(uint32_t &a, uint32_t &b, uint32_t n, Ctrl *ctrl) {
+  if (a >= n || b >= n) {
+    set_err(ctrl, kErrRange);
+    a = 0u;
+    b = 0u;
+  }
+}
+
+template <class F>
+__device__ __forceinline__ void single_edge(uint32_t *P, const F fn, const uint2 *e, uint32_t n,
+                                            Ctrl *ctrl) {
+  uint2 x = ld_edge(e);
+  guard(x.x, x.y, n, ctrl);
+  unite(P, fn, x.x, ldP(P + x.x), x.y, ldP(P + x.y));
+}
+
+// Direct form: each thread takes Q 128-bit loads (2Q edges) per iteration,
+// issues all 4Q parent loads together, then resolves its edges one by one.
+template <class F, int Q>
+__global__ void __launch_bounds__(256) k_edge_pass_direct(const uint4 *__restrict__ e4,
+                                                          uint64_t n_quads, const uint2 *head,
+                                                          const uint2 *tail, uint32_t *P,
+                                                          uint32_t n, Ctrl *ctrl, int check_reject) {
+  if (check_reject && ld_volatile_u32(&ctrl->reject)) return;
+  const F fn = F::load(ctrl);
+  const uint64_t pol = policy_evict_first();
+  const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (t == 0 && head) single_edge(P, fn, head, n, ctrl);
+  if (t == 1 % T && tail) single_edge(P, fn, tail, n, ctrl);
+  for (uint64_t base = t; base < n_quads; base += T * Q) {
+    uint4 e[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      const uint64_t q = base + (uint64_t)j * T;
+      e[j] = q < n_quads ? ld_edges(e4 + q, pol) : make_uint4(0u, 0u, 0u, 0u);
+    }
+    uint32_t p[4 * Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      guard(e[j].x, e[j].y, n, ctrl);
+      guard(e[j].z, e[j].w, n, ctrl);
+      p[4 * j + 0] = ldP(P + e[j].x);
+      p[4 * j + 1] = ldP(P + e[j].y);
+      p[4 * j + 2] = ldP(P + e[j].z);
+      p[4 * j + 3] = ldP(P + e[j].w);
+    }
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      unite(P, fn, e[j].x, p[4 * j + 0], e[j].y, p[4 * j + 1]);
+      unite(P, fn, e[j].z, p[4 * j + 2], e[j].w, p[4 * j + 3]);
+    }
+  }
+}
+
+// Filtered form: after the parent loads, edges whose endpoints hold the same
+// parent value are dropped (this covers both endpoints already at root value
+// 0); the survivors of the warp are appended to a per-warp ring in shared
+// memory, and whenever 32 are queued the whole warp resolves them together,
+// one per lane, so root searches run in dense warps. At most 31 survivors are
+// carried from one append to the next, so a 64-entry ring suffices.
+constexpr int kRing = 64;
+
+template <class F, int Q>
+__global__ void __launch_bounds__(256) k_edge_pass_filtered(const uint4 *__restrict__ e4,
+                                                            uint64_t n_quads, const uint2 *head,
+                                                            const uint2 *tail, uint32_t *P,
+                                                            uint32_t n, Ctrl *ctrl,
+                                                            int check_reject) {
+  extern __shared__ uint32_t ring_smem[];
+  if (check_reject && ld_volatile_u32(&ctrl->reject)) return;
+  const F fn = F::load(ctrl);
+  const uint64_t pol = policy_evict_first();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t *ru = ring_smem + wid * (4 * kRing);
+  uint32_t *rpu = ru + kRing, *rv = ru + 2 * kRing, *rpv = ru + 3 * kRing;
+  const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (t == 0 && head) single_edge(P, fn, head, n, ctrl);
+  if (t == 1 % T && tail) single_edge(P, fn, tail, n, ctrl);
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  uint32_t qh = 0, qt = 0;  // ring head and tail (warp-uniform)
+  // the loop trip count must be warp-uniform: iterate on the warp's first lane
+  const uint64_t warp_t0 = t - (uint64_t)lane;
+  for (uint64_t wbase = warp_t0; wbase < n_quads; wbase += T * Q) {
+    const uint64_t base = wbase + (uint64_t)lane;
+    uint4 e[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      const uint64_t q = base + (uint64_t)j * T;
+      e[j] = q < n_quads ? ld_edges(e4 + q, pol) : make_uint4(0u, 0u, 0u, 0u);
+    }
+    uint32_t p[4 * Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      guard(e[j].x, e[j].y, n, ctrl);
+      guard(e[j].z, e[j].w, n, ctrl);
+      p[4 * j + 0] = ldP(P + e[j].x);
+      p[4 * j + 1] = ldP(P + e[j].y);
+      p[4 * j + 2] = ldP(P + e[j].z);
+      p[4 * j + 3] = ldP(P + e[j].w);
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * Q; ++k) {
+      const uint32_t a = (k & 1) ? e[k >> 1].z : e[k >> 1].x;
+      const uint32_t b = (k & 1) ? e[k >> 1].w : e[k >> 1].y;
+      const uint32_t pa = p[2 * k], pb = p[2 * k + 1];
+      const bool keep = pa != pb;
+      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+      if (keep) {
+        const uint32_t slot = (qt + __popc(bal & lt_mask)) & (kRing - 1);
+        ru[slot] = a;
+        rpu[slot] = pa;
+        rv[slot] = b;
+        rpv[slot] = pb;
+      }
+      qt += __popc(bal);
+      if (qt - qh >= 32u) {
+        __syncwarp();
+        const uint32_t slot = (qh + lane) & (kRing - 1);
+        const uint32_t sa = ru[slot], spa = rpu[slot], sb = rv[slot], spb = rpv[slot];
+        __syncwarp();
+        unite(P, fn, sa, spa, sb, spb);
+        qh += 32u;
+      }
+    }
+  }
+  // drain
+  __syncwarp();
+  if (lane < (int)(qt - qh)) {
+    const uint32_t slot = (qh + lane) & (kRing - 1);
+    unite(P, fn, ru[slot], rpu[slot], rv[slot], rpv[slot]);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_validate(const uint4 *__restrict__ e4, uint64_t n_quads,
+                                                  const uint2 *head, const uint2 *tail, uint32_t n,
+                                                  Ctrl *ctrl) {
+  const uint64_t pol = policy_evict_first();
+  const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  bool bad = false;
+  if (t == 0 && head) {
+    uint2 e = ld_edge(head);
+    bad |= e.x >= n || e.y >= n;
+  }
+  if (t == 1 % T && tail) {
+    uint2 e = ld_edge(tail);
+    bad |= e.x >= n || e.y >= n;
+  }
+  for (uint64_t q = t; q < n_quads; q += T) {
+    const uint4 e = ld_edges(e4 + q, pol);
+    bad |= (e.x >= n) | (e.y >= n) | (e.z >= n) | (e.w >= n);
+  }
+  if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) {
+    atomicOr(&ctrl->reject, 1u);
+    set_err(ctrl, kErrRange);
+  }
+}
+
+// ------------------------------------------------------------------ flatten
+
+// Smallest vertex whose root value is 0 under R. Its answer is at most m, so
+// only [0, m) is scanned, in chunks of increasing id; a block stops as soon as
+// its next chunk starts above the best candidate found so far.
+__global__ void __launch_bounds__(256) k_gmin_probe(uint32_t *P, uint32_t n, Ctrl *ctrl) {
+  const RootR fn = RootR::load(ctrl);
+  const uint32_t m = fn.m;
+  __shared__ uint32_t s_stop;
+  const uint64_t chunk = 4ull * blockDim.x;
+  for (uint64_t c = blockIdx.x;; c += gridDim.x) {
+    const uint64_t start = c * chunk;
+    if (threadIdx.x == 0) s_stop = (start >= m) || (start > ld_volatile_u32(&ctrl->gmin));
+    __syncthreads();
+    const bool stop = s_stop;
+    __syncthreads();
+    if (stop) return;
+    uint32_t best = 0xFFFFFFFFu;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint64_t v = start + (uint64_t)k * blockDim.x + threadIdx.x;
+      if (v < m && v < best) {
+        const uint32_t pv = ldP(P + v);
+        if (find_root_value(P, fn, (uint32_t)v, pv) == 0u) best = (uint32_t)v;
+      }
+    }
+    best = __reduce_min_sync(0xFFFFFFFFu, best);
+    if ((threadIdx.x & 31) == 0 && best != 0xFFFFFFFFu) atomicMin(&ctrl->gmin, best);
+  }
+}
+
+// Pointer jumping (Algorithm 3): every vertex finds its root value c with
+// path splitting, stores c into P (compression; roots are never written) and,
+// when L is given, writes its label: the root value, the root's id (min-id
+// labels under f = id), or under f = R the root's id for c != 0 and the
+// smallest vertex of m's component for c == 0. Roots are counted.
+template <class F, int LABEL>
+__global__ void __launch_bounds__(256) k_flatten(uint32_t *P, uint32_t n, uint32_t *__restrict__ L,
+                                                 Ctrl *ctrl) {
+  const F fn = F::load(ctrl);
+  uint32_t gmin = 0;
+  if (F::kRF && LABEL == kLabelMinId) gmin = ld_volatile_u32(&ctrl->gmin);
+  unsigned long long roots = 0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t v = (uint32_t)i;
+    const uint32_t pv = ldP(P + v);
+    uint32_t c;
+    if (pv == fn.f(v)) {
+      c = pv;
+      ++roots;
+    } else {
+      c = find_root_value(P, fn, v, pv);
+      if (c != pv) stP(P + v, c);
+    }
+    if (L) {
+      uint32_t lab;
+      if (LABEL == kLabelRootValue)
+        lab = c;
+      else if (F::kRF)
+        lab = c == 0u ? gmin : c - 1u;
+      else
+        lab = c;
+      __stcs(L + v, lab);
+    }
+  }
+  roots = warp_sum_u64(roots);
+  if ((threadIdx.x & 31) == 0 && roots) atomicAdd(&ctrl->ncomp, roots);
+}
+
+template <class F>
+__global__ void __launch_bounds__(256) k_count_roots(const uint32_t *__restrict__ P, uint32_t n,
+                                                     Ctrl *ctrl) {
+  const F fn = F::load(ctrl);
+  unsigned long long roots = 0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    roots += (P[i] == fn.f((uint32_t)i));
+  roots = warp_sum_u64(roots);
+  if ((threadIdx.x & 31) == 0 && roots) atomicAdd(&ctrl->ncomp, roots);
+}
+
+template <class F>
+__global__ void __launch_bounds__(256) k_connected(uint32_t *P, uint32_t n,
+                                                   const uint2 *__restrict__ pairs, uint64_t n_pairs,
+                                                   uint8_t *__restrict__ out, Ctrl *ctrl) {
+  const F fn = F::load(ctrl);
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_pairs;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint2 q = ld_edge(pairs + i);
+    uint8_t r = 0;
+    if (q.x >= n || q.y >= n) {
+      set_err(ctrl, kErrRange);
+    } else {
+      const uint32_t cu = find_root_value(P, fn, q.x, ldP(P + q.x));
+      const uint32_t cv = find_root_value(P, fn, q.y, ldP(P + q.y));
+      r = cu == cv;
+    }
+    out[i] = r;
+  }
+}
+
+}  // namespace
+
+// ======================================================================= host
+
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+}
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
+    g_num_sms = v;
+  }
+  return g_num_sms;
+}
+
+EdgeSpan split_edges(const uint32_t *edges, uint64_t n_edges) {
+  EdgeSpan s;
+  if (n_edges == 0) return s;
+  const uint2 *e2 = reinterpret_cast<const uint2 *>(edges);
+  uint64_t h = ((uintptr_t)edges & 15u) ? 1u : 0u;
+  if (h) s.head = e2;
+  const uint64_t body = n_edges - h;
+  s.n_quads = body / 2u;
+  s.quads = reinterpret_cast<const uint4 *>(e2 + h);
+  if (body & 1u) s.tail = e2 + h + 2u * s.n_quads;
+  return s;
+}
+
+cudaError_t launch_init(bool rf, uint32_t *P, uint32_t n, Ctrl *ctrl, int m_src, uint32_t m_hint,
+                        cudaStream_t s) {
+  const uint64_t work = n / 4u + 1u;
+  if (rf) {
+    const unsigned g = clamp_grid((work + 255) / 256, persistent_cap((const void *)k_init<RootR>, 256, 0));
+    k_init<RootR><<<g, 256, 0, s>>>(P, n, ctrl, m_src, m_hint); note_launch();
+  } else {
+    const unsigned g = clamp_grid((work + 255) / 256, persistent_cap((const void *)k_init<RootId>, 256, 0));
+    k_init<RootId><<<g, 256, 0, s>>>(P, n, ctrl, m_src, m_hint); note_launch();
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_degree_u32(const EdgeSpan &e, uint32_t *cnt, uint32_t n, cudaStream_t s) {
+  const unsigned g = clamp_grid((e.n_quads + 255) / 256,
+                                persistent_cap((const void *)k_degree<uint32_t>, 256, 0));
+  k_degree<uint32_t><<<g, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, cnt, n); note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_degree_u64(const EdgeSpan &e, unsigned long long *cnt, uint32_t n, cudaStream_t s) {
+  const unsigned g = clamp_grid((e.n_quads + 255) / 256,
+                                persistent_cap((const void *)k_degree<unsigned long long>, 256, 0));
+  k_degree<unsigned long long><<<g, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, cnt, n); note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_degree_sampled_u32(const uint2 *edges, uint64_t n_edges, uint64_t edge_base,
+                                      uint32_t stride, uint32_t *cnt, uint32_t n, cudaStream_t s) {
+  if (n_edges == 0) return cudaSuccess;
+  if (stride == 0) stride = 1;
+  const uint64_t groups = (n_edges + 1023) / 1024 / stride + 2;
+  const unsigned g = clamp_grid(groups * 1024 / 256,
+                                persistent_cap((const void *)k_degree_sampled, 256, 0));
+  k_degree_sampled<<<g, 256, 0, s>>>(edges, n_edges, edge_base, stride, cnt, n); note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_argmax_u32(const uint32_t *cnt, uint32_t n, Ctrl *ctrl, cudaStream_t s) {
+  const unsigned g = clamp_grid(((uint64_t)n + 255) / 256, persistent_cap((const void *)k_argmax_u32, 256, 0));
+  k_argmax_u32<<<g, 256, 0, s>>>(cnt, n, ctrl); note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_argmax_u64(const unsigned long long *cnt, uint32_t n, Ctrl *ctrl, cudaStream_t s) {
+  const unsigned g = clamp_grid(((uint64_t)n + 255) / 256, persistent_cap((const void *)k_maxcnt_u64, 256, 0));
+  k_maxcnt_u64<<<g, 256, 0, s>>>(cnt, n, ctrl); note_launch();
+  k_minid_u64<<<g, 256, 0, s>>>(cnt, n, ctrl); note_launch();
+  return cudaGetLastError();
+}
+
+namespace {
+template <class F, int Q>
+cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, uint32_t n, Ctrl *ctrl,
+                        bool check_reject, cudaStream_t s) {
+  const uint64_t per_block = (uint64_t)block * Q;
+  if (filter) {
+    const size_t smem = (size_t)(block / 32) * 4 * kRing * sizeof(uint32_t);
+    const void *k = (const void *)k_edge_pass_filtered<F, Q>;
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const unsigned g = clamp_grid((e.n_quads + per_block - 1) / per_block, persistent_cap(k, block, smem));
+    k_edge_pass_filtered<F, Q><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
+                                                      check_reject ? 1 : 0); note_launch();
+  } else {
+    const void *k = (const void *)k_edge_pass_direct<F, Q>;
+    const unsigned g = clamp_grid((e.n_quads + per_block - 1) / per_block, persistent_cap(k, block, 0));
+    k_edge_pass_direct<F, Q><<<g, block, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
+                                                 check_reject ? 1 : 0); note_launch();
+  }
+  return cudaGetLastError();
+}
+
+template <class F>
+cudaError_t edge_pass_f(int filter, int ept, int block, const EdgeSpan &e, uint32_t *P, uint32_t n,
+                        Ctrl *ctrl, bool check_reject, cudaStream_t s) {
+  switch (ept) {
+    case 2: return edge_pass_q<F, 1>(filter, block, e, P, n, ctrl, check_reject, s);
+    case 8: return edge_pass_q<F, 4>(filter, block, e, P, n, ctrl, check_reject, s);
+    default: return edge_pass_q<F, 2>(filter, block, e, P, n, ctrl, check_reject, s);
+  }
+}
+}  // namespace
+
+cudaError_t launch_edge_pass(bool rf, int filter, int ept, int block, const EdgeSpan &e, uint32_t *P,
+                             uint32_t n, Ctrl *ctrl, bool check_reject, cudaStream_t s) {
+  if (block != 128 && block != 256 && block != 512) block = 256;
+  if (e.n_quads == 0 && !e.head && !e.tail) return cudaSuccess;
+  return rf ? edge_pass_f<RootR>(filter, ept, block, e, P, n, ctrl, check_reject, s)
+            : edge_pass_f<RootId>(filter, ept, block, e, P, n, ctrl, check_reject, s);
+}
+
+cudaError_t launch_validate(const EdgeSpan &e, uint32_t n, Ctrl *ctrl, cudaStream_t s) {
+  if (e.n_quads == 0 && !e.head && !e.tail) return cudaSuccess;
+  const unsigned g = clamp_grid((e.n_quads + 255) / 256, persistent_cap((const void *)k_validate, 256, 0));
+  k_validate<<<g, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, n, ctrl); note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flatten(bool rf, int label_space, uint32_t *P, uint32_t n, uint32_t *L, Ctrl *ctrl,
+                           cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const uint64_t want = ((uint64_t)n + 255) / 256;
+  if (rf && label_space == kLabelMinId && L) {
+    const unsigned gp = clamp_grid(want / 4 + 1, persistent_cap((const void *)k_gmin_probe, 256, 0));
+    k_gmin_probe<<<gp, 256, 0, s>>>(P, n, ctrl); note_launch();
+  }
+#define CC_FLAT(F_, LAB_)                                                                    \
+  do {                                                                                       \
+    const unsigned g = clamp_grid(want, persistent_cap((const void *)k_flatten<F_, LAB_>, 256, 0)); \
+    k_flatten<F_, LAB_><<<g, 256, 0, s>>>(P, n, L, ctrl); note_launch();                                     \
+  } while (0)
+  if (rf) {
+    if (label_space == kLabelRootValue) CC_FLAT(RootR, kLabelRootValue);
+    else CC_FLAT(RootR, kLabelMinId);
+  } else {
+    if (label_space == kLabelRootValue) CC_FLAT(RootId, kLabelRootValue);
+    else CC_FLAT(RootId, kLabelMinId);
+  }
+#undef CC_FLAT
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_roots(bool rf, const uint32_t *P, uint32_t n, Ctrl *ctrl, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const uint64_t want = ((uint64_t)n + 255) / 256;
+  if (rf) {
+    const unsigned g = clamp_grid(want, persistent_cap((const void *)k_count_roots<RootR>, 256, 0));
+    k_count_roots<RootR><<<g, 256, 0, s>>>(P, n, ctrl); note_launch();
+  } else {
+    const unsigned g = clamp_grid(want, persistent_cap((const void *)k_count_roots<RootId>, 256, 0));
+    k_count_roots<RootId><<<g, 256, 0, s>>>(P, n, ctrl); note_launch();
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_connected(bool rf, uint32_t *P, uint32_t n, const uint2 *pairs, uint64_t n_pairs,
+                             uint8_t *out, Ctrl *ctrl, cudaStream_t s) {
+  if (n_pairs == 0) return cudaSuccess;
+  const uint64_t want = (n_pairs + 255) / 256;
+  if (rf) {
+    const unsigned g = clamp_grid(want, persistent_cap((const void *)k_connected<RootR>, 256, 0));
+    k_connected<RootR><<<g, 256, 0, s>>>(P, n, pairs, n_pairs, out, ctrl); note_launch();
+  } else {
+    const unsigned g = clamp_grid(want, persistent_cap((const void *)k_connected<RootId>, 256, 0));
+    k_connected<RootId><<<g, 256, 0, s>>>(P, n, pairs, n_pairs, out, ctrl); note_launch();
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace cc

@@ -1,0 +1,292 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle,
+bit for bit (labels are integers; there is no tolerance).
+
+Covers every edge-pass variant (filter on/off, 2/4/8 edges per thread, block
+sizes), both root functions and both label spaces, ragged and misaligned
+inputs, degenerate graphs, adversarial edge orders, hot-CAS stars, queries,
+incremental inserts, checkpoints, host-buffer runs and device-side error
+reporting.
+"""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+cc = pytest.importorskip("paper_2507_03695_gb300")
+
+
+def dev_edges(e: np.ndarray, misalign: bool = False):
+    e = np.ascontiguousarray(e, dtype=np.uint32).reshape(-1, 2)
+    if not misalign:
+        return torch.from_numpy(e.view(np.int32)).cuda()
+    buf = torch.empty((len(e) + 1, 2), dtype=torch.int32, device="cuda")
+    buf[1:] = torch.from_numpy(e.view(np.int32)).cuda()
+    view = buf[1:]
+    assert view.data_ptr() % 16 == 8
+    return view
+
+
+def run_labels(n, e, misalign=False, **opts):
+    with cc.Graph(n, **opts) as g:
+        L = torch.full((max(n, 1),), -1, dtype=torch.int32, device="cuda")
+        g.run(dev_edges(e, misalign), L[:n] if n else None)
+        g.sync()
+        return L[:n].cpu().numpy().view(np.uint32), g.num_components(), g.root_vertex()
+
+
+@pytest.fixture(scope="module")
+def rmat16():
+    w = graphgen.RMAT16
+    e = w.host_edges()
+    return w.n_vertices, e, oracle.min_labels(w.n_vertices, e)
+
+
+@pytest.mark.parametrize("mode", [cc.CC_ROOT_MAXDEG, cc.CC_ROOT_IDENTITY])
+@pytest.mark.parametrize("flt", [cc.CC_FILTER_ON, cc.CC_FILTER_OFF])
+@pytest.mark.parametrize("ept", [2, 4, 8])
+@pytest.mark.parametrize("block", [128, 256, 512])
+def test_rmat16_every_variant(rmat16, mode, flt, ept, block):
+    n, e, want = rmat16
+    got, ncomp, m = run_labels(n, e, mode=mode, filter=flt, edges_per_thread=ept, block_size=block)
+    np.testing.assert_array_equal(got, want)
+    assert ncomp == oracle.num_components(want)
+    if mode == cc.CC_ROOT_MAXDEG:
+        assert m == oracle.max_degree_vertex(n, e)
+
+
+@pytest.mark.parametrize("label_space", [cc.CC_LABEL_MIN_ID, cc.CC_LABEL_ROOT_VALUE])
+@pytest.mark.parametrize("select", [cc.CC_ROOT_SELECT_EXACT, cc.CC_ROOT_SELECT_SAMPLED])
+def test_rmat16_label_spaces(rmat16, label_space, select):
+    n, e, want = rmat16
+    got, _, m = run_labels(n, e, mode=cc.CC_ROOT_MAXDEG, label_space=label_space, root_select=select,
+                           sample_stride=4)
+    if select == cc.CC_ROOT_SELECT_EXACT:
+        assert m == oracle.max_degree_vertex(n, e)
+    if label_space == cc.CC_LABEL_MIN_ID:
+        np.testing.assert_array_equal(got, want)
+    else:
+        # root-value labels for the planted vertex the library reports
+        np.testing.assert_array_equal(got, oracle.root_value_labels(n, e, m))
+
+
+def test_identity_root_value_equals_min_id(rmat16):
+    n, e, want = rmat16
+    got, _, _ = run_labels(n, e, mode=cc.CC_ROOT_IDENTITY, label_space=cc.CC_LABEL_ROOT_VALUE)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_root_hint(rmat16):
+    n, e, want = rmat16
+    for hint in (0, 1, n // 2, n - 1):
+        got, _, m = run_labels(n, e, mode=cc.CC_ROOT_MAXDEG, root_hint=hint)
+        assert m == hint
+        np.testing.assert_array_equal(got, want)
+        got, _, _ = run_labels(n, e, mode=cc.CC_ROOT_MAXDEG, root_hint=hint,
+                               label_space=cc.CC_LABEL_ROOT_VALUE)
+        np.testing.assert_array_equal(got, oracle.root_value_labels(n, e, hint))
+
+
+CASES = [(1, 0), (1, 1), (2, 1), (3, 2), (5, 3), (7, 0), (1000, 1), (1000, 2), (1000, 3),
+         (1000, 999), (1000, 5000), (4099, 4097), (65536 + 3, 200001), (300007, 900013)]
+
+
+@pytest.mark.parametrize("n,m", CASES)
+@pytest.mark.parametrize("misalign", [False, True])
+def test_random_ragged(n, m, misalign):
+    rng = np.random.default_rng(n * 7919 + m)
+    e = rng.integers(0, n, size=(m, 2)).astype(np.uint32)
+    want = oracle.min_labels(n, e)
+    for mode in (cc.CC_ROOT_MAXDEG, cc.CC_ROOT_IDENTITY):
+        for flt in (cc.CC_FILTER_ON, cc.CC_FILTER_OFF):
+            got, ncomp, _ = run_labels(n, e, misalign, mode=mode, filter=flt)
+            np.testing.assert_array_equal(got, want)
+            assert ncomp == oracle.num_components(want)
+
+
+def test_empty_vertex_set():
+    with cc.Graph(0) as g:
+        g.run(torch.empty((0, 2), dtype=torch.int32, device="cuda"), None)
+        g.sync()
+        assert g.num_components() == 0
+
+
+def _structured():
+    n = 200000
+    out = {}
+    out["path_descending"] = (n, np.stack([np.arange(n - 1, 0, -1), np.arange(n - 2, -1, -1)], 1))
+    out["path_ascending"] = (n, np.stack([np.arange(0, n - 1), np.arange(1, n)], 1))
+    out["path_desc_reversed_pairs"] = (n, np.stack([np.arange(n - 2, -1, -1), np.arange(n - 1, 0, -1)], 1))
+    out["star_high_centre"] = (n, np.stack([np.full(n - 1, n - 1), np.arange(n - 1)], 1))
+    out["star_low_centre_dup"] = (n, np.tile(np.stack([np.zeros(n - 1, int), np.arange(1, n)], 1), (3, 1)))
+    sizes = [1, 2, 3, 7, 30, 57, 300]
+    starts = np.cumsum([0] + sizes[:-1])
+    cl = [(s + i, s + j) for s, z in zip(starts, sizes) for i in range(z) for j in range(i + 1, z)]
+    out["cliques"] = (sum(sizes), np.array(cl))
+    W, H = 700, 300
+    ids = np.arange(W * H).reshape(H, W)
+    out["full_grid"] = (W * H, np.concatenate([np.stack([ids[:, :-1].ravel(), ids[:, 1:].ravel()], 1),
+                                               np.stack([ids[:-1, :].ravel(), ids[1:, :].ravel()], 1)]))
+    out["self_loops"] = (5000, np.stack([np.arange(5000), np.arange(5000)], 1))
+    out["one_edge_repeated"] = (10, np.tile(np.array([[7, 3]]), (100000, 1)))
+    out["grid_gen_p09"] = (256 * 256, graphgen.grid(256, 256, 9))
+    return out
+
+
+STRUCT = _structured()
+
+
+@pytest.mark.parametrize("name", sorted(STRUCT))
+def test_structured(name):
+    n, e = STRUCT[name]
+    e = np.asarray(e, dtype=np.uint32)
+    want = oracle.min_labels(n, e)
+    for mode in (cc.CC_ROOT_MAXDEG, cc.CC_ROOT_IDENTITY):
+        for flt in (cc.CC_FILTER_ON, cc.CC_FILTER_OFF):
+            got, ncomp, m = run_labels(n, e, mode=mode, filter=flt)
+            np.testing.assert_array_equal(got, want)
+            assert ncomp == oracle.num_components(want)
+            if mode == cc.CC_ROOT_MAXDEG:
+                assert m == oracle.max_degree_vertex(n, e)
+
+
+def test_order_direction_duplicate_invariance(rmat16):
+    n, e, want = rmat16
+    rng = np.random.default_rng(1)
+    e2 = e[rng.permutation(len(e))]
+    e2 = np.where(rng.random((len(e2), 1)) < 0.5, e2[:, ::-1], e2)
+    e2 = np.concatenate([e2, e2[:1000], np.stack([np.arange(n), np.arange(n)], 1)]).astype(np.uint32)
+    got, _, _ = run_labels(n, e2)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_connected_queries(rmat16):
+    n, e, want = rmat16
+    q = graphgen.pairs(n, 100003, 5)
+    with cc.Graph(n) as g:
+        g.run(dev_edges(e))
+        out = torch.empty(len(q), dtype=torch.uint8, device="cuda")
+        g.connected(dev_edges(q), out)
+        g.sync()
+        np.testing.assert_array_equal(out.cpu().numpy(), oracle.connected(want, q))
+        for (u, v) in q[:20]:
+            assert cc.cc_connected1(g.h, int(u), int(v)) == bool(want[u] == want[v])
+
+
+@pytest.mark.parametrize("mode", [cc.CC_ROOT_MAXDEG, cc.CC_ROOT_IDENTITY])
+def test_incremental_inserts_equal_union(mode):
+    n = 1 << 16
+    base = graphgen.rmat(16, 1 << 17, 21, scramble=True)
+    batches = [graphgen.pairs(n, k, 30 + i) for i, k in enumerate([1, 1000, 7, 40000, 3, 12345])]
+    with cc.Graph(n, mode=mode) as g:
+        L = torch.empty(n, dtype=torch.int32, device="cuda")
+        g.run(dev_edges(base), L)
+        seen = [base]
+        for b in batches:
+            g.insert(dev_edges(b))
+            seen.append(b)
+            g.labels(L)
+            g.sync()
+            want = oracle.min_labels(n, np.concatenate(seen))
+            np.testing.assert_array_equal(L.cpu().numpy().view(np.uint32), want)
+            assert g.num_components() == oracle.num_components(want)
+    # inserts on a fresh handle, without any cc_run
+    with cc.Graph(n, mode=mode) as g:
+        L = torch.empty(n, dtype=torch.int32, device="cuda")
+        for b in batches:
+            g.insert(dev_edges(b))
+        assert g.num_components() == oracle.num_components(oracle.min_labels(n, np.concatenate(batches)))
+        g.labels(L)
+        g.sync()
+        np.testing.assert_array_equal(L.cpu().numpy().view(np.uint32),
+                                      oracle.min_labels(n, np.concatenate(batches)))
+
+
+def test_insert_rejects_out_of_range_batch():
+    n = 5000
+    base = graphgen.er(n, 3000, 2)
+    with cc.Graph(n) as g:
+        L0 = torch.empty(n, dtype=torch.int32, device="cuda")
+        g.run(dev_edges(base), L0)
+        g.sync()
+        bad = graphgen.pairs(n, 4000, 9)
+        bad[1234, 1] = n  # one id out of range
+        g.insert(dev_edges(bad))
+        assert cc.cc_sync_status(g.h) == cc.CC_ERR_OUT_OF_RANGE
+        L1 = torch.empty(n, dtype=torch.int32, device="cuda")
+        g.labels(L1)
+        g.sync()  # the error was reported once and cleared
+        np.testing.assert_array_equal(L1.cpu().numpy(), L0.cpu().numpy())
+
+
+def test_run_reports_out_of_range():
+    n = 100
+    e = np.array([[1, 2], [3, 100], [4, 5]], np.uint32)
+    with cc.Graph(n) as g:
+        g.run(dev_edges(e), None)
+        assert cc.cc_sync_status(g.h) == cc.CC_ERR_OUT_OF_RANGE
+        assert cc.cc_sync_status(g.h) == cc.CC_OK
+        q = torch.tensor([[0, 1], [5, 999]], dtype=torch.int32, device="cuda")
+        out = torch.empty(2, dtype=torch.uint8, device="cuda")
+        g.connected(q, out)
+        assert cc.cc_sync_status(g.h) == cc.CC_ERR_OUT_OF_RANGE
+        with pytest.raises(cc.CCError):
+            cc.cc_connected1(g.h, 0, 100)
+
+
+def test_checkpoint_restore_midstream():
+    n = 1 << 15
+    base = graphgen.rmat(15, 1 << 16, 40, scramble=True)
+    batches = [graphgen.pairs(n, 3000, 50 + i) for i in range(4)]
+    for mode in (cc.CC_ROOT_MAXDEG, cc.CC_ROOT_IDENTITY):
+        with cc.Graph(n, mode=mode) as g:
+            g.run(dev_edges(base))
+            g.insert(dev_edges(batches[0]))
+            g.insert(dev_edges(batches[1]))
+            ck = cc.cc_checkpoint(g.h)
+            m_before = g.root_vertex()
+        with cc.Graph(n, mode=mode) as h:
+            cc.cc_restore(h.h, ck)
+            assert h.root_vertex() == m_before
+            h.insert(dev_edges(batches[2]))
+            h.insert(dev_edges(batches[3]))
+            L = torch.empty(n, dtype=torch.int32, device="cuda")
+            h.labels(L)
+            h.sync()
+            want = oracle.min_labels(n, np.concatenate([base] + batches))
+            np.testing.assert_array_equal(L.cpu().numpy().view(np.uint32), want)
+
+
+@pytest.mark.parametrize("mode,select", [(cc.CC_ROOT_MAXDEG, cc.CC_ROOT_SELECT_EXACT),
+                                         (cc.CC_ROOT_MAXDEG, cc.CC_ROOT_SELECT_SAMPLED),
+                                         (cc.CC_ROOT_IDENTITY, cc.CC_ROOT_SELECT_EXACT)])
+def test_run_host_buffers(mode, select):
+    n = 1 << 18
+    E = (1 << 24) + (1 << 20) + 5  # two copy chunks (2^24 edges each), odd count
+    e = graphgen.rmat(18, E, 60, scramble=True)
+    want = oracle.min_labels(n, e)
+    host = torch.from_numpy(e.view(np.int32)).pin_memory()
+    L = torch.empty(n, dtype=torch.int32).pin_memory()
+    with cc.Graph(n, E, mode=mode, root_select=select) as g:
+        cc.cc_run_host(g.h, host, None, L)
+        np.testing.assert_array_equal(L.numpy().view(np.uint32), want)
+        if select == cc.CC_ROOT_SELECT_EXACT and mode == cc.CC_ROOT_MAXDEG:
+            assert g.root_vertex() == oracle.max_degree_vertex(n, e)
+        with pytest.raises(cc.CCError):
+            cc.cc_run_host(g.h, host, E + 1, L)
+
+
+def test_phase_times_and_budget():
+    n = 1 << 16
+    e = graphgen.rmat(16, 1 << 20, 1, scramble=False)
+    with cc.Graph(n, timing=1) as g:
+        g.run(dev_edges(e))
+        t = cc.cc_phase_times(g.h)
+        assert all(x >= 0 for x in t) and t[4] >= t[2]
+        assert cc.cc_device_bytes(g.h) >= 4 * n
+    with pytest.raises(cc.CCError) as ex:
+        cc.Graph(n, hbm_budget_bytes=1024)
+    assert ex.value.status == cc.CC_ERR_OOM
