@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 namespace cc {
@@ -22,14 +23,18 @@ struct alignas(128) Ctrl {
   unsigned long long maxkey;  // root select, u32 counts: (deg << 32) | ~v, atomicMax
   unsigned long long maxcnt;  // root select, u64 counts: max degree
   unsigned long long ncomp;   // roots counted by the last flatten / count pass
+  alignas(8) uint32_t q_u;    // cc_connected1 pair: read as one 8-byte (u, v) load
+  uint32_t q_v;
+  uint32_t q_out;             // cc_connected1 result (first byte)
   uint32_t m_sel;             // root select, u64 counts: smallest v with deg == maxcnt
   uint32_t m;                 // planted vertex in use (written by init)
   uint32_t gmin;              // smallest vertex of m's component (min-id labels, f = R)
   uint32_t err;               // kErr* bits
   uint32_t reject;            // the insert batch being applied failed validation
-  uint32_t q_u, q_v, q_out;   // cc_connected1 scratch
   unsigned long long stats[4];  // optional edge-pass counters
 };
+static_assert(offsetof(Ctrl, q_u) % 8 == 0, "the query pair is loaded with an 8-byte access");
+static_assert(offsetof(Ctrl, maxkey) % 8 == 0 && offsetof(Ctrl, ncomp) % 8 == 0, "64-bit atomics");
 
 // Label spaces (cc_label_space).
 enum : int { kLabelMinId = 0, kLabelRootValue = 1 };

@@ -197,7 +197,7 @@ __device__ __forceinline__ void single_edge(uint32_t *P, const F fn, const uint2
 // Direct form: each thread takes Q 128-bit loads (2Q edges) per iteration,
 // issues all 4Q parent loads together, then resolves its edges one by one.
 template <class F, int Q>
-__global__ void __launch_bounds__(256) k_edge_pass_direct(const uint4 *__restrict__ e4,
+__global__ void __launch_bounds__(512) k_edge_pass_direct(const uint4 *__restrict__ e4,
                                                           uint64_t n_quads, const uint2 *head,
                                                           const uint2 *tail, uint32_t *P,
                                                           uint32_t n, Ctrl *ctrl, int check_reject) {
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(256) k_edge_pass_direct(const uint4 *__restric
 constexpr int kRing = 64;
 
 template <class F, int Q>
-__global__ void __launch_bounds__(256) k_edge_pass_filtered(const uint4 *__restrict__ e4,
+__global__ void __launch_bounds__(512) k_edge_pass_filtered(const uint4 *__restrict__ e4,
                                                             uint64_t n_quads, const uint2 *head,
                                                             const uint2 *tail, uint32_t *P,
                                                             uint32_t n, Ctrl *ctrl,
