@@ -218,6 +218,34 @@ CC_API cc_status cc_restore(cc_graph *g, const void *host_buf, uint64_t bytes);
 /* Device bytes owned by the handle. */
 CC_API cc_status cc_device_bytes(const cc_graph *g, uint64_t *bytes);
 
+/* Largest vertex count cc_max_degree_vertex_noalloc accepts. */
+#define CC_NOALLOC_MAX_VERTICES (1u << 22)
+
+/* The maximum-degree vertex of an edge list, for callers that cannot allocate
+ * device memory. The paper has no counterpart: it is this library's root
+ * selection (degree = occurrences as an endpoint, a self-loop counts twice,
+ * ties to the smaller id; the same answer as cc_root_vertex after a cc_run in
+ * CC_ROOT_MAXDEG mode with exact selection) with no handle and no
+ * cudaMalloc. It is meant for code that must not allocate: code running
+ * inside another framework's allocator or pool callbacks, services whose
+ * device memory is fixed at start-up, and code that cannot afford the device
+ * synchronisation cudaMalloc/cudaFree may cause.
+ *  - In: edges_dev, n_edges COO pairs (8-byte aligned; ids >= n_vertices are
+ *    not counted), n_vertices in [1, CC_NOALLOC_MAX_VERTICES], n_edges < 2^31.
+ *  - Out: *m_out_dev (one uint32 in device memory, 4-byte aligned), written
+ *    on `stream`; the call is stream-ordered and returns once enqueued.
+ *  - Scratch: a fixed static device array inside the library (about 16 MiB
+ *    per GPU that loads the library, held until the process exits). The first
+ *    call on a device looks up its address (cudaGetSymbolAddress); make that
+ *    first call before any stream capture. All calls share the array and
+ *    each clears what it uses, so calls whose work overlaps on the GPU race:
+ *    serialise them (one stream, or events).
+ * Errors: CC_ERR_INVALID_ARGUMENT (NULL or misaligned pointer, n_vertices 0),
+ * CC_ERR_TOO_LARGE (n_vertices or n_edges over the limits), CC_ERR_CUDA. */
+CC_API cc_status cc_max_degree_vertex_noalloc(const uint32_t *edges_dev, uint64_t n_edges,
+                                              uint64_t n_vertices, uint32_t *m_out_dev,
+                                              cc_stream_t stream);
+
 /* Frees the handle after waiting for its work. NULL is ignored. */
 CC_API void cc_destroy(cc_graph *g);
 

@@ -77,6 +77,7 @@ def lib():
             "cc_phase_times": (_i32, [_ptr, P(ctypes.c_float)]),
             "cc_phase_times_total": (_i32, [_ptr, P(ctypes.c_float), P(_u64)]),
             "cc_kernel_launches": (_u64, []),
+            "cc_max_degree_vertex_noalloc": (_i32, [_ptr, _u64, _u64, _ptr, _ptr]),
             "cc_checkpoint_size": (_i32, [_ptr, P(_u64)]),
             "cc_checkpoint": (_i32, [_ptr, _ptr, _u64]),
             "cc_restore": (_i32, [_ptr, _ptr, _u64]),
@@ -217,6 +218,14 @@ def cc_phase_times_total(g: int) -> tuple[list[float], int]:
 
 def cc_kernel_launches() -> int:
     return int(lib().cc_kernel_launches())
+
+
+def cc_max_degree_vertex_noalloc(edges, n_vertices: int, m_out, n_edges: int | None = None,
+                                 stream=None) -> None:
+    """Maximum-degree vertex into the device uint32 m_out, allocating nothing."""
+    _check(lib().cc_max_degree_vertex_noalloc(_addr(edges), _count_pairs(edges, n_edges), n_vertices,
+                                              _addr(m_out), _stream(stream)),
+           "cc_max_degree_vertex_noalloc")
 
 
 def cc_checkpoint_size(g: int) -> int:
