@@ -44,15 +44,21 @@ def _stale(target: str) -> bool:
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          defines: tuple[str, ...] = (), out_dir: str | None = None) -> str:
+    """Compile and link libcc.so. `defines` adds -D build options and
+    `out_dir` builds into another folder (the default is the in-tree _build)."""
+    bdir = out_dir or BUILD
+    lib = os.path.join(bdir, "libcc.so")
     with _LOCK:
-        if not force and not _stale(LIB):
-            return LIB
-        os.makedirs(BUILD, exist_ok=True)
+        if not force and not defines and not _stale(lib):
+            return lib
+        os.makedirs(bdir, exist_ok=True)
         extra = ["-Xptxas", "-v"] if ptxas_info else []
+        extra += [f"-D{d}" for d in defines]
 
         def compile_one(src: str) -> str:
-            obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+            obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
             cmd = ["nvcc", *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
@@ -65,13 +71,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
         with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
             objs = list(ex.map(compile_one, sources()))
-        tmp = LIB + f".tmp{os.getpid()}"
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = ["nvcc", "-shared", f"-gencode=arch=compute_{ARCH},code=sm_{ARCH}", "-o", tmp, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
-        return LIB
+        os.replace(tmp, lib)
+        return lib
 
 
 if __name__ == "__main__":

@@ -11,7 +11,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/cc.h"
+#include "cc.h"
 #include "cc_internal.h"
 
 using cc::Ctrl;
@@ -24,6 +24,7 @@ struct cc_graph {
   uint32_t *P = nullptr;
   void *cnt = nullptr;  // root-select histogram (uint32 or uint64 per vertex)
   size_t cnt_bytes = 0;
+  cc::CertScratch *cert = nullptr;  // certified root-select scratch
   Ctrl *ctrl = nullptr;
   Ctrl *host_ctrl = nullptr;  // pinned mirror
   uint32_t *staging = nullptr;
@@ -130,9 +131,8 @@ cc_status fetch_ctrl(cc_graph *g, cudaStream_t s) {
 
 bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
 
-// Root selection (f = R with no hint): degree histogram over all edges, or
-// over the sampled groups, then the argmax with ties to the smaller id.
-// Returns the init kernel's source of m.
+// Root selection (f = R with no hint): the certified exact selection, or the
+// argmax of a histogram over the sampled groups. Leaves m in ctrl->maxkey.
 cc_status root_select(cc_graph *g, const uint32_t *edges, uint64_t n_edges, const cc::EdgeSpan &span,
                       cudaStream_t s, int *m_src) {
   const uint32_t n = (uint32_t)g->n;
@@ -148,25 +148,20 @@ cc_status root_select(cc_graph *g, const uint32_t *edges, uint64_t n_edges, cons
     CC_TRY(dev_alloc(g, &g->cnt, need));
     g->cnt_bytes = need;
   }
-  CC_TRY(cudaMemsetAsync(g->cnt, 0, need, s));
-  if (wide) {
-    CC_TRY(cudaMemsetAsync(&g->ctrl->maxcnt, 0, sizeof(unsigned long long), s));
-    CC_TRY(cudaMemsetAsync(&g->ctrl->m_sel, 0xFF, sizeof(uint32_t), s));
-    CC_TRY(cc::launch_degree_u64(span, (unsigned long long *)g->cnt, n, s));
-    CC_TRY(cc::launch_argmax_u64((const unsigned long long *)g->cnt, n, g->ctrl, s));
-    *m_src = cc::kMFromSelected;
-  } else {
+  *m_src = cc::kMFromPackedMax;
+  if (sampled) {
+    CC_TRY(cudaMemsetAsync(g->cnt, 0, need, s));
     CC_TRY(cudaMemsetAsync(&g->ctrl->maxkey, 0, sizeof(unsigned long long), s));
-    if (sampled)
-      CC_TRY(cc::launch_degree_sampled_u32(reinterpret_cast<const uint2 *>(edges), n_edges, 0, stride,
-                                           (uint32_t *)g->cnt, n, s));
-    else
-      CC_TRY(cc::launch_degree_u32(span, (uint32_t *)g->cnt, n, s));
+    CC_TRY(cc::launch_degree_sampled_u32(reinterpret_cast<const uint2 *>(edges), n_edges, 0, stride,
+                                         (uint32_t *)g->cnt, n, s));
     CC_TRY(cc::launch_argmax_u32((const uint32_t *)g->cnt, n, g->ctrl, s));
-    *m_src = cc::kMFromPackedMax;
+    return CC_OK;
   }
+  CC_TRY(cc::launch_root_select_certified(edges, n_edges, span, g->cnt, wide, n, g->cert, g->ctrl, s));
   return CC_OK;
 }
+
+void record(cc_graph *g, int i, cudaStream_t s);
 
 constexpr size_t kMaxEventSets = 4096;
 
@@ -243,7 +238,8 @@ cc_status cc_create(uint64_t n_vertices, uint64_t n_edges_capacity, const cc_opt
 
   // host-side checks first: they need no device
   const bool rf = o.mode == CC_ROOT_MAXDEG;
-  const size_t need = p_bytes(n_vertices) + (rf ? (size_t)n_vertices * 4 : 0) + sizeof(Ctrl) +
+  const size_t need = p_bytes(n_vertices) +
+                      (rf ? (size_t)n_vertices * 4 + sizeof(cc::CertScratch) : 0) + sizeof(Ctrl) +
                       (size_t)n_edges_capacity * 8;
   if (o.hbm_budget_bytes && need > o.hbm_budget_bytes) return CC_ERR_OOM;
 
@@ -272,6 +268,7 @@ cc_status cc_create(uint64_t n_vertices, uint64_t n_edges_capacity, const cc_opt
     if (g->rf && n_vertices) {
       if ((e = dev_alloc(g, &g->cnt, (size_t)n_vertices * 4)) != cudaSuccess) break;
       g->cnt_bytes = (size_t)n_vertices * 4;
+      if ((e = dev_alloc(g, (void **)&g->cert, sizeof(cc::CertScratch))) != cudaSuccess) break;
     }
     if (n_edges_capacity) {
       if ((e = dev_alloc(g, (void **)&g->staging, (size_t)n_edges_capacity * 8)) != cudaSuccess) break;
@@ -304,6 +301,7 @@ void cc_destroy(cc_graph *g) {
   cudaDeviceSynchronize();
   dev_free(g, g->P, p_bytes(g->n));
   dev_free(g, g->cnt, g->cnt_bytes);
+  dev_free(g, g->cert, sizeof(cc::CertScratch));
   dev_free(g, g->ctrl, sizeof(Ctrl));
   dev_free(g, g->staging, (size_t)g->capacity * 8);
   dev_free(g, g->label_dev, (size_t)g->n * 4);
@@ -362,34 +360,12 @@ cc_status cc_run_host(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges,
   if (g->n == 0) return CC_OK;
   const uint32_t n = (uint32_t)g->n;
   if (L_out_host && !g->label_dev) CC_TRY(dev_alloc(g, (void **)&g->label_dev, (size_t)n * 4));
+  // When m is known before the edges arrive (identity, or a hint), the edge
+  // pass runs on each chunk as soon as it lands; otherwise the root selection
+  // needs every edge first, and the copies only overlap each other.
   const bool select = g->rf && g->opt.root_hint == CC_ROOT_AUTO;
-  const uint32_t stride = g->opt.sample_stride ? (uint32_t)g->opt.sample_stride : 16u;
-  const bool sampled = g->opt.root_select == CC_ROOT_SELECT_SAMPLED && stride > 1;
-  const bool wide = select && !sampled && n_edges >= (1ULL << 31);
-  int m_src = cc::kMFromHint;
   const uint32_t hint = (g->rf && !select) ? (uint32_t)g->opt.root_hint : 0u;
-  if (select) {
-    const size_t need = (size_t)n * (wide ? 8 : 4);
-    if (g->cnt_bytes < need) {
-      CC_TRY(cudaStreamSynchronize(s));
-      dev_free(g, g->cnt, g->cnt_bytes);
-      g->cnt = nullptr;
-      g->cnt_bytes = 0;
-      CC_TRY(dev_alloc(g, &g->cnt, need));
-      g->cnt_bytes = need;
-    }
-    CC_TRY(cudaMemsetAsync(g->cnt, 0, need, s));
-    if (wide) {
-      CC_TRY(cudaMemsetAsync(&g->ctrl->maxcnt, 0, sizeof(unsigned long long), s));
-      CC_TRY(cudaMemsetAsync(&g->ctrl->m_sel, 0xFF, sizeof(uint32_t), s));
-      m_src = cc::kMFromSelected;
-    } else {
-      CC_TRY(cudaMemsetAsync(&g->ctrl->maxkey, 0, sizeof(unsigned long long), s));
-      m_src = cc::kMFromPackedMax;
-    }
-  } else {
-    CC_TRY(cc::launch_init(g->rf, g->P, n, g->ctrl, m_src, hint, s));
-  }
+  if (!select) CC_TRY(cc::launch_init(g->rf, g->P, n, g->ctrl, cc::kMFromHint, hint, s));
   // the copy stream starts after everything already enqueued on s
   CC_TRY(cudaEventRecord(g->copy_ev, s));
   CC_TRY(cudaStreamWaitEvent(g->copy_stream, g->copy_ev, 0));
@@ -397,29 +373,21 @@ cc_status cc_run_host(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges,
     const uint64_t cnt = (n_edges - off) < kHostChunk ? (n_edges - off) : kHostChunk;
     CC_TRY(cudaMemcpyAsync(g->staging + 2 * off, edges_host + 2 * off, cnt * 8, cudaMemcpyHostToDevice,
                            g->copy_stream));
-    CC_TRY(cudaEventRecord(g->copy_ev, g->copy_stream));
-    CC_TRY(cudaStreamWaitEvent(s, g->copy_ev, 0));
-    const cc::EdgeSpan span = cc::split_edges(g->staging + 2 * off, cnt);
-    if (select) {
-      if (wide)
-        CC_TRY(cc::launch_degree_u64(span, (unsigned long long *)g->cnt, n, s));
-      else if (sampled)
-        CC_TRY(cc::launch_degree_sampled_u32(reinterpret_cast<const uint2 *>(g->staging + 2 * off), cnt,
-                                             off, stride, (uint32_t *)g->cnt, n, s));
-      else
-        CC_TRY(cc::launch_degree_u32(span, (uint32_t *)g->cnt, n, s));
-    } else {
-      CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), span, g->P, n, g->ctrl,
-                                  false, s));
+    if (!select) {
+      CC_TRY(cudaEventRecord(g->copy_ev, g->copy_stream));
+      CC_TRY(cudaStreamWaitEvent(s, g->copy_ev, 0));
+      CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g),
+                                  cc::split_edges(g->staging + 2 * off, cnt), g->P, n, g->ctrl, false, s));
     }
   }
   if (select) {
-    if (wide)
-      CC_TRY(cc::launch_argmax_u64((const unsigned long long *)g->cnt, n, g->ctrl, s));
-    else
-      CC_TRY(cc::launch_argmax_u32((const uint32_t *)g->cnt, n, g->ctrl, s));
-    CC_TRY(cc::launch_init(g->rf, g->P, n, g->ctrl, m_src, hint, s));
+    CC_TRY(cudaEventRecord(g->copy_ev, g->copy_stream));
+    CC_TRY(cudaStreamWaitEvent(s, g->copy_ev, 0));
     const cc::EdgeSpan all = cc::split_edges(g->staging, n_edges);
+    int m_src = cc::kMFromHint;
+    cc_status st = root_select(g, g->staging, n_edges, all, s, &m_src);
+    if (st != CC_OK) return st;
+    CC_TRY(cc::launch_init(g->rf, g->P, n, g->ctrl, m_src, hint, s));
     CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), all, g->P, n, g->ctrl,
                                 false, s));
   }

@@ -28,6 +28,7 @@ namespace cc {
 // f(v) = v (Algorithm 1; Algorithm 3 with the identity, Section IV).
 struct RootId {
   static constexpr bool kRF = false;
+  static constexpr uint32_t kOff = 0;  // f(x) = x + kOff for every x with f(x) != 0
   __device__ __forceinline__ static RootId load(const Ctrl *) { return RootId{}; }
   __device__ __forceinline__ uint32_t f(uint32_t x) const { return x; }
   __device__ __forceinline__ uint32_t finv(uint32_t c) const { return c; }
@@ -36,6 +37,7 @@ struct RootId {
 // f = R (Eq. 1), f^-1 = R^-1 (Eq. 2).
 struct RootR {
   static constexpr bool kRF = true;
+  static constexpr uint32_t kOff = 1;
   uint32_t m;
   __device__ __forceinline__ static RootR load(const Ctrl *ctrl) {
     return RootR{*(const volatile uint32_t *)&ctrl->m};
@@ -72,9 +74,20 @@ __device__ __forceinline__ uint2 ld_edge(const uint2 *a) {
 // Parent-array load. A weak load may be served from this SM's L1 and so be
 // stale; by the facts above a stale value is an older ancestor, which keeps
 // every search correct. (CAS results always come from L2.)
+// Build option CC_PLOAD selects the cache behaviour of these loads: 0 (default)
+// allocates in L1, 1 bypasses L1 allocation, 2 caches in L2 only (.cg).
+#ifndef CC_PLOAD
+#define CC_PLOAD 0
+#endif
 __device__ __forceinline__ uint32_t ldP(const uint32_t *p) {
   uint32_t r;
+#if CC_PLOAD == 1
+  asm volatile("ld.global.L1::no_allocate.u32 %0, [%1];" : "=r"(r) : "l"(p) : "memory");
+#elif CC_PLOAD == 2
+  asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(r) : "l"(p) : "memory");
+#else
   asm volatile("ld.global.u32 %0, [%1];" : "=r"(r) : "l"(p) : "memory");
+#endif
   return r;
 }
 
@@ -94,82 +107,93 @@ __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t *p) {
 
 __device__ __forceinline__ void set_err(Ctrl *ctrl, uint32_t bit) { atomicOr(&ctrl->err, bit); }
 
+// ----------------------------------------------------------- instrumentation
+// Built with -DCC_STATS, the searches count their work into a device array
+// (edges that reach a root search, parent loads in searches, CAS attempts, CAS
+// failures); diagnostics only, off in normal builds.
+#ifdef CC_STATS
+__device__ unsigned long long g_cc_stats[4];  // only cc_kernels.cu includes this header
+#define CC_STAT(i) atomicAdd(&g_cc_stats[(i)], 1ULL)
+#else
+#define CC_STAT(i) ((void)0)
+#endif
+
 // ------------------------------------------------------------------ searches
+//
+// The searches work on names: vertex x is named f(x), and P[x] holds the name
+// of x's parent (x's own name when x is a root). Every vertex except the one
+// named 0 has f(x) = x + kOff, so the slot of name c >= 1 is
+// slots(P)[c] = P[c - kOff]: a walk up the parents needs neither f nor f^-1,
+// only an address with a constant offset. The vertex named 0 is never loaded
+// through its name: it can never be hooked, so reading the name 0 ends a walk.
 
-// Root value of x, given px = a value P[x] has held. Walks with path splitting
-// (each visited non-root x gets its grandparent's value). The walk is at most
-// n steps because f strictly decreases along parents.
 template <class F>
-__device__ __forceinline__ uint32_t find_root_value(uint32_t *P, const F fn, uint32_t x, uint32_t px) {
-  while (px != fn.f(x)) {
-    if (px == 0u) return 0u;  // the value-0 vertex is a permanent root
-    const uint32_t w = fn.finv(px);
-    const uint32_t pw = ldP(P + w);
-    if (pw != px) stP(P + x, pw);  // w is not a root: split x past it
-    x = w;
-    px = pw;
-  }
-  return px;
+__device__ __forceinline__ uint32_t *slots(uint32_t *P) {
+  return P - F::kOff;
 }
 
-// Same, without writes (queries that must not touch P).
-template <class F>
-__device__ __forceinline__ uint32_t find_root_value_ro(const uint32_t *P, const F fn, uint32_t x,
-                                                       uint32_t px) {
-  while (px != fn.f(x)) {
-    if (px == 0u) return 0u;
-    x = fn.finv(px);
-    px = ldP(P + x);
+// Root name of the vertex named c, given pc = a value its P has held. Walks
+// with path splitting (each visited non-root gets its grandparent's name).
+// The walk is at most n steps because names strictly decrease along parents.
+__device__ __forceinline__ uint32_t root_name(uint32_t *S, uint32_t c, uint32_t pc) {
+  while (pc != c) {
+    if (pc == 0u) return 0u;  // the permanent root
+    const uint32_t pw = ldP(S + pc);
+    if (pw != pc) stP(S + c, pw);  // the parent is not a root: split past it
+    c = pc;
+    pc = pw;
   }
-  return px;
+  return c;
 }
 
-// One edge of the hooking pass (Algorithm 3): pu and pv are values P[u] and
-// P[v] have held. Repeats { find both roots; equal -> done; CAS the root of
-// larger f from f(root) to the other root's f } until a CAS succeeds. A
-// failed CAS returns the root's new parent value, and the search resumes from
-// that root (the current roots, not the original endpoints). Any moment at
-// which both sides show the same parent value proves a common tree and ends
-// the edge, which includes the case of both endpoints already holding 0.
-template <class F>
-__device__ __forceinline__ void unite(uint32_t *P, const F fn, uint32_t u, uint32_t pu, uint32_t v,
-                                      uint32_t pv) {
+// One edge of the hooking pass (Algorithm 3) in names: cu, cv name the
+// endpoints and pu, pv are values their P held. Repeats { find both roots;
+// equal -> done; CAS the root of larger name from its name to the other
+// root's name } until a CAS succeeds. A failed CAS returns the root's new
+// parent, and the search resumes from that root (the current roots, not the
+// original endpoints). Any moment at which both sides show the same parent
+// name proves a common tree and ends the edge, which includes the case of
+// both endpoints already holding 0.
+__device__ __forceinline__ void unite(uint32_t *S, uint32_t cu, uint32_t pu, uint32_t cv, uint32_t pv) {
+  if (pu != pv) CC_STAT(0);
   while (true) {
     if (pu == pv) return;
-    while (pu != fn.f(u)) {
+    while (pu != cu) {
       if (pu == 0u) {
-        u = fn.finv(0u);
+        cu = 0u;
         break;
       }
-      const uint32_t w = fn.finv(pu);
-      const uint32_t pw = ldP(P + w);
-      if (pw != pu) stP(P + u, pw);
-      u = w;
+      CC_STAT(1);
+      const uint32_t pw = ldP(S + pu);
+      if (pw != pu) stP(S + cu, pw);
+      cu = pu;
       pu = pw;
       if (pu == pv) return;
     }
-    while (pv != fn.f(v)) {
+    while (pv != cv) {
       if (pv == 0u) {
-        v = fn.finv(0u);
+        cv = 0u;
         break;
       }
-      const uint32_t w = fn.finv(pv);
-      const uint32_t pw = ldP(P + w);
-      if (pw != pv) stP(P + v, pw);
-      v = w;
+      CC_STAT(1);
+      const uint32_t pw = ldP(S + pv);
+      if (pw != pv) stP(S + cv, pw);
+      cv = pv;
       pv = pw;
       if (pu == pv) return;
     }
     if (pu == pv) return;  // same root
+    CC_STAT(2);
     if (pu < pv) {
-      const uint32_t old = atomicCAS(P + v, pv, pu);
+      const uint32_t old = atomicCAS(S + cv, pv, pu);
       if (old == pv) return;
-      pv = old;  // v was hooked meanwhile: continue from v
+      pv = old;  // that root was hooked meanwhile: continue from it
     } else {
-      const uint32_t old = atomicCAS(P + u, pu, pv);
+      const uint32_t old = atomicCAS(S + cu, pu, pv);
       if (old == pu) return;
       pu = old;
     }
+    CC_STAT(3);
   }
 }
 

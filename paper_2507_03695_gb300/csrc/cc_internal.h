@@ -16,7 +16,7 @@ enum : uint32_t {
 };
 
 // Where the init kernel takes the planted vertex m from.
-enum : int { kMFromHint = 0, kMFromPackedMax = 1, kMFromSelected = 2 };
+enum : int { kMFromHint = 0, kMFromPackedMax = 1 };
 
 // Per-handle control block in device memory (one cache line or two).
 struct alignas(128) Ctrl {
@@ -26,11 +26,13 @@ struct alignas(128) Ctrl {
   alignas(8) uint32_t q_u;    // cc_connected1 pair: read as one 8-byte (u, v) load
   uint32_t q_v;
   uint32_t q_out;             // cc_connected1 result (first byte)
-  uint32_t m_sel;             // root select, u64 counts: smallest v with deg == maxcnt
+  uint32_t m_sel;             // root select, 64-bit counts: smallest v with deg == maxcnt
   uint32_t m;                 // planted vertex in use (written by init)
   uint32_t gmin;              // smallest vertex of m's component (min-id labels, f = R)
   uint32_t err;               // kErr* bits
   uint32_t reject;            // the insert batch being applied failed validation
+  uint32_t n_cand;            // root select: candidates found by the sampled pass
+  uint32_t cert;              // root select: 1 when the candidate pass proved the argmax
   unsigned long long stats[4];  // optional edge-pass counters
 };
 static_assert(offsetof(Ctrl, q_u) % 8 == 0, "the query pair is loaded with an 8-byte access");
@@ -55,18 +57,52 @@ EdgeSpan split_edges(const uint32_t *edges, uint64_t n_edges);
 
 int num_sms();
 
+// Grid of min(want, cap) blocks (at least one).
+inline unsigned clamp_grid(uint64_t want, uint64_t cap) {
+  if (want == 0) want = 1;
+  return (unsigned)(want < cap ? want : cap);
+}
+
+// Blocks that fit on the whole GPU at once for this kernel and block size.
+inline uint64_t persistent_cap(const void *kernel, int block, size_t smem) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, smem) != cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  return (uint64_t)num_sms() * (uint64_t)occ;
+}
+
 // Process-wide count of kernel launches issued by the library.
 void note_launch();
 unsigned long long launch_count();
 
 cudaError_t launch_init(bool rf, uint32_t *P, uint32_t n, Ctrl *ctrl, int m_src, uint32_t m_hint,
                         cudaStream_t s);
+// Scratch of the certified exact root selection (cc_rootsel.cu).
+constexpr uint32_t kCertCand = 2048;     // candidate vertices at most
+constexpr uint32_t kCertSlots = 8192;    // open-addressing table of the candidates
+constexpr uint32_t kCertBuckets = 8192;  // hash buckets of the degree bound
+struct CertScratch {
+  uint32_t cand[kCertCand];
+  uint32_t keys[kCertSlots];                  // vertex + 1 (0 = empty)
+  unsigned long long cand_cnt[kCertSlots];    // exact degree of the slot's vertex
+  unsigned long long bucket[kCertBuckets];    // endpoint occurrences per bucket
+};
+
+// Certified exact root selection: sampled candidates, one exact pass over all
+// edges counting candidate degrees and bucket totals in shared memory, a
+// proof that no other vertex reaches the best candidate's degree, and the
+// full histogram as a fallback that runs only when the proof fails.
+// cnt holds n counters of 4 bytes (8 when wide); afterwards ctrl->maxkey
+// encodes m ((deg << 32) | ~m for the init kernel).
+cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges, const EdgeSpan &e,
+                                         void *cnt, bool wide, uint32_t n, CertScratch *cs, Ctrl *ctrl,
+                                         cudaStream_t s);
+
 cudaError_t launch_degree_u32(const EdgeSpan &e, uint32_t *cnt, uint32_t n, cudaStream_t s);
-cudaError_t launch_degree_u64(const EdgeSpan &e, unsigned long long *cnt, uint32_t n, cudaStream_t s);
 cudaError_t launch_degree_sampled_u32(const uint2 *edges, uint64_t n_edges, uint64_t edge_base,
                                       uint32_t stride, uint32_t *cnt, uint32_t n, cudaStream_t s);
 cudaError_t launch_argmax_u32(const uint32_t *cnt, uint32_t n, Ctrl *ctrl, cudaStream_t s);
-cudaError_t launch_argmax_u64(const unsigned long long *cnt, uint32_t n, Ctrl *ctrl, cudaStream_t s);
 cudaError_t launch_edge_pass(bool rf, int filter, int ept, int block, const EdgeSpan &e, uint32_t *P,
                              uint32_t n, Ctrl *ctrl, bool check_reject, cudaStream_t s);
 cudaError_t launch_validate(const EdgeSpan &e, uint32_t n, Ctrl *ctrl, cudaStream_t s);

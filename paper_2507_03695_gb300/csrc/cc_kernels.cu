@@ -20,19 +20,6 @@ namespace {
 
 int g_num_sms = 0;
 
-inline unsigned clamp_grid(uint64_t want, uint64_t cap) {
-  if (want == 0) want = 1;
-  return (unsigned)(want < cap ? want : cap);
-}
-
-inline uint64_t persistent_cap(const void *kernel, int block, size_t smem) {
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, smem) != cudaSuccess ||
-      occ < 1)
-    occ = 1;
-  return (uint64_t)num_sms() * (uint64_t)occ;
-}
-
 // ------------------------------------------------------------------- init
 
 template <class F>
@@ -42,10 +29,8 @@ __global__ void __launch_bounds__(256) k_init(uint32_t *__restrict__ P, uint32_t
   if (F::kRF) {
     if (m_src == kMFromHint)
       m = m_hint;
-    else if (m_src == kMFromPackedMax)
-      m = ~(uint32_t)(*(volatile unsigned long long *)&ctrl->maxkey);
     else
-      m = *(volatile uint32_t *)&ctrl->m_sel;
+      m = ~(uint32_t)(*(volatile unsigned long long *)&ctrl->maxkey);
     if (m >= n) m = 0;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -78,102 +63,6 @@ __global__ void __launch_bounds__(256) k_init(uint32_t *__restrict__ P, uint32_t
   }
 }
 
-// ------------------------------------------------------------ root select
-
-template <typename C>
-__device__ __forceinline__ void count_edge(C *cnt, uint32_t n, uint32_t a, uint32_t b) {
-  if (a < n) atomicAdd(cnt + a, (C)1);
-  if (b < n) atomicAdd(cnt + b, (C)1);
-}
-
-template <typename C>
-__global__ void __launch_bounds__(256) k_degree(const uint4 *__restrict__ e4, uint64_t n_quads,
-                                                const uint2 *head, const uint2 *tail,
-                                                C *__restrict__ cnt, uint32_t n) {
-  const uint64_t pol = policy_evict_first();
-  const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
-  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (t == 0 && head) {
-    uint2 e = ld_edge(head);
-    count_edge(cnt, n, e.x, e.y);
-  }
-  if (t == 1 % T && tail) {
-    uint2 e = ld_edge(tail);
-    count_edge(cnt, n, e.x, e.y);
-  }
-  for (uint64_t q = t; q < n_quads; q += T) {
-    const uint4 e = ld_edges(e4 + q, pol);
-    count_edge(cnt, n, e.x, e.y);
-    count_edge(cnt, n, e.z, e.w);
-  }
-}
-
-// Sampled histogram: edge i (global index edge_base + i) is counted iff
-// ((edge_base + i) / 1024) % stride == 0.
-__global__ void __launch_bounds__(256) k_degree_sampled(const uint2 *__restrict__ e, uint64_t n_edges,
-                                                        uint64_t edge_base, uint32_t stride,
-                                                        uint32_t *__restrict__ cnt, uint32_t n) {
-  const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
-  // iterate over sampled global indices only
-  const uint64_t g_first = edge_base / 1024u;
-  const uint64_t g_last = (edge_base + n_edges + 1023u) / 1024u;  // exclusive
-  uint64_t g0 = (g_first + stride - 1) / stride * stride;          // first sampled group
-  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;; k += T) {
-    const uint64_t grp = g0 + (k / 1024u) * stride;
-    if (grp >= g_last) break;
-    const uint64_t gi = grp * 1024u + (k % 1024u);
-    if (gi < edge_base || gi >= edge_base + n_edges) continue;
-    const uint2 x = ld_edge(e + (gi - edge_base));
-    count_edge(cnt, n, x.x, x.y);
-  }
-}
-
-__device__ __forceinline__ void block_max_u64(unsigned long long key, unsigned long long *target) {
-  __shared__ unsigned long long sm[32];
-  key = warp_max_u64(key);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) sm[wid] = key;
-  __syncthreads();
-  if (wid == 0) {
-    key = lane < (int)(blockDim.x >> 5) ? sm[lane] : 0ULL;
-    key = warp_max_u64(key);
-    if (lane == 0 && key) atomicMax(target, key);
-  }
-}
-
-// Packed key (deg << 32) | ~v: the largest key has the largest degree and,
-// among equal degrees, the smallest v.
-__global__ void __launch_bounds__(256) k_argmax_u32(const uint32_t *__restrict__ cnt, uint32_t n,
-                                                    Ctrl *ctrl) {
-  unsigned long long best = 0;
-  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
-       v += (uint64_t)gridDim.x * blockDim.x) {
-    const unsigned long long key = ((unsigned long long)cnt[v] << 32) | (uint32_t)~(uint32_t)v;
-    best = key > best ? key : best;
-  }
-  block_max_u64(best, &ctrl->maxkey);
-}
-
-__global__ void __launch_bounds__(256) k_maxcnt_u64(const unsigned long long *__restrict__ cnt,
-                                                    uint32_t n, Ctrl *ctrl) {
-  unsigned long long best = 0;
-  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
-       v += (uint64_t)gridDim.x * blockDim.x)
-    best = cnt[v] > best ? cnt[v] : best;
-  block_max_u64(best, &ctrl->maxcnt);
-}
-
-__global__ void __launch_bounds__(256) k_minid_u64(const unsigned long long *__restrict__ cnt,
-                                                   uint32_t n, Ctrl *ctrl) {
-  const unsigned long long mx = *(volatile unsigned long long *)&ctrl->maxcnt;
-  uint32_t best = 0xFFFFFFFFu;
-  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
-       v += (uint64_t)gridDim.x * blockDim.x)
-    if (cnt[v] == mx && (uint32_t)v < best) best = (uint32_t)v;
-  best = __reduce_min_sync(0xFFFFFFFFu, best);
-  if ((threadIdx.x & 31) == 0 && best != 0xFFFFFFFFu) atomicMin(&ctrl->m_sel, best);
-}
-
 // --------------------------------------------------------------- edge pass
 
 // Range check of one edge; an out-of-range id flags the error and turns the
@@ -191,7 +80,7 @@ __device__ __forceinline__ void single_edge(uint32_t *P, const F fn, const uint2
                                             Ctrl *ctrl) {
   uint2 x = ld_edge(e);
   guard(x.x, x.y, n, ctrl);
-  unite(P, fn, x.x, ldP(P + x.x), x.y, ldP(P + x.y));
+  unite(slots<F>(P), fn.f(x.x), ldP(P + x.x), fn.f(x.y), ldP(P + x.y));
 }
 
 // Direct form: each thread takes Q 128-bit loads (2Q edges) per iteration,
@@ -203,6 +92,7 @@ __global__ void __launch_bounds__(512) k_edge_pass_direct(const uint4 *__restric
                                                           uint32_t n, Ctrl *ctrl, int check_reject) {
   if (check_reject && ld_volatile_u32(&ctrl->reject)) return;
   const F fn = F::load(ctrl);
+  uint32_t *const S = slots<F>(P);
   const uint64_t pol = policy_evict_first();
   const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -227,8 +117,8 @@ __global__ void __launch_bounds__(512) k_edge_pass_direct(const uint4 *__restric
     }
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
-      unite(P, fn, e[j].x, p[4 * j + 0], e[j].y, p[4 * j + 1]);
-      unite(P, fn, e[j].z, p[4 * j + 2], e[j].w, p[4 * j + 3]);
+      unite(S, fn.f(e[j].x), p[4 * j + 0], fn.f(e[j].y), p[4 * j + 1]);
+      unite(S, fn.f(e[j].z), p[4 * j + 2], fn.f(e[j].w), p[4 * j + 3]);
     }
   }
 }
@@ -250,6 +140,7 @@ __global__ void __launch_bounds__(512) k_edge_pass_filtered(const uint4 *__restr
   extern __shared__ uint32_t ring_smem[];
   if (check_reject && ld_volatile_u32(&ctrl->reject)) return;
   const F fn = F::load(ctrl);
+  uint32_t *const S = slots<F>(P);
   const uint64_t pol = policy_evict_first();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t *ru = ring_smem + wid * (4 * kRing);
@@ -289,9 +180,9 @@ __global__ void __launch_bounds__(512) k_edge_pass_filtered(const uint4 *__restr
       const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
       if (keep) {
         const uint32_t slot = (qt + __popc(bal & lt_mask)) & (kRing - 1);
-        ru[slot] = a;
+        ru[slot] = fn.f(a);
         rpu[slot] = pa;
-        rv[slot] = b;
+        rv[slot] = fn.f(b);
         rpv[slot] = pb;
       }
       qt += __popc(bal);
@@ -300,7 +191,7 @@ __global__ void __launch_bounds__(512) k_edge_pass_filtered(const uint4 *__restr
         const uint32_t slot = (qh + lane) & (kRing - 1);
         const uint32_t sa = ru[slot], spa = rpu[slot], sb = rv[slot], spb = rpv[slot];
         __syncwarp();
-        unite(P, fn, sa, spa, sb, spb);
+        unite(S, sa, spa, sb, spb);
         qh += 32u;
       }
     }
@@ -309,7 +200,7 @@ __global__ void __launch_bounds__(512) k_edge_pass_filtered(const uint4 *__restr
   __syncwarp();
   if (lane < (int)(qt - qh)) {
     const uint32_t slot = (qh + lane) & (kRing - 1);
-    unite(P, fn, ru[slot], rpu[slot], rv[slot], rpv[slot]);
+    unite(S, ru[slot], rpu[slot], rv[slot], rpv[slot]);
   }
 }
 
@@ -361,7 +252,7 @@ __global__ void __launch_bounds__(256) k_gmin_probe(uint32_t *P, uint32_t n, Ctr
       const uint64_t v = start + (uint64_t)k * blockDim.x + threadIdx.x;
       if (v < m && v < best) {
         const uint32_t pv = ldP(P + v);
-        if (find_root_value(P, fn, (uint32_t)v, pv) == 0u) best = (uint32_t)v;
+        if (root_name(slots<RootR>(P), fn.f((uint32_t)v), pv) == 0u) best = (uint32_t)v;
       }
     }
     best = __reduce_min_sync(0xFFFFFFFFu, best);
@@ -390,7 +281,7 @@ __global__ void __launch_bounds__(256) k_flatten(uint32_t *P, uint32_t n, uint32
       c = pv;
       ++roots;
     } else {
-      c = find_root_value(P, fn, v, pv);
+      c = root_name(slots<F>(P), fn.f(v), pv);
       if (c != pv) stP(P + v, c);
     }
     if (L) {
@@ -432,8 +323,8 @@ __global__ void __launch_bounds__(256) k_connected(uint32_t *P, uint32_t n,
     if (q.x >= n || q.y >= n) {
       set_err(ctrl, kErrRange);
     } else {
-      const uint32_t cu = find_root_value(P, fn, q.x, ldP(P + q.x));
-      const uint32_t cv = find_root_value(P, fn, q.y, ldP(P + q.y));
+      const uint32_t cu = root_name(slots<F>(P), fn.f(q.x), ldP(P + q.x));
+      const uint32_t cv = root_name(slots<F>(P), fn.f(q.y), ldP(P + q.y));
       r = cu == cv;
     }
     out[i] = r;
@@ -484,44 +375,6 @@ cudaError_t launch_init(bool rf, uint32_t *P, uint32_t n, Ctrl *ctrl, int m_src,
     const unsigned g = clamp_grid((work + 255) / 256, persistent_cap((const void *)k_init<RootId>, 256, 0));
     k_init<RootId><<<g, 256, 0, s>>>(P, n, ctrl, m_src, m_hint); note_launch();
   }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_degree_u32(const EdgeSpan &e, uint32_t *cnt, uint32_t n, cudaStream_t s) {
-  const unsigned g = clamp_grid((e.n_quads + 255) / 256,
-                                persistent_cap((const void *)k_degree<uint32_t>, 256, 0));
-  k_degree<uint32_t><<<g, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, cnt, n); note_launch();
-  return cudaGetLastError();
-}
-
-cudaError_t launch_degree_u64(const EdgeSpan &e, unsigned long long *cnt, uint32_t n, cudaStream_t s) {
-  const unsigned g = clamp_grid((e.n_quads + 255) / 256,
-                                persistent_cap((const void *)k_degree<unsigned long long>, 256, 0));
-  k_degree<unsigned long long><<<g, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, cnt, n); note_launch();
-  return cudaGetLastError();
-}
-
-cudaError_t launch_degree_sampled_u32(const uint2 *edges, uint64_t n_edges, uint64_t edge_base,
-                                      uint32_t stride, uint32_t *cnt, uint32_t n, cudaStream_t s) {
-  if (n_edges == 0) return cudaSuccess;
-  if (stride == 0) stride = 1;
-  const uint64_t groups = (n_edges + 1023) / 1024 / stride + 2;
-  const unsigned g = clamp_grid(groups * 1024 / 256,
-                                persistent_cap((const void *)k_degree_sampled, 256, 0));
-  k_degree_sampled<<<g, 256, 0, s>>>(edges, n_edges, edge_base, stride, cnt, n); note_launch();
-  return cudaGetLastError();
-}
-
-cudaError_t launch_argmax_u32(const uint32_t *cnt, uint32_t n, Ctrl *ctrl, cudaStream_t s) {
-  const unsigned g = clamp_grid(((uint64_t)n + 255) / 256, persistent_cap((const void *)k_argmax_u32, 256, 0));
-  k_argmax_u32<<<g, 256, 0, s>>>(cnt, n, ctrl); note_launch();
-  return cudaGetLastError();
-}
-
-cudaError_t launch_argmax_u64(const unsigned long long *cnt, uint32_t n, Ctrl *ctrl, cudaStream_t s) {
-  const unsigned g = clamp_grid(((uint64_t)n + 255) / 256, persistent_cap((const void *)k_maxcnt_u64, 256, 0));
-  k_maxcnt_u64<<<g, 256, 0, s>>>(cnt, n, ctrl); note_launch();
-  k_minid_u64<<<g, 256, 0, s>>>(cnt, n, ctrl); note_launch();
   return cudaGetLastError();
 }
 
@@ -625,3 +478,13 @@ cudaError_t launch_connected(bool rf, uint32_t *P, uint32_t n, const uint2 *pair
 }
 
 }  // namespace cc
+
+#ifdef CC_STATS
+// Diagnostics builds only: read and clear the search counters.
+extern "C" __attribute__((visibility("default"))) int cc_stats_read(unsigned long long out[4]) {
+  cudaError_t e = cudaMemcpyFromSymbol(out, cc::g_cc_stats, 4 * sizeof(unsigned long long));
+  unsigned long long z[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(cc::g_cc_stats, z, sizeof(z));
+  return (int)e;
+}
+#endif

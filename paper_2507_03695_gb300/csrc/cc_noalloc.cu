@@ -22,7 +22,7 @@
 
 #include <mutex>
 
-#include "../../include/cc.h"
+#include "cc.h"
 #include "cc_internal.h"
 
 namespace {

@@ -1,0 +1,386 @@
+// cc_rootsel.cu - selection of the planted vertex m of Eq. 1: the vertex of
+// maximum degree (Algorithm 4, max_degree()), degree = occurrences as an
+// endpoint (a self-loop counts twice, duplicates count), ties to the smaller
+// id.
+//
+// A global histogram needs one random atomic per endpoint, which on R-MAT
+// graphs is slower than the edge pass itself. The default exact selection is
+// therefore certified instead:
+//   1. a histogram over 1 group of 1024 edges in 32 (global atomics) gives
+//      candidate hubs: every vertex with at least 1/32 of the largest sampled
+//      count (at most kCertCand of them);
+//   2. one pass over all edges counts, in shared memory only, the exact
+//      degree of every candidate and the total endpoint occurrences of every
+//      hash bucket of vertex ids;
+//   3. if the best candidate's degree D exceeds, in every bucket, the
+//      occurrences that belong to non-candidates, no non-candidate can reach
+//      D, so the best candidate (smaller id on ties) is the exact answer;
+//   4. otherwise (graphs without a dominant hub, such as grids) the full
+//      global histogram runs; its kernels read the certificate flag and
+//      return at once when step 3 succeeded.
+// The answer is the exact maximum-degree vertex in both cases.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cc_device.cuh"
+#include "cc_internal.h"
+
+namespace cc {
+
+namespace {
+
+__device__ __forceinline__ bool skipped(const uint32_t *skip) {
+  return skip && *(const volatile uint32_t *)skip != 0u;
+}
+
+template <typename C>
+__device__ __forceinline__ void count_edge(C *cnt, uint32_t n, uint32_t a, uint32_t b) {
+  if (a < n) atomicAdd(cnt + a, (C)1);
+  if (b < n) atomicAdd(cnt + b, (C)1);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_zero_cnt(C *cnt, uint32_t n, const uint32_t *skip) {
+  if (skipped(skip)) return;
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+       v += (uint64_t)gridDim.x * blockDim.x)
+    cnt[v] = (C)0;
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_degree(const uint4 *__restrict__ e4, uint64_t n_quads,
+                                                const uint2 *head, const uint2 *tail,
+                                                C *__restrict__ cnt, uint32_t n, const uint32_t *skip) {
+  if (skipped(skip)) return;
+  const uint64_t pol = policy_evict_first();
+  const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (t == 0 && head) {
+    uint2 e = ld_edge(head);
+    count_edge(cnt, n, e.x, e.y);
+  }
+  if (t == 1 % T && tail) {
+    uint2 e = ld_edge(tail);
+    count_edge(cnt, n, e.x, e.y);
+  }
+  for (uint64_t q = t; q < n_quads; q += T) {
+    const uint4 e = ld_edges(e4 + q, pol);
+    count_edge(cnt, n, e.x, e.y);
+    count_edge(cnt, n, e.z, e.w);
+  }
+}
+
+// Sampled histogram: edge i (global index edge_base + i) is counted iff
+// ((edge_base + i) / 1024) % stride == 0.
+__global__ void __launch_bounds__(256) k_degree_sampled(const uint2 *__restrict__ e, uint64_t n_edges,
+                                                        uint64_t edge_base, uint32_t stride,
+                                                        uint32_t *__restrict__ cnt, uint32_t n) {
+  const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t g_first = edge_base / 1024u;
+  const uint64_t g_last = (edge_base + n_edges + 1023u) / 1024u;  // exclusive
+  const uint64_t g0 = (g_first + stride - 1) / stride * stride;    // first sampled group
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;; k += T) {
+    const uint64_t grp = g0 + (k / 1024u) * stride;
+    if (grp >= g_last) break;
+    const uint64_t gi = grp * 1024u + (k % 1024u);
+    if (gi < edge_base || gi >= edge_base + n_edges) continue;
+    const uint2 x = ld_edge(e + (gi - edge_base));
+    count_edge(cnt, n, x.x, x.y);
+  }
+}
+
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long key) {
+  __shared__ unsigned long long sm[32];
+  key = warp_max_u64(key);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sm[wid] = key;
+  __syncthreads();
+  key = lane < (int)(blockDim.x >> 5) ? sm[lane] : 0ULL;
+  return warp_max_u64(key);  // valid in every warp
+}
+
+// Packed key (deg << 32) | ~v: the largest key has the largest degree and,
+// among equal degrees, the smallest v.
+__global__ void __launch_bounds__(256) k_argmax_u32(const uint32_t *__restrict__ cnt, uint32_t n,
+                                                    Ctrl *ctrl, const uint32_t *skip) {
+  if (skipped(skip)) return;
+  unsigned long long best = 0;
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+       v += (uint64_t)gridDim.x * blockDim.x) {
+    const unsigned long long key = ((unsigned long long)cnt[v] << 32) | (uint32_t)~(uint32_t)v;
+    best = key > best ? key : best;
+  }
+  best = block_max_u64(best);
+  if (threadIdx.x == 0 && best) atomicMax(&ctrl->maxkey, best);
+}
+
+__global__ void __launch_bounds__(256) k_maxcnt_u64(const unsigned long long *__restrict__ cnt,
+                                                    uint32_t n, Ctrl *ctrl, const uint32_t *skip) {
+  if (skipped(skip)) return;
+  unsigned long long best = 0;
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+       v += (uint64_t)gridDim.x * blockDim.x)
+    best = cnt[v] > best ? cnt[v] : best;
+  best = block_max_u64(best);
+  if (threadIdx.x == 0 && best) atomicMax(&ctrl->maxcnt, best);
+}
+
+__global__ void __launch_bounds__(256) k_minid_u64(const unsigned long long *__restrict__ cnt,
+                                                   uint32_t n, Ctrl *ctrl, const uint32_t *skip) {
+  if (skipped(skip)) return;
+  const unsigned long long mx = *(volatile unsigned long long *)&ctrl->maxcnt;
+  uint32_t best = 0xFFFFFFFFu;
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+       v += (uint64_t)gridDim.x * blockDim.x)
+    if (cnt[v] == mx && (uint32_t)v < best) best = (uint32_t)v;
+  best = __reduce_min_sync(0xFFFFFFFFu, best);
+  if ((threadIdx.x & 31) == 0 && best != 0xFFFFFFFFu) atomicMin(&ctrl->m_sel, best);
+}
+
+// Packs the 64-bit-count answer (m_sel) into maxkey for the init kernel.
+__global__ void k_finalize_m(Ctrl *ctrl, const uint32_t *skip) {
+  if (skipped(skip)) return;
+  ctrl->maxkey = (unsigned long long)(uint32_t)~ctrl->m_sel;
+}
+
+// ----------------------------------------------------------- certification
+
+__device__ __forceinline__ uint32_t bucket_of(uint32_t x) { return (x * 2654435769u) >> 19; }
+__device__ __forceinline__ uint32_t slot_of(uint32_t x) {
+  return ((x ^ (x >> 15)) * 0x85EBCA6Bu) >> 19;
+}
+static_assert(kCertBuckets == 8192 && kCertSlots == 8192, "hashes produce 13-bit indices");
+
+// Candidates: every vertex whose sampled count is at least 1/32 of the largest.
+// Without a dominant hub (largest sampled count below 64) no certificate can
+// succeed, so no candidates are taken and the full histogram runs. The list
+// counter is bumped once per warp, and scanning stops once the list is full.
+__global__ void __launch_bounds__(256) k_select_candidates(const uint32_t *__restrict__ cnt, uint32_t n,
+                                                           Ctrl *ctrl, CertScratch *cs) {
+  const uint32_t cmax = (uint32_t)(*(volatile unsigned long long *)&ctrl->maxkey >> 32);
+  if (cmax < 64u) return;
+  const uint32_t thr = cmax >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  const uint64_t w0 = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  for (uint64_t base = w0 * 32; base < n; base += warps * 32) {
+    if (*(volatile uint32_t *)&ctrl->n_cand >= kCertCand) return;  // warp-uniform
+    const uint64_t v = base + (uint64_t)lane;
+    const bool q = v < n && cnt[v] >= thr;
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, q);
+    if (!bal) continue;
+    uint32_t first = 0;
+    if (lane == 0) first = atomicAdd(&ctrl->n_cand, (uint32_t)__popc(bal));
+    first = __shfl_sync(0xFFFFFFFFu, first, 0);
+    if (q) {
+      const uint32_t i = first + (uint32_t)__popc(bal & ((1u << lane) - 1u));
+      if (i < kCertCand) cs->cand[i] = (uint32_t)v;
+    }
+  }
+}
+
+// The open-addressing table of the candidates (one block; built once, so all
+// blocks of the counting pass agree on the slots).
+__global__ void __launch_bounds__(256) k_build_table(const Ctrl *ctrl, CertScratch *cs) {
+  const uint32_t nc = min(*(const volatile uint32_t *)&ctrl->n_cand, kCertCand);
+  for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) {
+    const uint32_t x = cs->cand[i];
+    uint32_t s = slot_of(x);
+    for (uint32_t probe = 0; probe < kCertSlots; ++probe) {
+      const uint32_t prev = atomicCAS(&cs->keys[s], 0u, x + 1u);
+      if (prev == 0u || prev == x + 1u) break;
+      s = (s + 1u) & (kCertSlots - 1u);
+    }
+  }
+}
+
+__device__ __forceinline__ void cert_count(uint32_t x, uint32_t n, const uint32_t *keys, uint32_t *cnts,
+                                           uint32_t *bk) {
+  if (x >= n) return;
+  atomicAdd(&bk[bucket_of(x)], 1u);
+  uint32_t s = slot_of(x);
+  for (uint32_t probe = 0; probe < kCertSlots; ++probe) {
+    const uint32_t k = keys[s];
+    if (k == x + 1u) {
+      atomicAdd(&cnts[s], 1u);
+      return;
+    }
+    if (k == 0u) return;
+    s = (s + 1u) & (kCertSlots - 1u);
+  }
+}
+
+constexpr size_t kCertSmem = (2 * kCertSlots + kCertBuckets) * sizeof(uint32_t);
+
+// One pass over all edges: exact candidate degrees and bucket totals, counted
+// in shared memory and flushed once per block.
+__global__ void __launch_bounds__(512) k_degree_certify(const uint4 *__restrict__ e4, uint64_t n_quads,
+                                                        const uint2 *head, const uint2 *tail, uint32_t n,
+                                                        CertScratch *cs, const Ctrl *ctrl) {
+  extern __shared__ uint32_t csm[];
+  // no candidates (no dominant hub): the proof cannot succeed, skip the pass
+  if (*(const volatile uint32_t *)&ctrl->n_cand == 0u) return;
+  uint32_t *keys = csm, *cnts = csm + kCertSlots, *bk = csm + 2 * kCertSlots;
+  for (uint32_t i = threadIdx.x; i < kCertSlots; i += blockDim.x) {
+    keys[i] = cs->keys[i];
+    cnts[i] = 0u;
+  }
+  for (uint32_t i = threadIdx.x; i < kCertBuckets; i += blockDim.x) bk[i] = 0u;
+  __syncthreads();
+  const uint64_t pol = policy_evict_first();
+  const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (t == 0 && head) {
+    const uint2 e = ld_edge(head);
+    cert_count(e.x, n, keys, cnts, bk);
+    cert_count(e.y, n, keys, cnts, bk);
+  }
+  if (t == 1 % T && tail) {
+    const uint2 e = ld_edge(tail);
+    cert_count(e.x, n, keys, cnts, bk);
+    cert_count(e.y, n, keys, cnts, bk);
+  }
+  for (uint64_t q = t; q < n_quads; q += T) {
+    const uint4 e = ld_edges(e4 + q, pol);
+    cert_count(e.x, n, keys, cnts, bk);
+    cert_count(e.y, n, keys, cnts, bk);
+    cert_count(e.z, n, keys, cnts, bk);
+    cert_count(e.w, n, keys, cnts, bk);
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < kCertSlots; i += blockDim.x)
+    if (cnts[i]) atomicAdd(&cs->cand_cnt[i], (unsigned long long)cnts[i]);
+  for (uint32_t i = threadIdx.x; i < kCertBuckets; i += blockDim.x)
+    if (bk[i]) atomicAdd(&cs->bucket[i], (unsigned long long)bk[i]);
+}
+
+// The proof (one block): D = best candidate degree; bound = the largest
+// bucket total left after removing the candidates' own occurrences. D > bound
+// means every non-candidate has degree < D.
+__global__ void __launch_bounds__(1024) k_certify_decide(const CertScratch *cs, Ctrl *ctrl) {
+  extern __shared__ unsigned long long rem[];  // kCertBuckets
+  for (uint32_t b = threadIdx.x; b < kCertBuckets; b += blockDim.x) rem[b] = cs->bucket[b];
+  __syncthreads();
+  unsigned long long best = 0;
+  bool wide = false;
+  for (uint32_t s = threadIdx.x; s < kCertSlots; s += blockDim.x) {
+    const uint32_t k = cs->keys[s];
+    if (!k) continue;
+    const uint32_t x = k - 1u;
+    const unsigned long long c = cs->cand_cnt[s];
+    atomicAdd(&rem[bucket_of(x)], (unsigned long long)(0ULL - c));
+    if (c >= (1ULL << 32)) {
+      wide = true;
+      continue;
+    }
+    const unsigned long long key = (c << 32) | (uint32_t)~x;
+    best = key > best ? key : best;
+  }
+  __syncthreads();
+  unsigned long long bound = 0;
+  for (uint32_t b = threadIdx.x; b < kCertBuckets; b += blockDim.x) bound = rem[b] > bound ? rem[b] : bound;
+  const int any_wide = __syncthreads_or(wide);
+  best = block_max_u64(best);
+  bound = block_max_u64(bound);
+  if (threadIdx.x == 0) {
+    const unsigned long long D = best >> 32;
+    if (!any_wide && best != 0ULL && D > bound) {
+      ctrl->maxkey = best;
+      ctrl->cert = 1u;
+    } else {
+      ctrl->maxkey = 0ULL;
+      ctrl->cert = 0u;
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+
+cudaError_t launch_degree_u32(const EdgeSpan &e, uint32_t *cnt, uint32_t n, cudaStream_t s) {
+  const unsigned g = clamp_grid((e.n_quads + 255) / 256, persistent_cap((const void *)k_degree<uint32_t>, 256, 0));
+  k_degree<uint32_t><<<g, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, cnt, n, nullptr);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_degree_sampled_u32(const uint2 *edges, uint64_t n_edges, uint64_t edge_base,
+                                      uint32_t stride, uint32_t *cnt, uint32_t n, cudaStream_t s) {
+  if (n_edges == 0) return cudaSuccess;
+  if (stride == 0) stride = 1;
+  const uint64_t groups = (n_edges + 1023) / 1024 / stride + 2;
+  const unsigned g = clamp_grid(groups * 1024 / 256, persistent_cap((const void *)k_degree_sampled, 256, 0));
+  k_degree_sampled<<<g, 256, 0, s>>>(edges, n_edges, edge_base, stride, cnt, n);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_argmax_u32(const uint32_t *cnt, uint32_t n, Ctrl *ctrl, cudaStream_t s) {
+  const unsigned g = clamp_grid(((uint64_t)n + 255) / 256, persistent_cap((const void *)k_argmax_u32, 256, 0));
+  k_argmax_u32<<<g, 256, 0, s>>>(cnt, n, ctrl, nullptr);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges, const EdgeSpan &e,
+                                         void *cnt, bool wide, uint32_t n, CertScratch *cs, Ctrl *ctrl,
+                                         cudaStream_t s) {
+  cudaError_t err;
+  // 0. reset the sampled counters, the scratch and the control fields
+  if ((err = cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(uint32_t), s)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(cs, 0, sizeof(CertScratch), s)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(&ctrl->maxkey, 0, 2 * sizeof(unsigned long long), s)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(&ctrl->m_sel, 0xFF, sizeof(uint32_t), s)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(&ctrl->n_cand, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) return err;
+  uint32_t *c32 = static_cast<uint32_t *>(cnt);
+  // 1. sampled histogram and its maximum
+  if ((err = launch_degree_sampled_u32(reinterpret_cast<const uint2 *>(edges), n_edges, 0, 32u, c32, n, s)) !=
+      cudaSuccess)
+    return err;
+  if ((err = launch_argmax_u32(c32, n, ctrl, s)) != cudaSuccess) return err;
+  // 2. candidates and their table
+  const unsigned gsel = clamp_grid(((uint64_t)n + 255) / 256, persistent_cap((const void *)k_select_candidates, 256, 0));
+  k_select_candidates<<<gsel, 256, 0, s>>>(c32, n, ctrl, cs);
+  note_launch();
+  k_build_table<<<1, 256, 0, s>>>(ctrl, cs);
+  note_launch();
+  // 3. the exact pass in shared memory
+  cudaFuncSetAttribute((const void *)k_degree_certify, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCertSmem);
+  cudaFuncSetAttribute((const void *)k_certify_decide, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(kCertBuckets * sizeof(unsigned long long)));
+  const unsigned gcert = clamp_grid((e.n_quads + 511) / 512, persistent_cap((const void *)k_degree_certify, 512, kCertSmem));
+  k_degree_certify<<<gcert, 512, kCertSmem, s>>>(e.quads, e.n_quads, e.head, e.tail, n, cs, ctrl);
+  note_launch();
+  // 4. the proof
+  k_certify_decide<<<1, 1024, kCertBuckets * sizeof(unsigned long long), s>>>(cs, ctrl);
+  note_launch();
+  // 5. full histogram, skipped when certified
+  const uint32_t *skip = &ctrl->cert;
+  const unsigned gz = clamp_grid(((uint64_t)n + 255) / 256, persistent_cap((const void *)k_zero_cnt<uint32_t>, 256, 0));
+  const unsigned gd = clamp_grid((e.n_quads + 255) / 256, persistent_cap((const void *)k_degree<uint32_t>, 256, 0));
+  if (wide) {
+    unsigned long long *c64 = static_cast<unsigned long long *>(cnt);
+    k_zero_cnt<unsigned long long><<<gz, 256, 0, s>>>(c64, n, skip);
+    note_launch();
+    k_degree<unsigned long long><<<gd, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, c64, n, skip);
+    note_launch();
+    k_maxcnt_u64<<<gz, 256, 0, s>>>(c64, n, ctrl, skip);
+    note_launch();
+    k_minid_u64<<<gz, 256, 0, s>>>(c64, n, ctrl, skip);
+    note_launch();
+    k_finalize_m<<<1, 1, 0, s>>>(ctrl, skip);
+    note_launch();
+  } else {
+    k_zero_cnt<uint32_t><<<gz, 256, 0, s>>>(c32, n, skip);
+    note_launch();
+    k_degree<uint32_t><<<gd, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, c32, n, skip);
+    note_launch();
+    k_argmax_u32<<<gz, 256, 0, s>>>(c32, n, ctrl, skip);
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace cc

@@ -290,3 +290,44 @@ def test_phase_times_and_budget():
     with pytest.raises(cc.CCError) as ex:
         cc.Graph(n, hbm_budget_bytes=1024)
     assert ex.value.status == cc.CC_ERR_OOM
+
+
+def _hidden_hub_graph(extra: int):
+    """Visible hub A = 500 in every 5th edge; hidden hub B = 100 only in edge
+    groups the root-selection sample skips (groups of 1024, one in 32 sampled),
+    with deg(B) = deg(A) + extra. Other endpoints avoid both hubs."""
+    n, E = 1 << 16, 1024 * 32 * 8
+    rng = np.random.default_rng(11)
+    e = rng.integers(1000, n, size=(E, 2)).astype(np.uint32)
+    idx = np.arange(E)
+    e[idx % 5 == 0, 0] = 500
+    dA = int((idx % 5 == 0).sum())
+    hidden_slots = idx[((idx // 1024) % 32 != 0) & ((idx % 5 == 1) | (idx % 5 == 2))]
+    e[hidden_slots[: dA + extra], 1] = 100
+    deg = np.bincount(e.ravel(), minlength=n)
+    assert deg[100] - deg[500] == extra
+    return n, e
+
+
+@pytest.mark.parametrize("extra", [-1, 0, 1, 5000])
+def test_root_select_hidden_hub(extra):
+    n, e = _hidden_hub_graph(extra)
+    want_m = oracle.max_degree_vertex(n, e)
+    assert want_m == (500 if extra < 0 else 100)
+    got, _, m = run_labels(n, e, mode=cc.CC_ROOT_MAXDEG, label_space=cc.CC_LABEL_ROOT_VALUE)
+    assert m == want_m
+    np.testing.assert_array_equal(got, oracle.root_value_labels(n, e, want_m))
+
+
+def test_root_select_many_candidates():
+    """Thousands of equally heavy vertices (more than the candidate list
+    holds) plus one slightly heavier: still the exact maximum."""
+    n = 1 << 18
+    rng = np.random.default_rng(4)
+    heavy = rng.choice(n, size=6000, replace=False).astype(np.uint32)
+    e = np.stack([np.repeat(heavy, 100), rng.integers(0, n, size=600000)], 1).astype(np.uint32)
+    top = heavy[1234]
+    e = np.concatenate([e, np.stack([np.full(3, top), rng.integers(0, n, size=3)], 1)]).astype(np.uint32)
+    e = e[rng.permutation(len(e))]
+    _, _, m = run_labels(n, e, mode=cc.CC_ROOT_MAXDEG)
+    assert m == oracle.max_degree_vertex(n, e)
