@@ -80,8 +80,9 @@ cudaError_t launch_init(bool rf, uint32_t *P, uint32_t n, Ctrl *ctrl, int m_src,
                         cudaStream_t s);
 // Scratch of the certified exact root selection (cc_rootsel.cu).
 constexpr uint32_t kCertCand = 2048;     // candidate vertices at most
-constexpr uint32_t kCertSlots = 8192;    // open-addressing table of the candidates
+constexpr uint32_t kCertSlots = 4096;    // open-addressing table of the candidates
 constexpr uint32_t kCertBuckets = 8192;  // hash buckets of the degree bound
+constexpr uint32_t kCertSample = 128;    // the sampled pass keeps 1 group of 1024 edges in this many
 struct CertScratch {
   uint32_t cand[kCertCand];
   uint32_t keys[kCertSlots];                  // vertex + 1 (0 = empty)

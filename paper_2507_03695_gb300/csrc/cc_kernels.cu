@@ -260,15 +260,80 @@ __global__ void __launch_bounds__(256) k_gmin_probe(uint32_t *P, uint32_t n, Ctr
   }
 }
 
-// Pointer jumping (Algorithm 3): every vertex finds its root value c with
+// Pointer jumping (Algorithm 3): every vertex finds its root name c with
 // path splitting, stores c into P (compression; roots are never written) and,
-// when L is given, writes its label: the root value, the root's id (min-id
-// labels under f = id), or under f = R the root's id for c != 0 and the
-// smallest vertex of m's component for c == 0. Roots are counted.
+// when L is given, writes its label: the root's name (root-value labels, and
+// min-id labels under f = id), or under f = R the root's id c - 1 for c != 0
+// and the smallest vertex of m's component for c == 0. Roots are counted.
+template <class F, int LABEL>
+__device__ __forceinline__ uint32_t label_of(uint32_t c, uint32_t gmin) {
+  if (LABEL == kLabelRootValue || !F::kRF) return c;
+  return c == 0u ? gmin : c - 1u;
+}
+
+template <class F>
+__device__ __forceinline__ uint32_t flatten_one(uint32_t *S, const F fn, uint32_t v, uint32_t pv,
+                                                unsigned long long &roots) {
+  const uint32_t cv = fn.f(v);
+  if (pv == cv) {
+    ++roots;
+    return pv;
+  }
+  return root_name(S, cv, pv);
+}
+
+// Four consecutive vertices per thread: 16-byte loads of P, 16-byte stores of
+// the compressed names (only when one changed; every name written is a valid
+// ancestor, and roots are never changed) and of the labels.
+template <class F, int LABEL>
+__global__ void __launch_bounds__(256) k_flatten4(uint32_t *P, uint32_t n, uint32_t *__restrict__ L,
+                                                  Ctrl *ctrl) {
+  const F fn = F::load(ctrl);
+  uint32_t *const S = slots<F>(P);
+  uint32_t gmin = 0;
+  if (F::kRF && LABEL == kLabelMinId) gmin = ld_volatile_u32(&ctrl->gmin);
+  unsigned long long roots = 0;
+  const uint64_t n4 = n / 4u;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n4;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t v = (uint32_t)(4 * i);
+    uint4 p;
+    asm volatile("ld.global.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(p.x), "=r"(p.y), "=r"(p.z), "=r"(p.w)
+                 : "l"(P + v)
+                 : "memory");
+    uint4 c;
+    c.x = flatten_one(S, fn, v, p.x, roots);
+    c.y = flatten_one(S, fn, v + 1u, p.y, roots);
+    c.z = flatten_one(S, fn, v + 2u, p.z, roots);
+    c.w = flatten_one(S, fn, v + 3u, p.w, roots);
+    if (c.x != p.x || c.y != p.y || c.z != p.z || c.w != p.w)
+      asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(P + v), "r"(c.x), "r"(c.y), "r"(c.z),
+                   "r"(c.w)
+                   : "memory");
+    if (L)
+      __stcs(reinterpret_cast<uint4 *>(L + v),
+             make_uint4(label_of<F, LABEL>(c.x, gmin), label_of<F, LABEL>(c.y, gmin),
+                        label_of<F, LABEL>(c.z, gmin), label_of<F, LABEL>(c.w, gmin)));
+  }
+  // the last n % 4 vertices
+  if (blockIdx.x == 0 && threadIdx.x < (n & 3u)) {
+    const uint32_t v = (uint32_t)(4 * n4) + threadIdx.x;
+    const uint32_t pv = ldP(P + v);
+    const uint32_t c = flatten_one(S, fn, v, pv, roots);
+    if (c != pv) stP(P + v, c);
+    if (L) L[v] = label_of<F, LABEL>(c, gmin);
+  }
+  roots = warp_sum_u64(roots);
+  if ((threadIdx.x & 31) == 0 && roots) atomicAdd(&ctrl->ncomp, roots);
+}
+
+// One vertex per thread, for label buffers that are not 16-byte aligned.
 template <class F, int LABEL>
 __global__ void __launch_bounds__(256) k_flatten(uint32_t *P, uint32_t n, uint32_t *__restrict__ L,
                                                  Ctrl *ctrl) {
   const F fn = F::load(ctrl);
+  uint32_t *const S = slots<F>(P);
   uint32_t gmin = 0;
   if (F::kRF && LABEL == kLabelMinId) gmin = ld_volatile_u32(&ctrl->gmin);
   unsigned long long roots = 0;
@@ -276,24 +341,9 @@ __global__ void __launch_bounds__(256) k_flatten(uint32_t *P, uint32_t n, uint32
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t v = (uint32_t)i;
     const uint32_t pv = ldP(P + v);
-    uint32_t c;
-    if (pv == fn.f(v)) {
-      c = pv;
-      ++roots;
-    } else {
-      c = root_name(slots<F>(P), fn.f(v), pv);
-      if (c != pv) stP(P + v, c);
-    }
-    if (L) {
-      uint32_t lab;
-      if (LABEL == kLabelRootValue)
-        lab = c;
-      else if (F::kRF)
-        lab = c == 0u ? gmin : c - 1u;
-      else
-        lab = c;
-      __stcs(L + v, lab);
-    }
+    const uint32_t c = flatten_one(S, fn, v, pv, roots);
+    if (c != pv) stP(P + v, c);
+    if (L) __stcs(L + v, label_of<F, LABEL>(c, gmin));
   }
   roots = warp_sum_u64(roots);
   if ((threadIdx.x & 31) == 0 && roots) atomicAdd(&ctrl->ncomp, roots);
@@ -434,11 +484,18 @@ cudaError_t launch_flatten(bool rf, int label_space, uint32_t *P, uint32_t n, ui
     const unsigned gp = clamp_grid(want / 4 + 1, persistent_cap((const void *)k_gmin_probe, 256, 0));
     k_gmin_probe<<<gp, 256, 0, s>>>(P, n, ctrl); note_launch();
   }
-#define CC_FLAT(F_, LAB_)                                                                    \
-  do {                                                                                       \
-    const unsigned g = clamp_grid(want, persistent_cap((const void *)k_flatten<F_, LAB_>, 256, 0)); \
-    k_flatten<F_, LAB_><<<g, 256, 0, s>>>(P, n, L, ctrl); note_launch();                                     \
+#define CC_FLAT(F_, LAB_)                                                                         \
+  do {                                                                                            \
+    if (vec) {                                                                                    \
+      const unsigned g = clamp_grid(want / 4 + 1, persistent_cap((const void *)k_flatten4<F_, LAB_>, 256, 0)); \
+      k_flatten4<F_, LAB_><<<g, 256, 0, s>>>(P, n, L, ctrl);                                      \
+    } else {                                                                                      \
+      const unsigned g = clamp_grid(want, persistent_cap((const void *)k_flatten<F_, LAB_>, 256, 0)); \
+      k_flatten<F_, LAB_><<<g, 256, 0, s>>>(P, n, L, ctrl);                                       \
+    }                                                                                             \
+    note_launch();                                                                                \
   } while (0)
+  const bool vec = ((uintptr_t)L & 15u) == 0;  // P itself is 256-byte aligned
   if (rf) {
     if (label_space == kLabelRootValue) CC_FLAT(RootR, kLabelRootValue);
     else CC_FLAT(RootR, kLabelMinId);

@@ -6,7 +6,7 @@
 // A global histogram needs one random atomic per endpoint, which on R-MAT
 // graphs is slower than the edge pass itself. The default exact selection is
 // therefore certified instead:
-//   1. a histogram over 1 group of 1024 edges in 32 (global atomics) gives
+//   1. a histogram over 1 group of 1024 edges in 128 (global atomics) gives
 //      candidate hubs: every vertex with at least 1/32 of the largest sampled
 //      count (at most kCertCand of them);
 //   2. one pass over all edges counts, in shared memory only, the exact
@@ -146,11 +146,11 @@ __global__ void k_finalize_m(Ctrl *ctrl, const uint32_t *skip) {
 
 // ----------------------------------------------------------- certification
 
+// One multiplicative hash gives the bucket (13 bits) and the home slot of the
+// candidate table (its low 12 bits).
 __device__ __forceinline__ uint32_t bucket_of(uint32_t x) { return (x * 2654435769u) >> 19; }
-__device__ __forceinline__ uint32_t slot_of(uint32_t x) {
-  return ((x ^ (x >> 15)) * 0x85EBCA6Bu) >> 19;
-}
-static_assert(kCertBuckets == 8192 && kCertSlots == 8192, "hashes produce 13-bit indices");
+__device__ __forceinline__ uint32_t home_slot(uint32_t b) { return b & (kCertSlots - 1u); }
+static_assert(kCertBuckets == 8192 && kCertSlots <= kCertBuckets, "13-bit buckets, slots from their low bits");
 
 // Candidates: every vertex whose sampled count is at least 1/32 of the largest.
 // Without a dominant hub (largest sampled count below 64) no certificate can
@@ -165,7 +165,6 @@ __global__ void __launch_bounds__(256) k_select_candidates(const uint32_t *__res
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   const uint64_t w0 = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
   for (uint64_t base = w0 * 32; base < n; base += warps * 32) {
-    if (*(volatile uint32_t *)&ctrl->n_cand >= kCertCand) return;  // warp-uniform
     const uint64_t v = base + (uint64_t)lane;
     const bool q = v < n && cnt[v] >= thr;
     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, q);
@@ -177,6 +176,7 @@ __global__ void __launch_bounds__(256) k_select_candidates(const uint32_t *__res
       const uint32_t i = first + (uint32_t)__popc(bal & ((1u << lane) - 1u));
       if (i < kCertCand) cs->cand[i] = (uint32_t)v;
     }
+    if (first >= kCertCand) return;  // the list is full (warp-uniform)
   }
 }
 
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(256) k_build_table(const Ctrl *ctrl, CertScrat
   const uint32_t nc = min(*(const volatile uint32_t *)&ctrl->n_cand, kCertCand);
   for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) {
     const uint32_t x = cs->cand[i];
-    uint32_t s = slot_of(x);
+    uint32_t s = home_slot(bucket_of(x));
     for (uint32_t probe = 0; probe < kCertSlots; ++probe) {
       const uint32_t prev = atomicCAS(&cs->keys[s], 0u, x + 1u);
       if (prev == 0u || prev == x + 1u) break;
@@ -195,23 +195,27 @@ __global__ void __launch_bounds__(256) k_build_table(const Ctrl *ctrl, CertScrat
   }
 }
 
-__device__ __forceinline__ void cert_count(uint32_t x, uint32_t n, const uint32_t *keys, uint32_t *cnts,
-                                           uint32_t *bk) {
-  if (x >= n) return;
-  atomicAdd(&bk[bucket_of(x)], 1u);
-  uint32_t s = slot_of(x);
+// One endpoint: its bucket total, and its exact count when it is a candidate.
+// Ids >= n are counted too; they only make the bound more conservative (the
+// edge pass reports them).
+__device__ __forceinline__ void cert_count(uint32_t x, const uint32_t *keys, uint32_t *cnts, uint32_t *bk) {
+  const uint32_t b = bucket_of(x);
+  atomicAdd(&bk[b], 1u);
+  uint32_t s = home_slot(b);
+  uint32_t k = keys[s];
+  if (k == 0u) return;  // most endpoints: an empty home slot
   for (uint32_t probe = 0; probe < kCertSlots; ++probe) {
-    const uint32_t k = keys[s];
     if (k == x + 1u) {
       atomicAdd(&cnts[s], 1u);
       return;
     }
-    if (k == 0u) return;
     s = (s + 1u) & (kCertSlots - 1u);
+    k = keys[s];
+    if (k == 0u) return;
   }
 }
 
-constexpr size_t kCertSmem = (2 * kCertSlots + kCertBuckets) * sizeof(uint32_t);
+constexpr size_t kCertSmem = (2 * kCertSlots + kCertBuckets) * sizeof(uint32_t);  // 64 KiB
 
 // One pass over all edges: exact candidate degrees and bucket totals, counted
 // in shared memory and flushed once per block.
@@ -233,20 +237,20 @@ __global__ void __launch_bounds__(512) k_degree_certify(const uint4 *__restrict_
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (t == 0 && head) {
     const uint2 e = ld_edge(head);
-    cert_count(e.x, n, keys, cnts, bk);
-    cert_count(e.y, n, keys, cnts, bk);
+    cert_count(e.x, keys, cnts, bk);
+    cert_count(e.y, keys, cnts, bk);
   }
   if (t == 1 % T && tail) {
     const uint2 e = ld_edge(tail);
-    cert_count(e.x, n, keys, cnts, bk);
-    cert_count(e.y, n, keys, cnts, bk);
+    cert_count(e.x, keys, cnts, bk);
+    cert_count(e.y, keys, cnts, bk);
   }
   for (uint64_t q = t; q < n_quads; q += T) {
     const uint4 e = ld_edges(e4 + q, pol);
-    cert_count(e.x, n, keys, cnts, bk);
-    cert_count(e.y, n, keys, cnts, bk);
-    cert_count(e.z, n, keys, cnts, bk);
-    cert_count(e.w, n, keys, cnts, bk);
+    cert_count(e.x, keys, cnts, bk);
+    cert_count(e.y, keys, cnts, bk);
+    cert_count(e.z, keys, cnts, bk);
+    cert_count(e.w, keys, cnts, bk);
   }
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < kCertSlots; i += blockDim.x)
@@ -336,7 +340,7 @@ cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges
   if ((err = cudaMemsetAsync(&ctrl->n_cand, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) return err;
   uint32_t *c32 = static_cast<uint32_t *>(cnt);
   // 1. sampled histogram and its maximum
-  if ((err = launch_degree_sampled_u32(reinterpret_cast<const uint2 *>(edges), n_edges, 0, 32u, c32, n, s)) !=
+  if ((err = launch_degree_sampled_u32(reinterpret_cast<const uint2 *>(edges), n_edges, 0, kCertSample, c32, n, s)) !=
       cudaSuccess)
     return err;
   if ((err = launch_argmax_u32(c32, n, ctrl, s)) != cudaSuccess) return err;
