@@ -60,6 +60,8 @@ def parse_args(argv=None):
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat24+grid8192")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--batched-graphs", type=int, default=4096)
     p.add_argument("--cpu-fraction", type=float, default=1 / 8,
                    help="share of each graph's edges in the CPU oracle sample")
     return p.parse_args(argv)
@@ -372,6 +374,7 @@ def run_ours(args):
 
     for h in handles:
         h.close()
+    batched = None if args.no_batched else bench_batched(args, cc, graphgen, torch, stream)
     if rank == 0:
         line = {
             "metric": "GTEPS", "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
@@ -395,6 +398,7 @@ def run_ours(args):
             "path_algorithmic_gbs": path_bytes / (ms_per_step * 1e-3) / 1e9,
             "gteps_without_root_select": E_total / (sum(p[4] - p[0] for p in phase_ms) * 1e-3) / 1e9,
             "e2e": e2e,
+            "batched": batched,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": int(launches),
@@ -403,6 +407,83 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[k]
+
+
+def bench_batched(args, cc, graphgen, torch, stream):
+    """The mixed batch of many small graphs: one tuned, CUDA-graph-captured
+    persistent launch (cc_run_batched) against the plain path of one cc_run
+    per graph (f = id, handles created beforehand)."""
+    import numpy as np
+    d = graphgen.batch_dev(args.batched_graphs, graphgen.BATCH_SEED)
+    torch.cuda.synchronize()
+    G = d.n_graphs
+    E = int(d.edge_off_host[-1])
+    V = int(d.vtx_off_host[-1])
+    L = torch.empty(V, dtype=torch.int32, device="cuda")
+    b = cc.Batch(G)
+    best, tune_ms = b.tune(G, d.vtx_off, d.edge_off, d.edges, L, stream=stream)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.run(G, d.vtx_off, d.edge_off, d.edges, L, stream=s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        b.run(G, d.vtx_off, d.edge_off, d.edges, L, stream=s)
+    reps = max(3, min(args.steps, 20))
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    lat = []
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    cur = torch.cuda.current_stream()
+    for e0, e1 in evs:
+        e0.record(cur)
+        graph.replay()
+        e1.record(cur)
+    torch.cuda.synchronize()
+    lat = [e0.elapsed_time(e1) for e0, e1 in evs]
+    b.sync()
+    L_batched = L.clone()
+    b.close()
+
+    # plain path: one cc_run per graph
+    vo, eo = d.vtx_off_host.astype(np.int64), d.edge_off_host.astype(np.int64)
+    hs = [cc.Graph(int(vo[g + 1] - vo[g]), mode=cc.CC_ROOT_IDENTITY) for g in range(G)]
+    ebase, lbase = d.edges.data_ptr(), L.data_ptr()
+
+    def plain():
+        for g, h in enumerate(hs):
+            cc.cc_run(h.h, ebase + 8 * int(eo[g]), int(eo[g + 1] - eo[g]), lbase + 4 * int(vo[g]), stream)
+
+    plain()
+    torch.cuda.synchronize()
+    plain_ms = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plain()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms.append(e0.elapsed_time(e1))
+    same = bool(torch.equal(L, L_batched))
+    for h in hs:
+        h.close()
+    med = percentile(lat, 50)
+    pmed = percentile(plain_ms, 50)
+    return {"workload": f"{G} graphs (40% G(n,m), 40% R-MAT, 20% grid p=0.9), |V| log-uniform in [2^8,2^18)",
+            "n_vertices": V, "n_edges": E, "gteps": E / (med * 1e-3) / 1e9, "ms_p50": med,
+            "ms_p99": percentile(lat, 99), "runs": reps, "tuned_config": best,
+            "plain_gteps": E / (pmed * 1e-3) / 1e9, "plain_ms_p50": pmed, "plain_ms_p99": percentile(plain_ms, 99),
+            "speedup_vs_plain": pmed / med, "labels_equal_plain": same,
+            "launch": "one cooperative persistent kernel, replayed from a CUDA graph"}
 
 
 def main(argv=None):

@@ -109,7 +109,8 @@ def _dev():
         lib.gg_er_dev.argtypes = [_u64, _u64, _u64, _u64, _ptr, _ptr]
         lib.gg_pairs_dev.argtypes = [_u64, _u64, _u64, _u64, _ptr, _ptr]
         lib.gg_grid_dev.argtypes = [_u64, _u32, _u32, _u64, _u32, _ptr, ctypes.POINTER(_u64), _ptr]
-        for f in (lib.gg_rmat_dev, lib.gg_er_dev, lib.gg_pairs_dev, lib.gg_grid_dev):
+        lib.gg_batch_fill_dev.argtypes = [_u64, _u32, _ptr, _u64, _ptr, _ptr]
+        for f in (lib.gg_rmat_dev, lib.gg_er_dev, lib.gg_pairs_dev, lib.gg_grid_dev, lib.gg_batch_fill_dev):
             f.restype = ctypes.c_int
         _dev_lib = lib
     return _dev_lib
@@ -248,6 +249,33 @@ def grid_dev(W: int, H: int, seed: int, p_thresh: int = P90, n_limit: int | None
     _check(_dev().gg_grid_dev(seed, W, H, n_limit, p_thresh, buf.data_ptr(), ctypes.byref(cnt),
                               _stream_ptr(stream)), "gg_grid_dev")
     return buf[: cnt.value].clone()
+
+
+@dataclass
+class DeviceBatch:
+    edges: "object"        # (E, 2) int32 torch tensor on the GPU, graph-local ids
+    vtx_off: "object"      # (G+1,) int64 torch tensor on the GPU
+    edge_off: "object"     # (G+1,) int64 torch tensor on the GPU
+    vtx_off_host: np.ndarray
+    edge_off_host: np.ndarray
+    kinds: np.ndarray
+
+    @property
+    def n_graphs(self) -> int:
+        return len(self.kinds)
+
+
+def batch_dev(n_graphs: int, seed: int, stream=None) -> DeviceBatch:
+    """The mixed batch generated in HBM (same bits as :func:`batch`)."""
+    import torch
+    kinds, vtx_off, edge_off = batch_plan(n_graphs, seed)
+    total = int(edge_off[-1])
+    eo = torch.from_numpy(edge_off.view(np.int64)).cuda()
+    vo = torch.from_numpy(vtx_off.view(np.int64)).cuda()
+    edges = torch.empty((total, 2), dtype=torch.int32, device="cuda")
+    _check(_dev().gg_batch_fill_dev(seed, n_graphs, eo.data_ptr(), total, edges.data_ptr(), _stream_ptr(stream)),
+           "gg_batch_fill_dev")
+    return DeviceBatch(edges, vo, eo, vtx_off, edge_off, kinds)
 
 
 # ---------------------------------------------------------------- workloads

@@ -89,6 +89,62 @@ __global__ void k_grid_fill(uint64_t gkey, uint32_t W, uint32_t H, uint64_t n_li
   }
 }
 
+// Mixed batch, G(n,m) and R-MAT graphs: one thread per edge of the
+// concatenated list; grid graphs are left to k_batch_grid.
+__global__ void k_batch_edges(uint64_t seed, uint32_t n_graphs, const uint64_t *edge_off, uint64_t total,
+                              uint2 *out) {
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < total;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t lo = 0, hi = n_graphs;  // largest g with edge_off[g] <= e
+    while (hi - lo > 1u) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (edge_off[mid] <= e) lo = mid; else hi = mid;
+    }
+    const gg_batch_shape sh = gg_batch_graph_shape(seed, lo);
+    if (sh.kind == GG_KIND_GRID) continue;
+    const uint64_t gk = gg_key(seed, GG_STREAM_BATCH_GRAPH + lo);
+    uint32_t u, v;
+    if (sh.kind == GG_KIND_RMAT)
+      gg_batch_rmat_edge(gk, sh.n_vertices, e - edge_off[lo], &u, &v);
+    else
+      gg_er_edge(gk, sh.n_vertices, e - edge_off[lo], &u, &v);
+    out[e] = make_uint2(u, v);
+  }
+}
+
+// Mixed batch, grid graphs: one block per graph scans the candidate slots in
+// order and writes the kept edges in that order.
+__global__ void k_batch_grid(uint64_t seed, uint32_t n_graphs, const uint64_t *edge_off, uint2 *out) {
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint64_t s_run;
+  for (uint32_t g = blockIdx.x; g < n_graphs; g += gridDim.x) {
+    const gg_batch_shape sh = gg_batch_graph_shape(seed, g);
+    if (sh.kind != GG_KIND_GRID) continue;
+    const uint64_t gk = gg_key(seed, GG_STREAM_BATCH_GRAPH + g);
+    const uint64_t slots = 2ULL * sh.grid_w * sh.grid_h;
+    if (threadIdx.x == 0) s_run = edge_off[g];
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (uint64_t base = 0; base < slots; base += blockDim.x) {
+      const uint64_t sl = base + threadIdx.x;
+      uint32_t u = 0, v = 0;
+      const int keep = sl < slots && gg_grid_slot(gk, sh.grid_w, sh.grid_h, sh.n_vertices, GG_P90, sl, &u, &v);
+      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+      if (lane == 0) s_warp[wid] = __popc(bal);
+      __syncthreads();
+      uint32_t before = 0, total = 0;
+      for (uint32_t w = 0; w < nw; ++w) {
+        if (w < wid) before += s_warp[w];
+        total += s_warp[w];
+      }
+      if (keep) out[s_run + before + __popc(bal & ((1u << lane) - 1u))] = make_uint2(u, v);
+      __syncthreads();
+      if (threadIdx.x == 0) s_run += total;
+      __syncthreads();
+    }
+  }
+}
+
 inline unsigned grid_for(uint64_t cnt) {
   uint64_t b = (cnt + 255) / 256;
   if (b > 152ULL * 64ULL) b = 152ULL * 64ULL;
@@ -153,3 +209,15 @@ GG_EXPORT int gg_grid_dev(uint64_t seed, uint32_t W, uint32_t H, uint64_t n_limi
   *count_out = total;
   return (int)err;
 }
+
+/* Edges of the mixed batch (graph-local ids) into out_dev, given the device
+ * copy of its edge offsets (uint64[n_graphs + 1], from gg_batch_plan). */
+GG_EXPORT int gg_batch_fill_dev(uint64_t seed, uint32_t n_graphs, const uint64_t *edge_off_dev,
+                                uint64_t total_edges, uint32_t *out_dev, cudaStream_t stream) {
+  if (n_graphs == 0) return 0;
+  uint2 *o = reinterpret_cast<uint2 *>(out_dev);
+  if (total_edges) k_batch_edges<<<grid_for(total_edges), 256, 0, stream>>>(seed, n_graphs, edge_off_dev, total_edges, o);
+  k_batch_grid<<<n_graphs < 4096u ? n_graphs : 4096u, 256, 0, stream>>>(seed, n_graphs, edge_off_dev, o);
+  return (int)cudaGetLastError();
+}
+

@@ -44,6 +44,16 @@ class cc_options(ctypes.Structure):
     ]
 
 
+class cc_batch_config(ctypes.Structure):
+    _fields_ = [
+        ("block_size", _i32), ("edges_per_thread", _i32), ("filter", _i32), ("tile_edges", _u32),
+        ("tile_vertices", _u32), ("reserved", _i32 * 3),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 class CCError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
@@ -84,6 +94,14 @@ def lib():
             "cc_device_bytes": (_i32, [_ptr, P(_u64)]),
             "cc_destroy": (None, [_ptr]),
             "cc_status_string": (ctypes.c_char_p, [_i32]),
+            "cc_batch_create": (_i32, [_u32, P(_ptr)]),
+            "cc_run_batched": (_i32, [_ptr, _u32, _ptr, _ptr, _ptr, _ptr, _ptr]),
+            "cc_batch_tune": (_i32, [_ptr, _u32, _ptr, _ptr, _ptr, _ptr, _ptr, P(cc_batch_config),
+                                     P(ctypes.c_float)]),
+            "cc_batch_set_config": (_i32, [_ptr, P(cc_batch_config)]),
+            "cc_batch_get_config": (_i32, [_ptr, P(cc_batch_config)]),
+            "cc_batch_sync": (_i32, [_ptr]),
+            "cc_batch_destroy": (None, [_ptr]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -305,3 +323,87 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ batched
+
+def cc_batch_create(max_graphs: int) -> int:
+    h = _ptr()
+    _check(lib().cc_batch_create(max_graphs, ctypes.byref(h)), "cc_batch_create")
+    return h.value
+
+
+def cc_run_batched(b: int, n_graphs: int, vtx_off, edge_off, edges, L_out, stream=None) -> None:
+    _check(lib().cc_run_batched(b, n_graphs, _addr(vtx_off), _addr(edge_off), _addr(edges), _addr(L_out),
+                                _stream(stream)), "cc_run_batched")
+
+
+def cc_batch_tune(b: int, n_graphs: int, vtx_off, edge_off, edges, L_out, stream=None):
+    """Autotune; returns (best config as a dict, its time in ms)."""
+    cfg = cc_batch_config()
+    ms = ctypes.c_float(0)
+    _check(lib().cc_batch_tune(b, n_graphs, _addr(vtx_off), _addr(edge_off), _addr(edges), _addr(L_out),
+                               _stream(stream), ctypes.byref(cfg), ctypes.byref(ms)), "cc_batch_tune")
+    return cfg.as_dict(), float(ms.value)
+
+
+def cc_batch_set_config(b: int, **cfg) -> None:
+    c = cc_batch_config()
+    _check(lib().cc_batch_get_config(b, ctypes.byref(c)), "cc_batch_get_config")
+    for k, v in cfg.items():
+        setattr(c, k, v)
+    _check(lib().cc_batch_set_config(b, ctypes.byref(c)), "cc_batch_set_config")
+
+
+def cc_batch_get_config(b: int) -> dict:
+    c = cc_batch_config()
+    _check(lib().cc_batch_get_config(b, ctypes.byref(c)), "cc_batch_get_config")
+    return c.as_dict()
+
+
+def cc_batch_sync(b: int) -> None:
+    _check(lib().cc_batch_sync(b), "cc_batch_sync")
+
+
+def cc_batch_sync_status(b: int) -> int:
+    return int(lib().cc_batch_sync(b))
+
+
+def cc_batch_destroy(b: int) -> None:
+    if b:
+        lib().cc_batch_destroy(b)
+
+
+class Batch:
+    """Owning wrapper of a cc_batch context."""
+
+    def __init__(self, max_graphs: int):
+        self.h = cc_batch_create(max_graphs)
+
+    def run(self, n_graphs, vtx_off, edge_off, edges, L_out, stream=None):
+        cc_run_batched(self.h, n_graphs, vtx_off, edge_off, edges, L_out, stream)
+        return L_out
+
+    def tune(self, n_graphs, vtx_off, edge_off, edges, L_out, stream=None):
+        return cc_batch_tune(self.h, n_graphs, vtx_off, edge_off, edges, L_out, stream)
+
+    def sync(self):
+        cc_batch_sync(self.h)
+
+    def close(self):
+        if self.h:
+            cc_batch_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -197,6 +197,67 @@ __device__ __forceinline__ void unite(uint32_t *S, uint32_t cu, uint32_t pu, uin
   }
 }
 
+// ------------------------------------------------------------ the warp ring
+//
+// Warp-level filter and compaction of the edge pass: after the parent loads,
+// an edge whose endpoints hold the same parent name is dropped (this covers
+// both endpoints already at name 0); survivors of the warp are appended to a
+// per-warp ring in shared memory (names and parent names of both endpoints),
+// and whenever 32 are queued the whole warp resolves them together, one per
+// lane, so root searches run in dense warps. At most 31 survivors are carried
+// between appends, so 64 entries suffice. All lanes of the warp must call
+// push() and drain() together.
+constexpr int kRing = 64;
+
+struct WarpRing {
+  uint32_t *cu, *pu, *cv, *pv;
+  uint32_t head, tail;
+  uint32_t lane, lt_mask;
+
+  // ring storage for this warp out of 4 * kRing words per warp
+  __device__ __forceinline__ void init(uint32_t *smem_words) {
+    const uint32_t wid = threadIdx.x >> 5;
+    cu = smem_words + wid * (4 * kRing);
+    pu = cu + kRing;
+    cv = cu + 2 * kRing;
+    pv = cu + 3 * kRing;
+    head = tail = 0;
+    lane = threadIdx.x & 31u;
+    lt_mask = (1u << lane) - 1u;
+  }
+
+  __device__ __forceinline__ void push(uint32_t *S, bool keep, uint32_t a, uint32_t pa, uint32_t b,
+                                       uint32_t pb) {
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+    if (keep) {
+      const uint32_t slot = (tail + __popc(bal & lt_mask)) & (kRing - 1);
+      cu[slot] = a;
+      pu[slot] = pa;
+      cv[slot] = b;
+      pv[slot] = pb;
+    }
+    tail += __popc(bal);
+    if (tail - head >= 32u) {
+      __syncwarp();
+      const uint32_t slot = (head + lane) & (kRing - 1);
+      const uint32_t sa = cu[slot], spa = pu[slot], sb = cv[slot], spb = pv[slot];
+      __syncwarp();
+      unite(S, sa, spa, sb, spb);
+      head += 32u;
+    }
+  }
+
+  __device__ __forceinline__ void drain(uint32_t *S) {
+    __syncwarp();
+    if (lane < tail - head) {
+      const uint32_t slot = (head + lane) & (kRing - 1);
+      unite(S, cu[slot], pu[slot], cv[slot], pv[slot]);
+    }
+    head = tail;
+    __syncwarp();
+  }
+};
+
 // ---------------------------------------------------------------- reductions
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x) {

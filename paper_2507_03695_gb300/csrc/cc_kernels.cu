@@ -123,14 +123,9 @@ __global__ void __launch_bounds__(512) k_edge_pass_direct(const uint4 *__restric
   }
 }
 
-// Filtered form: after the parent loads, edges whose endpoints hold the same
-// parent value are dropped (this covers both endpoints already at root value
-// 0); the survivors of the warp are appended to a per-warp ring in shared
-// memory, and whenever 32 are queued the whole warp resolves them together,
-// one per lane, so root searches run in dense warps. At most 31 survivors are
-// carried from one append to the next, so a 64-entry ring suffices.
-constexpr int kRing = 64;
-
+// Filtered form: the parent loads of a warp's edges feed the warp ring
+// (cc_device.cuh), which drops edges whose endpoints already share a parent
+// and resolves the survivors in dense warps.
 template <class F, int Q>
 __global__ void __launch_bounds__(512) k_edge_pass_filtered(const uint4 *__restrict__ e4,
                                                             uint64_t n_quads, const uint2 *head,
@@ -142,19 +137,16 @@ __global__ void __launch_bounds__(512) k_edge_pass_filtered(const uint4 *__restr
   const F fn = F::load(ctrl);
   uint32_t *const S = slots<F>(P);
   const uint64_t pol = policy_evict_first();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t *ru = ring_smem + wid * (4 * kRing);
-  uint32_t *rpu = ru + kRing, *rv = ru + 2 * kRing, *rpv = ru + 3 * kRing;
+  WarpRing ring;
+  ring.init(ring_smem);
   const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (t == 0 && head) single_edge(P, fn, head, n, ctrl);
   if (t == 1 % T && tail) single_edge(P, fn, tail, n, ctrl);
-  const uint32_t lt_mask = (1u << lane) - 1u;
-  uint32_t qh = 0, qt = 0;  // ring head and tail (warp-uniform)
   // the loop trip count must be warp-uniform: iterate on the warp's first lane
-  const uint64_t warp_t0 = t - (uint64_t)lane;
+  const uint64_t warp_t0 = t - (uint64_t)ring.lane;
   for (uint64_t wbase = warp_t0; wbase < n_quads; wbase += T * Q) {
-    const uint64_t base = wbase + (uint64_t)lane;
+    const uint64_t base = wbase + (uint64_t)ring.lane;
     uint4 e[Q];
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
@@ -176,32 +168,10 @@ __global__ void __launch_bounds__(512) k_edge_pass_filtered(const uint4 *__restr
       const uint32_t a = (k & 1) ? e[k >> 1].z : e[k >> 1].x;
       const uint32_t b = (k & 1) ? e[k >> 1].w : e[k >> 1].y;
       const uint32_t pa = p[2 * k], pb = p[2 * k + 1];
-      const bool keep = pa != pb;
-      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
-      if (keep) {
-        const uint32_t slot = (qt + __popc(bal & lt_mask)) & (kRing - 1);
-        ru[slot] = fn.f(a);
-        rpu[slot] = pa;
-        rv[slot] = fn.f(b);
-        rpv[slot] = pb;
-      }
-      qt += __popc(bal);
-      if (qt - qh >= 32u) {
-        __syncwarp();
-        const uint32_t slot = (qh + lane) & (kRing - 1);
-        const uint32_t sa = ru[slot], spa = rpu[slot], sb = rv[slot], spb = rpv[slot];
-        __syncwarp();
-        unite(S, sa, spa, sb, spb);
-        qh += 32u;
-      }
+      ring.push(S, pa != pb, fn.f(a), pa, fn.f(b), pb);
     }
   }
-  // drain
-  __syncwarp();
-  if (lane < (int)(qt - qh)) {
-    const uint32_t slot = (qh + lane) & (kRing - 1);
-    unite(S, ru[slot], rpu[slot], rv[slot], rpv[slot]);
-  }
+  ring.drain(S);
 }
 
 __global__ void __launch_bounds__(256) k_validate(const uint4 *__restrict__ e4, uint64_t n_quads,

@@ -87,8 +87,31 @@ def golden_for(w: graphgen.Workload) -> dict:
     }
 
 
+def golden_batch(n_graphs: int, seed: int) -> dict:
+    t0 = time.time()
+    b = graphgen.batch(n_graphs, seed)
+    L = oracle.batch_min_labels(b.edges, b.vtx_off, b.edge_off)
+    return {
+        "workload": f"batch{n_graphs}", "n_graphs": n_graphs, "seed": seed,
+        "n_vertices": int(b.vtx_off[-1]), "n_edges": int(b.edge_off[-1]),
+        "edges_sha256": sha(b.edges), "labels_sha256": sha(L),
+        "num_components": int(np.count_nonzero(L == (np.arange(len(L), dtype=np.int64)
+                                                     - np.repeat(b.vtx_off[:-1].astype(np.int64),
+                                                                 np.diff(b.vtx_off.astype(np.int64)))))),
+        "oracle_seconds": round(time.time() - t0, 1),
+    }
+
+
 def main(names):
     for name in names:
+        if name == "batch4096":
+            g = golden_batch(graphgen.BATCH_GRAPHS, graphgen.BATCH_SEED)
+            path = os.path.join(HERE, f"{name}.json")
+            with open(path, "w") as f:
+                json.dump(g, f, indent=1)
+                f.write("\n")
+            print(path, g["num_components"], g["oracle_seconds"], "s")
+            continue
         w = graphgen.WORKLOADS[name]
         g = golden_for(w)
         path = os.path.join(HERE, f"{name}.json")
