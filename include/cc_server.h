@@ -1,0 +1,121 @@
+/*
+ * cc_server.h - a serving runtime for many resident graphs (C ABI;
+ * conventions as in cc.h).
+ *
+ * Requests arrive at any time: new whole graphs, edge-insert batches,
+ * batches of connected(u, v) queries, label snapshots, and graph drops.
+ * Each resident graph keeps its parent array P live on the device, so an
+ * insert is one hooking pass over the new edges only (JT processes edges in
+ * any order and needs no re-initialisation; Section III treats received
+ * pairs the same way), and a query batch is two root searches per pair on
+ * the live P (u and v are connected iff their roots agree, Section II).
+ *
+ * Execution. Insert and query batches are cut into tiles and run by a
+ * persistent executor kernel that stays resident on a fixed share of every
+ * SM, takes tiles from a ring in mapped host memory and signals each request's
+ * completion through mapped memory; every wait in it is bounded, and it
+ * leaves after an idle period (it is relaunched on demand). New graphs (root
+ * selection, init, hooking pass, flatten) and snapshots (flatten) run on a
+ * side stream beside the executor. A host scheduler thread admits requests
+ * as memory and ordering allow (continuous batching): requests that arrive
+ * while others run start as soon as they may, and their tiles interleave
+ * with the running ones on the device.
+ *
+ * Ordering. Per graph, requests take effect in submission order: a query or
+ * snapshot sees exactly the inserts submitted before it for that graph.
+ * Consecutive inserts run together, and so do consecutive reads (queries
+ * and snapshots).
+ *
+ * Memory. The server owns one device arena of hbm_budget_bytes, allocated at
+ * creation; graphs are placed in it by first fit and a new graph waits until
+ * enough memory is free (drops release it). No cudaMalloc or cudaFree happens
+ * while serving. Request buffers (edges, pairs, outputs) are the caller's
+ * device memory: their contents must be complete on the device when the
+ * request is submitted (the server's streams do not wait for the caller's),
+ * and they must stay valid until the request completes. Outputs are complete
+ * in device memory when the ticket completes.
+ */
+#ifndef CC_SERVER_H
+#define CC_SERVER_H
+
+#include "cc.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cc_server cc_server;
+
+typedef enum cc_request_kind {
+  CC_REQ_NEW_GRAPH = 1,  /* n_vertices, edges_dev/n_edges; labels_dev optional */
+  CC_REQ_INSERT = 2,     /* graph, edges_dev/n_edges; rejected whole if an id is out of range */
+  CC_REQ_QUERY = 3,      /* graph, pairs_dev/n_pairs -> out_dev (uint8 per pair) */
+  CC_REQ_SNAPSHOT = 4,   /* graph -> labels_dev (uint32[n_vertices], label space of the config) */
+  CC_REQ_DROP_GRAPH = 5  /* graph: frees its memory after the requests before it */
+} cc_request_kind;
+
+typedef struct cc_request {
+  int32_t kind;               /* cc_request_kind */
+  uint32_t graph;             /* target graph (not used by CC_REQ_NEW_GRAPH) */
+  uint64_t n_vertices;        /* CC_REQ_NEW_GRAPH */
+  const uint32_t *edges_dev;  /* COO pairs, 8-byte aligned */
+  uint64_t n_edges;
+  const uint32_t *pairs_dev;  /* query pairs, 8-byte aligned */
+  uint64_t n_pairs;
+  uint8_t *out_dev;           /* query results */
+  uint32_t *labels_dev;       /* snapshot labels (or NEW_GRAPH labels when not NULL) */
+} cc_request;
+
+typedef struct cc_server_config {
+  uint64_t hbm_budget_bytes;       /* device arena for resident graphs (required)   */
+  uint32_t max_graphs;             /* graph ids 0 .. max_graphs-1; 0 = 1024          */
+  uint32_t executor_blocks_per_sm; /* resident executor blocks (256 threads); 0 = 2  */
+  uint32_t tile_edges;             /* edges (or pairs) per executor tile; 0 = 16384  */
+  uint32_t idle_timeout_us;        /* executor leaves after this much idleness; 0 = 20000 */
+  int32_t mode;                    /* cc_root_mode of new graphs; default CC_ROOT_MAXDEG */
+  int32_t label_space;             /* cc_label_space of snapshots; default MIN_ID   */
+  int32_t reserved[4];             /* must be zero */
+} cc_server_config;
+
+typedef struct cc_server_stats {
+  uint64_t submitted, completed, failed;
+  uint64_t resident_graphs, arena_bytes_used, arena_bytes;
+  uint64_t executor_launches, tiles_run;
+} cc_server_stats;
+
+CC_API void cc_server_config_init(cc_server_config *cfg);
+
+/* Creates the server on the current device: allocates the arena and the
+ * executor's rings, starts the scheduler thread. */
+CC_API cc_status cc_server_create(const cc_server_config *cfg, cc_server **out);
+
+/* Queues a request and returns its ticket at once. For CC_REQ_NEW_GRAPH the
+ * new graph's id is available immediately through cc_server_result_graph and
+ * may be used by requests submitted right after. Host-side argument errors
+ * are returned here (CC_ERR_INVALID_ARGUMENT, CC_ERR_TOO_LARGE when a graph
+ * can never fit the arena); device-side ones through the ticket. */
+CC_API cc_status cc_server_submit(cc_server *s, const cc_request *req, uint64_t *ticket);
+
+/* CC_OK with *result = the request's status when it has completed,
+ * CC_ERR_NOT_READY otherwise. */
+CC_API cc_status cc_server_poll(cc_server *s, uint64_t ticket, cc_status *result);
+
+/* Waits up to timeout_ns for the ticket; CC_ERR_TIMEOUT if it has not
+ * completed by then. */
+CC_API cc_status cc_server_wait(cc_server *s, uint64_t ticket, uint64_t timeout_ns, cc_status *result);
+
+CC_API cc_status cc_server_result_graph(cc_server *s, uint64_t ticket, uint32_t *graph);
+
+/* Submission-to-completion time of a completed ticket (host clock). */
+CC_API cc_status cc_server_latency_ns(cc_server *s, uint64_t ticket, uint64_t *ns);
+
+CC_API cc_status cc_server_get_stats(cc_server *s, cc_server_stats *st);
+
+/* Waits for every request, stops the executor and frees everything. */
+CC_API void cc_server_destroy(cc_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CC_SERVER_H */

@@ -54,6 +54,29 @@ class cc_batch_config(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class cc_request(ctypes.Structure):
+    _fields_ = [
+        ("kind", _i32), ("graph", _u32), ("n_vertices", _u64), ("edges_dev", _ptr), ("n_edges", _u64),
+        ("pairs_dev", _ptr), ("n_pairs", _u64), ("out_dev", _ptr), ("labels_dev", _ptr),
+    ]
+
+
+class cc_server_config(ctypes.Structure):
+    _fields_ = [
+        ("hbm_budget_bytes", _u64), ("max_graphs", _u32), ("executor_blocks_per_sm", _u32),
+        ("tile_edges", _u32), ("idle_timeout_us", _u32), ("mode", _i32), ("label_space", _i32),
+        ("reserved", _i32 * 4),
+    ]
+
+
+class cc_server_stats(ctypes.Structure):
+    _fields_ = [(k, _u64) for k in ("submitted", "completed", "failed", "resident_graphs", "arena_bytes_used",
+                                    "arena_bytes", "executor_launches", "tiles_run")]
+
+
+CC_REQ_NEW_GRAPH, CC_REQ_INSERT, CC_REQ_QUERY, CC_REQ_SNAPSHOT, CC_REQ_DROP_GRAPH = 1, 2, 3, 4, 5
+
+
 class CCError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
@@ -102,6 +125,15 @@ def lib():
             "cc_batch_get_config": (_i32, [_ptr, P(cc_batch_config)]),
             "cc_batch_sync": (_i32, [_ptr]),
             "cc_batch_destroy": (None, [_ptr]),
+            "cc_server_config_init": (None, [P(cc_server_config)]),
+            "cc_server_create": (_i32, [P(cc_server_config), P(_ptr)]),
+            "cc_server_submit": (_i32, [_ptr, P(cc_request), P(_u64)]),
+            "cc_server_poll": (_i32, [_ptr, _u64, P(_i32)]),
+            "cc_server_wait": (_i32, [_ptr, _u64, _u64, P(_i32)]),
+            "cc_server_result_graph": (_i32, [_ptr, _u64, P(_u32)]),
+            "cc_server_latency_ns": (_i32, [_ptr, _u64, P(_u64)]),
+            "cc_server_get_stats": (_i32, [_ptr, P(cc_server_stats)]),
+            "cc_server_destroy": (None, [_ptr]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -394,6 +426,135 @@ class Batch:
         if self.h:
             cc_batch_destroy(self.h)
             self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ serving
+
+def cc_server_config_init(**overrides) -> cc_server_config:
+    c = cc_server_config()
+    lib().cc_server_config_init(ctypes.byref(c))
+    for k, v in overrides.items():
+        setattr(c, k, v)
+    return c
+
+
+def cc_server_create(cfg: cc_server_config) -> int:
+    h = _ptr()
+    _check(lib().cc_server_create(ctypes.byref(cfg), ctypes.byref(h)), "cc_server_create")
+    return h.value
+
+
+def cc_server_submit(srv: int, req: cc_request) -> int:
+    t = _u64(0)
+    _check(lib().cc_server_submit(srv, ctypes.byref(req), ctypes.byref(t)), "cc_server_submit")
+    return int(t.value)
+
+
+def cc_server_poll(srv: int, ticket: int):
+    """None while running, else the request's status."""
+    r = _i32(0)
+    st = lib().cc_server_poll(srv, ticket, ctypes.byref(r))
+    if st == CC_ERR_NOT_READY:
+        return None
+    _check(st, "cc_server_poll")
+    return int(r.value)
+
+
+def cc_server_wait(srv: int, ticket: int, timeout_s: float = 60.0) -> int:
+    r = _i32(0)
+    _check(lib().cc_server_wait(srv, ticket, int(timeout_s * 1e9), ctypes.byref(r)), "cc_server_wait")
+    return int(r.value)
+
+
+def cc_server_result_graph(srv: int, ticket: int) -> int:
+    g = _u32(0)
+    _check(lib().cc_server_result_graph(srv, ticket, ctypes.byref(g)), "cc_server_result_graph")
+    return int(g.value)
+
+
+def cc_server_latency_ns(srv: int, ticket: int) -> int:
+    v = _u64(0)
+    _check(lib().cc_server_latency_ns(srv, ticket, ctypes.byref(v)), "cc_server_latency_ns")
+    return int(v.value)
+
+
+def cc_server_get_stats(srv: int) -> dict:
+    st = cc_server_stats()
+    _check(lib().cc_server_get_stats(srv, ctypes.byref(st)), "cc_server_get_stats")
+    return {k: int(getattr(st, k)) for k, _ in st._fields_}
+
+
+def cc_server_destroy(srv: int) -> None:
+    if srv:
+        lib().cc_server_destroy(srv)
+
+
+class Server:
+    """Owning wrapper of a cc_server. Request buffers (torch tensors) are kept
+    referenced until the request is waited for."""
+
+    def __init__(self, hbm_budget_bytes: int, **cfg):
+        self.h = cc_server_create(cc_server_config_init(hbm_budget_bytes=hbm_budget_bytes, **cfg))
+        self._keep = {}
+
+    def _submit(self, keep, **fields) -> int:
+        req = cc_request()
+        for k, v in fields.items():
+            setattr(req, k, v)
+        t = cc_server_submit(self.h, req)
+        self._keep[t] = keep
+        return t
+
+    def new_graph(self, n_vertices: int, edges, labels=None) -> tuple[int, int]:
+        t = self._submit((edges, labels), kind=CC_REQ_NEW_GRAPH, n_vertices=n_vertices,
+                         edges_dev=_addr(edges), n_edges=_count_pairs(edges, None), labels_dev=_addr(labels))
+        return t, cc_server_result_graph(self.h, t)
+
+    def insert(self, graph: int, edges) -> int:
+        return self._submit((edges,), kind=CC_REQ_INSERT, graph=graph, edges_dev=_addr(edges),
+                            n_edges=_count_pairs(edges, None))
+
+    def query(self, graph: int, pairs, out) -> int:
+        return self._submit((pairs, out), kind=CC_REQ_QUERY, graph=graph, pairs_dev=_addr(pairs),
+                            n_pairs=_count_pairs(pairs, None), out_dev=_addr(out))
+
+    def snapshot(self, graph: int, labels) -> int:
+        return self._submit((labels,), kind=CC_REQ_SNAPSHOT, graph=graph, labels_dev=_addr(labels))
+
+    def drop(self, graph: int) -> int:
+        return self._submit((), kind=CC_REQ_DROP_GRAPH, graph=graph)
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> int:
+        st = cc_server_wait(self.h, ticket, timeout_s)
+        self._keep.pop(ticket, None)
+        return st
+
+    def poll(self, ticket: int):
+        return cc_server_poll(self.h, ticket)
+
+    def latency_ns(self, ticket: int) -> int:
+        return cc_server_latency_ns(self.h, ticket)
+
+    def stats(self) -> dict:
+        return cc_server_get_stats(self.h)
+
+    def close(self):
+        if self.h:
+            cc_server_destroy(self.h)
+            self.h = 0
+            self._keep.clear()
 
     def __enter__(self):
         return self

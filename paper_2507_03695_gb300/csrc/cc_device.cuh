@@ -97,6 +97,19 @@ __device__ __forceinline__ uint32_t ldP_strong(const uint32_t *p) {
   return r;
 }
 
+// L2-only parent load (no L1 allocation): for long-lived kernels whose L1
+// may hold lines from before the latest writes of other kernels.
+__device__ __forceinline__ uint32_t ldP_cg(const uint32_t *p) {
+  uint32_t r;
+  asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(r) : "l"(p) : "memory");
+  return r;
+}
+
+template <bool kCG>
+__device__ __forceinline__ uint32_t ldP_t(const uint32_t *p) {
+  return kCG ? ldP_cg(p) : ldP(p);
+}
+
 __device__ __forceinline__ void stP(uint32_t *p, uint32_t v) {
   asm volatile("st.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -154,6 +167,7 @@ __device__ __forceinline__ uint32_t root_name(uint32_t *S, uint32_t c, uint32_t 
 // original endpoints). Any moment at which both sides show the same parent
 // name proves a common tree and ends the edge, which includes the case of
 // both endpoints already holding 0.
+template <bool kCG = false>
 __device__ __forceinline__ void unite(uint32_t *S, uint32_t cu, uint32_t pu, uint32_t cv, uint32_t pv) {
   if (pu != pv) CC_STAT(0);
   while (true) {
@@ -164,7 +178,7 @@ __device__ __forceinline__ void unite(uint32_t *S, uint32_t cu, uint32_t pu, uin
         break;
       }
       CC_STAT(1);
-      const uint32_t pw = ldP(S + pu);
+      const uint32_t pw = ldP_t<kCG>(S + pu);
       if (pw != pu) stP(S + cu, pw);
       cu = pu;
       pu = pw;
@@ -176,7 +190,7 @@ __device__ __forceinline__ void unite(uint32_t *S, uint32_t cu, uint32_t pu, uin
         break;
       }
       CC_STAT(1);
-      const uint32_t pw = ldP(S + pv);
+      const uint32_t pw = ldP_t<kCG>(S + pv);
       if (pw != pv) stP(S + cv, pw);
       cv = pv;
       pv = pw;
@@ -226,6 +240,7 @@ struct WarpRing {
     lt_mask = (1u << lane) - 1u;
   }
 
+  template <bool kCG = false>
   __device__ __forceinline__ void push(uint32_t *S, bool keep, uint32_t a, uint32_t pa, uint32_t b,
                                        uint32_t pb) {
     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
@@ -242,16 +257,17 @@ struct WarpRing {
       const uint32_t slot = (head + lane) & (kRing - 1);
       const uint32_t sa = cu[slot], spa = pu[slot], sb = cv[slot], spb = pv[slot];
       __syncwarp();
-      unite(S, sa, spa, sb, spb);
+      unite<kCG>(S, sa, spa, sb, spb);
       head += 32u;
     }
   }
 
+  template <bool kCG = false>
   __device__ __forceinline__ void drain(uint32_t *S) {
     __syncwarp();
     if (lane < tail - head) {
       const uint32_t slot = (head + lane) & (kRing - 1);
-      unite(S, cu[slot], pu[slot], cv[slot], pv[slot]);
+      unite<kCG>(S, cu[slot], pu[slot], cv[slot], pv[slot]);
     }
     head = tail;
     __syncwarp();

@@ -1,0 +1,183 @@
+"""The serving runtime (include/cc_server.h) against the CPU oracle.
+
+The central check: a mixed stream of requests over several graphs is
+submitted all at once (new graphs, inserts of many sizes, query batches,
+snapshots, drops) so that their work overlaps on the device; every query
+answer and snapshot must equal both the oracle on that graph's edges so far
+and the same request run alone (each graph's requests submitted one at a
+time, waiting for each)."""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+cc = pytest.importorskip("paper_2507_03695_gb300")
+
+GB = 1 << 30
+
+
+def dev(e):
+    return torch.from_numpy(np.ascontiguousarray(e, dtype=np.uint32).view(np.int32)).cuda()
+
+
+def make_script(seed):
+    """A request script: list of (graph_key, kind, payload)."""
+    rng = np.random.default_rng(seed)
+    script = []
+    graphs = {}
+    for k in range(4):
+        scale = int(rng.integers(10, 15))
+        n = 1 << scale
+        e = graphgen.rmat(scale, n * 4, 100 + k, scramble=True)
+        graphs[k] = n
+        script.append((k, "new", e))
+    for i in range(60):
+        k = int(rng.integers(0, 4))
+        n = graphs[k]
+        kind = rng.choice(["insert", "query", "snapshot"], p=[0.45, 0.45, 0.10])
+        if kind == "insert":
+            size = int(10 ** rng.uniform(0, 5.3))  # 1 .. 200K edges (1 to 13 tiles)
+            script.append((k, "insert", graphgen.pairs(n, size, 7, tag=i)))
+        elif kind == "query":
+            script.append((k, "query", graphgen.pairs(n, 3000, 8, tag=i)))
+        else:
+            script.append((k, "snapshot", None))
+    script.append((2, "drop", None))
+    script.append((4, "new", graphgen.er(5000, 9000, 55)))
+    graphs[4] = 5000
+    script.append((4, "query", graphgen.pairs(5000, 2000, 9, tag=999)))
+    script.append((4, "snapshot", None))
+    return script, graphs
+
+
+def expected(script, graphs):
+    """Oracle answers for every query / snapshot, in script order."""
+    seen = {k: [] for k in graphs}
+    out = []
+    for k, kind, payload in script:
+        if kind in ("new", "insert"):
+            seen[k].append(payload)
+            out.append(None)
+        elif kind in ("query", "snapshot"):
+            e = np.concatenate(seen[k]) if seen[k] else np.zeros((0, 2), np.uint32)
+            L = oracle.min_labels(graphs[k], e)
+            out.append(oracle.connected(L, payload) if kind == "query" else L)
+        else:
+            out.append(None)
+    return out
+
+
+def run_script(server, script, graphs, one_at_a_time):
+    gid = {}
+    tickets, results = [], []
+    for k, kind, payload in script:
+        res = None
+        if kind == "new":
+            t, gid[k] = server.new_graph(graphs[k], dev(payload))
+        elif kind == "insert":
+            t = server.insert(gid[k], dev(payload))
+        elif kind == "query":
+            res = torch.full((len(payload),), 7, dtype=torch.uint8, device="cuda")
+            q = dev(payload)
+            torch.cuda.synchronize()  # buffers complete before submission
+            t = server.query(gid[k], q, res)
+        elif kind == "snapshot":
+            res = torch.full((graphs[k],), -1, dtype=torch.int32, device="cuda")
+            torch.cuda.synchronize()
+            t = server.snapshot(gid[k], res)
+        else:
+            t = server.drop(gid[k])
+        tickets.append(t)
+        results.append(res)
+        if one_at_a_time:
+            assert server.wait(t) == cc.CC_OK
+    for t in tickets:
+        assert server.wait(t) == cc.CC_OK
+    torch.cuda.synchronize()
+    return [None if r is None else r.cpu().numpy() for r in results], tickets
+
+
+@pytest.mark.parametrize("mode", [cc.CC_ROOT_MAXDEG, cc.CC_ROOT_IDENTITY])
+def test_mixed_stream_equals_alone_and_oracle(mode):
+    script, graphs = make_script(3)
+    want = expected(script, graphs)
+    with cc.Server(2 * GB, mode=mode, tile_edges=16384) as s:
+        mixed, tickets = run_script(s, script, graphs, one_at_a_time=False)
+        st = s.stats()
+        assert st["completed"] == len(script) and st["failed"] == 0
+    with cc.Server(2 * GB, mode=mode, tile_edges=16384) as s:
+        alone, _ = run_script(s, script, graphs, one_at_a_time=True)
+    for i, (k, kind, _) in enumerate(script):
+        if kind == "query":
+            np.testing.assert_array_equal(mixed[i], want[i])
+            np.testing.assert_array_equal(alone[i], want[i])
+        elif kind == "snapshot":
+            np.testing.assert_array_equal(mixed[i].view(np.uint32), want[i])
+            np.testing.assert_array_equal(alone[i].view(np.uint32), want[i])
+
+
+def test_insert_with_bad_id_is_rejected_whole():
+    n = 1 << 12
+    base = graphgen.rmat(12, 1 << 14, 3, scramble=True)
+    with cc.Server(GB, tile_edges=1024) as s:
+        t, g = s.new_graph(n, dev(base))
+        assert s.wait(t) == cc.CC_OK
+        L0 = torch.empty(n, dtype=torch.int32, device="cuda")
+        assert s.wait(s.snapshot(g, L0)) == cc.CC_OK
+        for size in (500, 20000):  # one tile, and many tiles (validated first)
+            bad = graphgen.pairs(n, size, 4, tag=size)
+            bad[size // 2, 0] = n + 5
+            assert s.wait(s.insert(g, dev(bad))) == cc.CC_ERR_OUT_OF_RANGE
+            L1 = torch.empty(n, dtype=torch.int32, device="cuda")
+            assert s.wait(s.snapshot(g, L1)) == cc.CC_OK
+            assert torch.equal(L0, L1)
+        q = dev(np.array([[0, 1], [2, n]], np.uint32))
+        out = torch.empty(2, dtype=torch.uint8, device="cuda")
+        assert s.wait(s.query(g, q, out)) == cc.CC_ERR_OUT_OF_RANGE
+
+
+def test_admission_waits_for_memory_and_drop_frees_it():
+    n = 1 << 20  # ~8.2 MiB per graph under f = R (P + histogram + scratch)
+    e = graphgen.rmat(20, 1 << 21, 5, scramble=True)
+    with cc.Server(12 << 20) as s:
+        ta, ga = s.new_graph(n, dev(e))
+        tb, gb = s.new_graph(n, dev(e))  # cannot fit until graph a is dropped
+        assert s.wait(ta) == cc.CC_OK
+        assert s.poll(tb) is None
+        L = torch.empty(n, dtype=torch.int32, device="cuda")
+        assert s.wait(s.snapshot(ga, L)) == cc.CC_OK
+        td = s.drop(ga)
+        assert s.wait(td) == cc.CC_OK
+        assert s.wait(tb) == cc.CC_OK
+        L2 = torch.empty(n, dtype=torch.int32, device="cuda")
+        assert s.wait(s.snapshot(gb, L2)) == cc.CC_OK
+        want = oracle.min_labels(n, e)
+        np.testing.assert_array_equal(L.cpu().numpy().view(np.uint32), want)
+        np.testing.assert_array_equal(L2.cpu().numpy().view(np.uint32), want)
+        with pytest.raises(cc.CCError):
+            s.new_graph(1 << 30, dev(e))  # can never fit the arena
+
+
+def test_executor_relaunches_after_idle_and_errors_at_submit():
+    n = 4096
+    e = graphgen.er(n, 5000, 1)
+    with cc.Server(GB, idle_timeout_us=1000) as s:
+        t, g = s.new_graph(n, dev(e))
+        assert s.wait(t) == cc.CC_OK
+        out = torch.empty(100, dtype=torch.uint8, device="cuda")
+        q = graphgen.pairs(n, 100, 2)
+        assert s.wait(s.query(g, dev(q), out)) == cc.CC_OK
+        import time
+        time.sleep(0.05)  # the executor leaves after 1 ms of idleness
+        assert s.wait(s.insert(g, dev(graphgen.pairs(n, 3000, 3)))) == cc.CC_OK
+        assert s.wait(s.query(g, dev(q), out)) == cc.CC_OK
+        assert s.stats()["executor_launches"] >= 2
+        want = oracle.connected(oracle.min_labels(n, np.concatenate([e, graphgen.pairs(n, 3000, 3)])), q)
+        np.testing.assert_array_equal(out.cpu().numpy(), want)
+        with pytest.raises(cc.CCError):
+            s.insert(g + 17, dev(e))  # unknown graph
+        assert s.latency_ns(t) > 0
