@@ -62,6 +62,9 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batched-graphs", type=int, default=4096)
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serving-requests", type=int, default=2000,
+                   help="requests per arrival rate (the full configuration uses 20000)")
     p.add_argument("--cpu-fraction", type=float, default=1 / 8,
                    help="share of each graph's edges in the CPU oracle sample")
     return p.parse_args(argv)
@@ -375,6 +378,12 @@ def run_ours(args):
     for h in handles:
         h.close()
     batched = None if args.no_batched else bench_batched(args, cc, graphgen, torch, stream)
+    serving = None
+    if not args.no_serving:
+        try:
+            serving = bench_serving(args, cc, graphgen, torch)
+        except Exception as exc:  # report, do not hang the benchmark
+            serving = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0:
         line = {
             "metric": "GTEPS", "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
@@ -399,6 +408,7 @@ def run_ours(args):
             "gteps_without_root_select": E_total / (sum(p[4] - p[0] for p in phase_ms) * 1e-3) / 1e9,
             "e2e": e2e,
             "batched": batched,
+            "serving": serving,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": int(launches),
@@ -484,6 +494,138 @@ def bench_batched(args, cc, graphgen, torch, stream):
             "plain_gteps": E / (pmed * 1e-3) / 1e9, "plain_ms_p50": pmed, "plain_ms_p99": percentile(plain_ms, 99),
             "speedup_vs_plain": pmed / med, "labels_equal_plain": same,
             "launch": "one cooperative persistent kernel, replayed from a CUDA graph"}
+
+
+def bench_serving(args, cc, graphgen, torch):
+    """Poisson arrivals on a resident R-MAT scale-26 graph: insert batches,
+    query batches, snapshots and new graphs (dropped again a few requests
+    later) through the serving runtime, against the plain path that runs
+    each request alone, in arrival order, with the single-graph calls."""
+    import time
+
+    import numpy as np
+    w = graphgen.RMAT26
+    n = w.n_vertices
+    dev = torch.device("cuda")
+    e_res = w.device_edges()
+    R = args.serving_requests
+    rng = np.random.default_rng(6)
+    kinds = rng.choice(4, size=R, p=[0.45, 0.45, 0.05, 0.05])  # insert, query, snapshot, new graph
+    sizes = np.minimum((10 ** rng.uniform(3, 7, size=R)).astype(np.int64), 10 ** 7)
+    POOL = 1 << 26
+    pool = graphgen.pairs_dev(n, POOL, 61)
+    offs = rng.integers(0, POOL - 10 ** 7, size=R)
+    qpool = graphgen.pairs_dev(n, 1 << 22, 62)
+    qoffs = rng.integers(0, (1 << 22) - 10 ** 4, size=R)
+    scales = rng.integers(12, 23, size=R)
+    new_edges = {int(sc): graphgen.rmat_dev(int(sc), 16 << int(sc), 70 + int(sc)) for sc in np.unique(scales)}
+    qout = torch.empty(10 ** 4 * 64, dtype=torch.uint8, device=dev)
+    snap = [torch.empty(n, dtype=torch.int32, device=dev) for _ in range(4)]
+    torch.cuda.synchronize()
+
+    def payload(i):
+        k = int(kinds[i])
+        if k == 0:
+            return pool[int(offs[i]): int(offs[i]) + int(sizes[i])]
+        if k == 1:
+            return qpool[int(qoffs[i]): int(qoffs[i]) + 10 ** 4]
+        if k == 3:
+            return new_edges[int(scales[i])]
+        return None
+
+    # ---- plain path: every request alone, synchronously, in order
+    stream = torch.cuda.current_stream()
+    base = cc.Graph(n)
+    base.run(e_res, None)
+    base.sync()
+    service = np.zeros(R)
+    for i in range(R):
+        k = int(kinds[i])
+        t0 = time.perf_counter()
+        if k == 0:
+            base.insert(payload(i))
+            base.sync()
+        elif k == 1:
+            base.connected(payload(i), qout[i % 64 * 10 ** 4: (i % 64 + 1) * 10 ** 4])
+            base.sync()
+        elif k == 2:
+            base.labels(snap[0])
+            base.sync()
+        else:
+            sc = int(scales[i])
+            with cc.Graph(1 << sc) as g2:
+                g2.run(payload(i), None)
+                g2.sync()
+        service[i] = time.perf_counter() - t0
+    base.close()
+    capacity = R / service.sum()
+    edges_total = int(sizes[kinds == 0].sum() + sum(16 << int(scales[i]) for i in range(R) if kinds[i] == 3))
+
+    results = []
+    for rho in (0.25, 0.5, 0.9, "burst"):
+        if rho == "burst":  # every request at once: saturated throughput
+            lam = float("inf")
+            arrivals = np.zeros(R)
+        else:
+            lam = rho * capacity
+            arrivals = np.cumsum(rng.exponential(1.0 / lam, size=R))
+        # plain FIFO server with the measured service times
+        done = np.zeros(R)
+        t_free = 0.0
+        for i in range(R):
+            t_free = max(arrivals[i], t_free) + service[i]
+            done[i] = t_free
+        plain_lat = (done - arrivals) * 1e3
+        # the serving runtime
+        srv = cc.Server(24 << 30, idle_timeout_us=200000)
+        t, gid = srv.new_graph(n, e_res)
+        if srv.wait(t, 120) != cc.CC_OK:
+            raise RuntimeError("resident graph admission failed")
+        tickets, lag, drops = [], np.zeros(R), []
+        pending_drop = []
+        t0 = time.perf_counter()
+        for i in range(R):
+            target = t0 + arrivals[i]
+            while time.perf_counter() < target:
+                pass
+            lag[i] = time.perf_counter() - target
+            k = int(kinds[i])
+            if k == 0:
+                tk = srv.insert(gid, payload(i))
+            elif k == 1:
+                tk = srv.query(gid, payload(i), qout[i % 64 * 10 ** 4: (i % 64 + 1) * 10 ** 4])
+            elif k == 2:
+                tk = srv.snapshot(gid, snap[i % 4])
+            else:
+                tk, g2 = srv.new_graph(1 << int(scales[i]), payload(i))
+                pending_drop.append((i + 5, g2))
+            tickets.append(tk)
+            while pending_drop and pending_drop[0][0] <= i:
+                drops.append(srv.drop(pending_drop.pop(0)[1]))
+        for _, g2 in pending_drop:
+            drops.append(srv.drop(g2))
+        for tk in tickets + drops:
+            if srv.wait(tk, 120) != cc.CC_OK:
+                raise RuntimeError(f"serving request {tk} failed")
+        makespan = time.perf_counter() - t0
+        lat = np.array([lag[i] * 1e3 + srv.latency_ns(tk) / 1e6 for i, tk in enumerate(tickets)])
+        st = srv.stats()
+        srv.close()
+        results.append({
+            "load": rho, "arrival_rate_per_s": None if rho == "burst" else lam,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "plain_p50_ms": float(np.percentile(plain_lat, 50)), "plain_p99_ms": float(np.percentile(plain_lat, 99)),
+            "throughput_req_per_s": R / makespan, "plain_throughput_req_per_s": R / max(done[-1], arrivals[-1]),
+            "edges_per_s": edges_total / makespan, "plain_edges_per_s": edges_total / max(done[-1], arrivals[-1]),
+            "executor_launches": st["executor_launches"], "side_drains": st["side_drains"],
+        })
+    del pool, qpool, new_edges, snap, e_res
+    torch.cuda.empty_cache()
+    return {"resident": w.name, "requests_per_rate": R,
+            "mix": "45% inserts (10^3..10^7 uniform pairs), 45% queries (10^4 pairs), 5% snapshots, "
+                   "5% new R-MAT graphs scale 12..22 (each dropped 5 requests later)",
+            "plain_capacity_req_per_s": capacity, "rates": results,
+            "latency": "arrival to completion, host clock"}
 
 
 def main(argv=None):

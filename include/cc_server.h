@@ -16,10 +16,13 @@
  * completion through mapped memory; every wait in it is bounded, and it
  * leaves after an idle period (it is relaunched on demand). New graphs (root
  * selection, init, hooking pass, flatten) and snapshots (flatten) run on a
- * side stream beside the executor. A host scheduler thread admits requests
- * as memory and ordering allow (continuous batching): requests that arrive
- * while others run start as soon as they may, and their tiles interleave
- * with the running ones on the device.
+ * side stream beside the executor; the executor asks for the largest shared
+ * memory carveout so that they fit beside it, and side work that still waits
+ * longer than 20 ms makes the host drain the executor (it finishes every
+ * published tile, leaves, and is relaunched). A host scheduler thread admits
+ * requests as memory and ordering allow (continuous batching): requests that
+ * arrive while others run start as soon as they may, and their tiles
+ * interleave with the running ones on the device.
  *
  * Ordering. Per graph, requests take effect in submission order: a query or
  * snapshot sees exactly the inserts submitted before it for that graph.
@@ -34,6 +37,14 @@
  * request is submitted (the server's streams do not wait for the caller's),
  * and they must stay valid until the request completes. Outputs are complete
  * in device memory when the ticket completes.
+ *
+ * Module loading. The executor stays resident while requests are in flight.
+ * With CUDA's lazy module loading, the first launch of any kernel in the
+ * process can wait until the device is idle, so cc_server_create runs every
+ * kernel the server uses once before the executor starts. Other code that
+ * launches kernels for the first time while a server is busy may wait until
+ * it goes idle; such processes should load eagerly
+ * (CUDA_MODULE_LOADING=EAGER) or warm those kernels up before serving.
  */
 #ifndef CC_SERVER_H
 #define CC_SERVER_H
@@ -69,8 +80,10 @@ typedef struct cc_request {
 typedef struct cc_server_config {
   uint64_t hbm_budget_bytes;       /* device arena for resident graphs (required)   */
   uint32_t max_graphs;             /* graph ids 0 .. max_graphs-1; 0 = 1024          */
-  uint32_t executor_blocks_per_sm; /* resident executor blocks (256 threads); 0 = 2  */
-  uint32_t tile_edges;             /* edges (or pairs) per executor tile; 0 = 16384  */
+  uint32_t executor_blocks_per_sm; /* resident executor blocks (256 threads); 0 = 3, which
+                                      leaves room on every SM for the side-stream kernels */
+  uint32_t tile_edges;             /* largest executor tile in edges or pairs; 0 = 16384;
+                                      requests are cut finer to spread over all blocks */
   uint32_t idle_timeout_us;        /* executor leaves after this much idleness; 0 = 20000 */
   int32_t mode;                    /* cc_root_mode of new graphs; default CC_ROOT_MAXDEG */
   int32_t label_space;             /* cc_label_space of snapshots; default MIN_ID   */
@@ -81,6 +94,7 @@ typedef struct cc_server_stats {
   uint64_t submitted, completed, failed;
   uint64_t resident_graphs, arena_bytes_used, arena_bytes;
   uint64_t executor_launches, tiles_run;
+  uint64_t side_drains;  /* executor drains forced by starved side-stream work */
 } cc_server_stats;
 
 CC_API void cc_server_config_init(cc_server_config *cfg);
@@ -111,7 +125,8 @@ CC_API cc_status cc_server_latency_ns(cc_server *s, uint64_t ticket, uint64_t *n
 
 CC_API cc_status cc_server_get_stats(cc_server *s, cc_server_stats *st);
 
-/* Waits for every request, stops the executor and frees everything. */
+/* Waits for the requests still running (at most about 10 s), stops the
+ * executor and frees everything. */
 CC_API void cc_server_destroy(cc_server *s);
 
 #ifdef __cplusplus

@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <stddef.h>
 #include <stdint.h>
 
@@ -61,6 +63,20 @@ int num_sms();
 inline unsigned clamp_grid(uint64_t want, uint64_t cap) {
   if (want == 0) want = 1;
   return (unsigned)(want < cap ? want : cap);
+}
+
+// Sets a kernel attribute once per device. Setting a function attribute can
+// make the host wait for the device, so it is done on first use only, never
+// per launch; `done` is the call site's per-device bit mask.
+inline cudaError_t ensure_func_attr(const void *kernel, cudaFuncAttribute attr, int value,
+                                    std::atomic<unsigned long long> &done) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, attr, value);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
 }
 
 // Blocks that fit on the whole GPU at once for this kernel and block size.

@@ -406,8 +406,8 @@ cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, u
   if (filter) {
     const size_t smem = (size_t)(block / 32) * 4 * kRing * sizeof(uint32_t);
     const void *k = (const void *)k_edge_pass_filtered<F, Q>;
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static_assert((1024 / 32) * 4 * kRing * sizeof(uint32_t) <= 48 * 1024,
+                  "the ring of a 1024-thread block fits the default dynamic shared memory limit");
     const unsigned g = clamp_grid((e.n_quads + per_block - 1) / per_block, persistent_cap(k, block, smem));
     k_edge_pass_filtered<F, Q><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
                                                       check_reject ? 1 : 0); note_launch();

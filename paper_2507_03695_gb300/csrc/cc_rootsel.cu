@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(512) k_degree_certify(const uint4 *__restrict_
 // The proof (one block): D = best candidate degree; bound = the largest
 // bucket total left after removing the candidates' own occurrences. D > bound
 // means every non-candidate has degree < D.
-__global__ void __launch_bounds__(1024) k_certify_decide(const CertScratch *cs, Ctrl *ctrl) {
+__global__ void __launch_bounds__(256) k_certify_decide(const CertScratch *cs, Ctrl *ctrl) {
   extern __shared__ unsigned long long rem[];  // kCertBuckets
   for (uint32_t b = threadIdx.x; b < kCertBuckets; b += blockDim.x) rem[b] = cs->bucket[b];
   __syncthreads();
@@ -351,14 +351,19 @@ cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges
   k_build_table<<<1, 256, 0, s>>>(ctrl, cs);
   note_launch();
   // 3. the exact pass in shared memory
-  cudaFuncSetAttribute((const void *)k_degree_certify, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCertSmem);
-  cudaFuncSetAttribute((const void *)k_certify_decide, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(kCertBuckets * sizeof(unsigned long long)));
+  static std::atomic<unsigned long long> smem_set_certify{0}, smem_set_decide{0};
+  if ((err = ensure_func_attr((const void *)k_degree_certify, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kCertSmem, smem_set_certify)) != cudaSuccess)
+    return err;
+  if ((err = ensure_func_attr((const void *)k_certify_decide, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(kCertBuckets * sizeof(unsigned long long)), smem_set_decide)) != cudaSuccess)
+    return err;
   const unsigned gcert = clamp_grid((e.n_quads + 511) / 512, persistent_cap((const void *)k_degree_certify, 512, kCertSmem));
   k_degree_certify<<<gcert, 512, kCertSmem, s>>>(e.quads, e.n_quads, e.head, e.tail, n, cs, ctrl);
   note_launch();
   // 4. the proof
-  k_certify_decide<<<1, 1024, kCertBuckets * sizeof(unsigned long long), s>>>(cs, ctrl);
+  // one small block, so it fits beside resident kernels (the serving executor)
+  k_certify_decide<<<1, 256, kCertBuckets * sizeof(unsigned long long), s>>>(cs, ctrl);
   note_launch();
   // 5. full histogram, skipped when certified
   const uint32_t *skip = &ctrl->cert;

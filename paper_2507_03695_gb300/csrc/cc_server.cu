@@ -3,14 +3,18 @@
 // kernel that runs insert and query tiles on the live parent arrays of
 // resident graphs.
 //
-// Host <-> device protocol (all in mapped pinned host memory):
+// Host <-> device protocol (mapped pinned host memory unless noted):
 //   ring[]     work items written by the host; `published` counts them;
+//   taken      (device memory) items claimed so far: a block claims the next
+//              index with one fetch-and-add and waits, bounded, until the
+//              host has published it;
 //   done_seq[] per request slot: the executor stores the item's sequence
 //              number after the request's last tile (release, system scope);
-//   err[]      per request slot: an out-of-range id was seen;
-//   stop       asks the executor to leave.
-// In device memory: `taken` (items claimed by executor blocks) and, per slot,
-// `finished` (tiles done; the last finisher resets it and signals).
+//   err[]      per request slot: 1 = an out-of-range id, 2 = a gated wait
+//              expired;
+//   stop       the host asks the executor to leave (after an idle period,
+//              when every published item has been processed; the host then
+//              sets taken back to published before the next launch).
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -20,6 +24,7 @@
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -35,10 +40,19 @@ namespace srv {
 constexpr uint32_t kRingCap = 1u << 16;  // work items in the ring
 constexpr uint32_t kSlots = 4096;        // requests with executor tiles in flight
 enum : uint32_t { kItemEdges = 1, kItemValidate = 2, kItemApply = 3, kItemQuery = 4 };
+constexpr unsigned long long kGateTimeoutNs = 2000000000ULL;  // gated apply tile: 2 s
+constexpr unsigned long long kWaitLimitNs = 30000000000ULL;   // waiting for an item: 30 s
+// Side-stream requests in flight at once: bounds the launches queued on the
+// side stream so that a launch never blocks the scheduler thread.
+constexpr size_t kMaxSideRunning = 16;
+// A side-stream request still unfinished this long while the executor runs
+// makes the host drain the executor once, so that kernels that cannot fit
+// beside it get the SMs.
+constexpr uint64_t kSideStarveNs = 20ULL * 1000 * 1000;
 
 struct alignas(16) WorkItem {
-  uint32_t kind, slot, seq, n_tiles;
-  uint32_t rf, m, n, pad;
+  uint32_t kind, slot, seq, n_tiles;  // n_tiles: tiles that count towards completion
+  uint32_t rf, m, n, n_gate;          // n_gate: validate tiles an apply tile waits for
   uint64_t P, src, begin, end, out;
   uint64_t pad2;
 };
@@ -47,7 +61,8 @@ static_assert(sizeof(WorkItem) == 80, "work item layout");
 struct HostShared {
   unsigned long long published;
   unsigned int stop;
-  unsigned int pad[13];
+  unsigned int exec_err;  // an executor wait expired (the host stopped answering)
+  unsigned int pad[12];
   WorkItem ring[kRingCap];
   unsigned int done_seq[kSlots];
   unsigned int err[kSlots];
@@ -55,7 +70,8 @@ struct HostShared {
 
 struct DevShared {
   unsigned long long taken;
-  unsigned int finished[kSlots];
+  unsigned int finished[kSlots];   // completion-counting tiles done
+  unsigned int validated[kSlots];  // validate tiles done
 };
 
 __device__ __forceinline__ unsigned long long now_ns() {
@@ -76,14 +92,23 @@ __device__ __forceinline__ unsigned int ld_volatile_sys_u32(const unsigned int *
   return v;
 }
 
-__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p) {
-  unsigned long long v;
-  asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
 __device__ __forceinline__ void st_release_sys_u32(unsigned int *p, unsigned int v) {
   asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// A work item from mapped host memory: five 16-byte loads in flight at once.
+__device__ __forceinline__ void load_item(const WorkItem *src, WorkItem *dst) {
+  const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+  uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+  uint4 v[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
+    asm volatile("ld.volatile.global.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v[k].x), "=r"(v[k].y), "=r"(v[k].z), "=r"(v[k].w)
+                 : "l"(s4 + k)
+                 : "memory");
+#pragma unroll
+  for (int k = 0; k < 5; ++k) d4[k] = v[k];
 }
 
 // Request buffers may be rewritten by the client between requests while the
@@ -100,47 +125,68 @@ __device__ __forceinline__ uint32_t name_of(uint32_t x, uint32_t rf, uint32_t m)
   return rf ? (x == m ? 0u : x + 1u) : x;
 }
 
-// The persistent executor: blocks take work items one at a time, run them,
-// and count the request's finished tiles. A block leaves when `stop` is set
-// or when no item arrives for idle_ns.
-__global__ void __launch_bounds__(256) k_executor(HostShared *hs, DevShared *ds, unsigned long long idle_ns) {
+// Read-only root name of a vertex: walk parents (L2 loads) until a root or
+// the permanent root 0.
+__device__ __forceinline__ void walk_step(const uint32_t *S, uint32_t &c, uint32_t &p, bool &done) {
+  if (!done) {
+    if (p == c || p == 0u) {
+      if (p == 0u) c = 0u;
+      done = true;
+    } else {
+      c = p;
+      p = ldP_cg(S + c);
+    }
+  }
+}
+
+constexpr int kEpt = 4;  // elements per thread per round
+
+// The persistent executor: each block claims the next item index, waits
+// (bounded) until the host has published it, runs it, and counts the
+// request's finished tiles. Blocks leave when the host sets `stop`.
+__global__ void __launch_bounds__(256) k_executor(HostShared *hs, DevShared *ds) {
   __shared__ WorkItem it;
   __shared__ int s_leave;
-  __shared__ unsigned int s_bad;
+  __shared__ unsigned int s_bad, s_skip;
   __shared__ uint32_t ring_smem[8 * 4 * kRing];
   while (true) {
     if (threadIdx.x == 0) {
-      int leave = 1;
+      int leave = 0;
+      const unsigned long long t = atomicAdd(&ds->taken, 1ULL);
       const unsigned long long t0 = now_ns();
-      while (true) {
-        const unsigned long long pub = ld_acquire_sys_u64(&hs->published);
-        const unsigned long long t = ld_volatile_u64(&ds->taken);
-        if (t < pub) {
-          if (atomicCAS(&ds->taken, t, t + 1ULL) == t) {
-            const volatile WorkItem *src = &hs->ring[t % kRingCap];
-            it.kind = src->kind;
-            it.slot = src->slot;
-            it.seq = src->seq;
-            it.n_tiles = src->n_tiles;
-            it.rf = src->rf;
-            it.m = src->m;
-            it.n = src->n;
-            it.P = src->P;
-            it.src = src->src;
-            it.begin = src->begin;
-            it.end = src->end;
-            it.out = src->out;
-            leave = 0;
-            break;
-          }
-          continue;  // another block took it: look again at once
+      unsigned int backoff = 32;
+      while (ld_acquire_sys_u64(&hs->published) <= t) {
+        if (ld_volatile_sys_u32(&hs->stop)) {
+          leave = 1;
+          break;
         }
-        if (ld_volatile_sys_u32(&hs->stop)) break;
-        if (now_ns() - t0 > idle_ns) break;  // bounded idle wait
-        __nanosleep(256);
+        if (now_ns() - t0 > kWaitLimitNs) {  // the host stopped answering
+          *(volatile unsigned int *)&hs->exec_err = 1u;
+          leave = 1;
+          break;
+        }
+        __nanosleep(backoff);
+        if (backoff < 4096) backoff <<= 1;
       }
+      if (!leave) load_item(&hs->ring[t % kRingCap], &it);
       s_leave = leave;
       s_bad = 0u;
+      s_skip = 0u;
+      // a gated apply tile waits (bounded) until every validate tile of its
+      // request has finished; they were all claimed before it (ring order)
+      if (!leave && it.kind == kItemApply && it.n_gate) {
+        const unsigned long long g0 = now_ns();
+        while (ld_volatile_sys_u32(&ds->validated[it.slot]) < it.n_gate) {
+          if (now_ns() - g0 > kGateTimeoutNs) {
+            s_skip = 1u;
+            s_bad = 2u;  // reported as a timeout
+            break;
+          }
+          __nanosleep(128);
+        }
+        __threadfence();
+        if (ld_volatile_sys_u32(&hs->err[it.slot])) s_skip = 1u;  // rejected: apply nothing
+      }
     }
     __syncthreads();
     if (s_leave) return;
@@ -155,65 +201,99 @@ __global__ void __launch_bounds__(256) k_executor(HostShared *hs, DevShared *ds,
         const uint2 e = ld_pair_cg(src + i);
         bad |= e.x >= n || e.y >= n;
       }
-      if (bad) s_bad = 1u;
+      if (bad) atomicMax(&s_bad, 1u);
     }
     __syncthreads();
-    if ((it.kind == kItemEdges && !s_bad) || it.kind == kItemApply) {
+    if ((it.kind == kItemEdges && !s_bad) || (it.kind == kItemApply && !s_skip)) {
       WarpRing ring;
       ring.init(ring_smem);
-      // warp-uniform rounds over the tile
-      for (uint64_t r0 = it.begin; r0 < it.end; r0 += blockDim.x) {
-        const uint64_t i = r0 + threadIdx.x;
-        uint32_t a = 0, b = 0, pa = 0, pb = 0;
-        if (i < it.end) {
-          const uint2 e = ld_pair_cg(src + i);
-          if (e.x < n && e.y < n) {
-            a = name_of(e.x, rf, m);
-            b = name_of(e.y, rf, m);
-            pa = ldP_cg(P + e.x);
-            pb = ldP_cg(P + e.y);
+      // warp-uniform rounds of kEpt edges per thread, all parent loads issued together
+      for (uint64_t r0 = it.begin; r0 < it.end; r0 += (uint64_t)blockDim.x * kEpt) {
+        uint32_t a[kEpt], b[kEpt], pa[kEpt], pb[kEpt];
+#pragma unroll
+        for (int j = 0; j < kEpt; ++j) {
+          const uint64_t i = r0 + (uint64_t)j * blockDim.x + threadIdx.x;
+          a[j] = b[j] = pa[j] = pb[j] = 0u;
+          if (i < it.end) {
+            const uint2 e = ld_pair_cg(src + i);
+            if (e.x < n && e.y < n) {
+              a[j] = e.x;
+              b[j] = e.y;
+              pa[j] = 1u;
+            }
           }
         }
-        ring.push<true>(S, pa != pb, a, pa, b, pb);
+#pragma unroll
+        for (int j = 0; j < kEpt; ++j) {
+          if (pa[j]) {
+            pa[j] = ldP_cg(P + a[j]);
+            pb[j] = ldP_cg(P + b[j]);
+            a[j] = name_of(a[j], rf, m);
+            b[j] = name_of(b[j], rf, m);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kEpt; ++j) ring.push<true>(S, pa[j] != pb[j], a[j], pa[j], b[j], pb[j]);
       }
       ring.drain<true>(S);
     } else if (it.kind == kItemQuery) {
       uint8_t *out = reinterpret_cast<uint8_t *>(it.out);
       bool bad = false;
-      for (uint64_t i = it.begin + threadIdx.x; i < it.end; i += blockDim.x) {
-        const uint2 q = ld_pair_cg(src + i);
-        uint8_t r = 0;
-        if (q.x >= n || q.y >= n) {
-          bad = true;
-        } else {
-          // read-only walks: queries never write P
-          uint32_t cu = name_of(q.x, rf, m), pu = ldP_cg(P + q.x);
-          while (pu != cu && pu != 0u) {
-            cu = pu;
-            pu = ldP_cg(S + pu);
+      for (uint64_t r0 = it.begin; r0 < it.end; r0 += (uint64_t)blockDim.x * kEpt) {
+        // kEpt queries per thread, their 2 * kEpt read-only walks in lock step
+        uint32_t c[2 * kEpt], p[2 * kEpt];
+        bool done[2 * kEpt], valid[kEpt];
+#pragma unroll
+        for (int j = 0; j < kEpt; ++j) {
+          const uint64_t i = r0 + (uint64_t)j * blockDim.x + threadIdx.x;
+          done[2 * j] = done[2 * j + 1] = true;
+          valid[j] = false;
+          c[2 * j] = c[2 * j + 1] = p[2 * j] = p[2 * j + 1] = 0u;
+          if (i < it.end) {
+            const uint2 q = ld_pair_cg(src + i);
+            if (q.x >= n || q.y >= n) {
+              bad = true;
+            } else {
+              c[2 * j] = name_of(q.x, rf, m);
+              c[2 * j + 1] = name_of(q.y, rf, m);
+              p[2 * j] = ldP_cg(P + q.x);
+              p[2 * j + 1] = ldP_cg(P + q.y);
+              done[2 * j] = done[2 * j + 1] = false;
+              valid[j] = true;
+            }
           }
-          if (pu == 0u) cu = 0u;
-          uint32_t cv = name_of(q.y, rf, m), pv = ldP_cg(P + q.y);
-          while (pv != cv && pv != 0u) {
-            cv = pv;
-            pv = ldP_cg(S + pv);
-          }
-          if (pv == 0u) cv = 0u;
-          r = cu == cv;
         }
-        out[i] = r;
+        bool any = true;
+        while (any) {  // ends: names strictly decrease along parents
+          any = false;
+#pragma unroll
+          for (int k = 0; k < 2 * kEpt; ++k) {
+            walk_step(S, c[k], p[k], done[k]);
+            any |= !done[k];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kEpt; ++j) {
+          const uint64_t i = r0 + (uint64_t)j * blockDim.x + threadIdx.x;
+          if (i < it.end) out[i] = (uint8_t)(valid[j] && c[2 * j] == c[2 * j + 1]);
+        }
       }
-      if (bad) s_bad = 1u;
+      if (bad) atomicMax(&s_bad, 1u);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      if (s_bad) *(volatile unsigned int *)&hs->err[it.slot] = 1u;
-      __threadfence();
-      const unsigned int prev = atomicAdd(&ds->finished[it.slot], 1u);
-      if (prev + 1u == it.n_tiles) {
-        ds->finished[it.slot] = 0u;
-        __threadfence_system();
-        st_release_sys_u32(&hs->done_seq[it.slot], it.seq);
+      if (s_bad) *(volatile unsigned int *)&hs->err[it.slot] = s_bad;
+      __threadfence_system();
+      if (it.kind == kItemValidate) {
+        atomicAdd(&ds->validated[it.slot], 1u);
+      } else {
+        const unsigned int prev = atomicAdd(&ds->finished[it.slot], 1u);
+        if (prev + 1u == it.n_tiles) {
+          ds->finished[it.slot] = 0u;
+          ds->validated[it.slot] = 0u;
+          __threadfence_system();
+          st_release_sys_u32(&hs->done_seq[it.slot], it.seq);
+        }
       }
     }
     __syncthreads();
@@ -293,14 +373,15 @@ enum GroupClass { kIdle = 0, kWriters = 1, kReaders = 2, kExclusive = 3 };
 struct Req {
   cc_request r{};
   uint32_t graph = 0;
-  uint64_t t_submit = 0, t_done = 0;
-  int state = kQueued;
-  cc_status result = CC_OK;
-  // executor bookkeeping
+  uint64_t ticket = 0;
+  uint64_t t_submit = 0;
+  std::atomic<uint64_t> t_done{0};
+  std::atomic<int> state{kQueued};
+  std::atomic<int> result{CC_OK};
+  // scheduler-thread bookkeeping
   uint32_t slot = UINT32_MAX, seq = 0, n_tiles = 0;
-  int phase = 0;  // inserts: 1 validating, 2 applying
-  // side-stream bookkeeping
   cudaEvent_t ev = nullptr;
+  uint64_t t_side = 0;  // side-stream work issued (or the executor last drained for it) at
 };
 
 struct GraphState {
@@ -312,7 +393,7 @@ struct GraphState {
   cc::CertScratch *cert = nullptr;
   cc::Ctrl *ctrl = nullptr;
   uint32_t m = 0;
-  std::deque<uint64_t> fifo;
+  std::deque<Req *> fifo;
   int group = kIdle;
   int active = 0;
 };
@@ -323,123 +404,151 @@ struct cc_server {
   cc_server_config cfg{};
   int device = 0;
   char *arena_base = nullptr;
-  Arena arena;
   HostShared *hs = nullptr;  // host view of the mapped block
   HostShared *hs_dev = nullptr;
   DevShared *ds = nullptr;
   cudaStream_t exec_stream = nullptr, side_stream = nullptr;
   cudaEvent_t exec_ev = nullptr;
-  bool exec_running = false;
-  uint32_t *side_words = nullptr;  // pinned: per-graph m and error words read back after a run
-  // shared with client threads (mu)
-  std::mutex mu;
-  std::condition_variable cv;
-  std::vector<Req> reqs;          // ticket t is reqs[t - 1]
-  std::deque<uint64_t> inbox;
-  std::vector<int> id_state;      // 0 free, 1 assigned, 2 dropping
+  uint32_t *side_words = nullptr;  // pinned: per-graph m and error word read back after admission
+  // submission side (sub_mu): request objects, the inbox, graph ids
+  std::mutex sub_mu;
+  std::condition_variable sub_cv;
+  std::vector<std::unique_ptr<Req>> reqs;  // ticket t is reqs[t - 1]
+  std::vector<Req *> inbox;
+  std::vector<int> id_state;  // 0 free, 1 assigned, 2 dropping
   std::vector<uint32_t> free_ids;
-  cc_server_stats stats{};
   bool quit = false;
+  // completion side (done_mu): waiters
+  std::mutex done_mu;
+  std::condition_variable done_cv;
+  std::atomic<uint64_t> submitted{0}, completed{0}, failed{0}, executor_launches{0}, tiles_run{0};
+  std::atomic<uint64_t> arena_used{0}, resident{0}, side_drains{0};
   // scheduler-thread state
+  Arena arena;
   std::vector<GraphState> graphs;
   std::vector<uint32_t> free_slots;
-  std::vector<uint64_t> slot_ticket;
+  std::vector<Req *> slot_req;
+  std::vector<uint32_t> slot_gen;  // per-slot sequence: every publication takes a new one
   uint64_t in_flight_items = 0;
-  std::vector<uint64_t> side_running;  // tickets with side-stream work in flight
+  std::vector<Req *> side_running;  // requests with side-stream work in flight
+  bool exec_running = false, exec_stopping = false;
+  uint64_t idle_since = 0;
   std::thread thread;
 };
 
 namespace {
 
-uint64_t graph_bytes(const cc_server *s, uint64_t n, uint64_t n_edges, bool rf) {
+uint64_t graph_bytes(uint64_t n, uint64_t n_edges, bool rf) {
   size_t b = align256((size_t)((n + 3) / 4 * 4) * 4) + align256(sizeof(cc::Ctrl));
   if (rf) b += align256((size_t)n * (n_edges >= (1ULL << 31) ? 8 : 4)) + align256(sizeof(cc::CertScratch));
-  (void)s;
   return b;
 }
 
-void complete(cc_server *s, uint64_t t, cc_status st) {
-  Req &r = s->reqs[t - 1];
-  r.state = kDone;
-  r.result = st;
-  r.t_done = host_ns();
-  s->stats.completed++;
-  if (st != CC_OK) s->stats.failed++;
+void complete(cc_server *s, Req *r, cc_status st) {
+  r->result.store(st);
+  r->t_done.store(host_ns());
+  r->state.store(kDone, std::memory_order_release);
+  s->completed++;
+  if (st != CC_OK) s->failed++;
 }
 
-void publish_tiles(cc_server *s, Req &r, uint32_t kind, uint64_t count, const uint32_t *src,
-                   const GraphState &g) {
-  uint64_t tile = s->cfg.tile_edges;
-  const uint64_t min_tile = (count + (cc::srv::kRingCap / 4) - 1) / (cc::srv::kRingCap / 4);
-  if (tile < min_tile) tile = min_tile;
-  const uint32_t n_tiles = (uint32_t)((count + tile - 1) / tile);
-  r.n_tiles = n_tiles;
-  r.seq++;
-  s->hs->err[r.slot] = 0u;
-  unsigned long long pub = s->hs->published;
-  for (uint32_t i = 0; i < n_tiles; ++i) {
+// Elements per tile: enough tiles to spread a request over every executor
+// block twice, at least at_least, at most the configured tile size, and few
+// enough to fit the ring.
+uint64_t tile_for(const cc_server *s, uint64_t count, uint64_t at_least) {
+  const uint64_t blocks = (uint64_t)cc::num_sms() * s->cfg.executor_blocks_per_sm;
+  uint64_t t = (count + 2 * blocks - 1) / (2 * blocks);
+  t = (t + 255) / 256 * 256;
+  if (t < at_least) t = at_least;
+  if (t > s->cfg.tile_edges) t = s->cfg.tile_edges;
+  const uint64_t min_tile = (count + (cc::srv::kRingCap / 8) - 1) / (cc::srv::kRingCap / 8);
+  return t < min_tile ? min_tile : t;
+}
+
+uint64_t n_tiles_of(uint64_t count, uint64_t tile) { return (count + tile - 1) / tile; }
+
+void write_tiles(cc_server *s, const Req &r, uint32_t kind, uint64_t count, const uint32_t *src,
+                 const GraphState &g, uint64_t tile, uint32_t n_count, uint32_t n_gate,
+                 unsigned long long &pub) {
+  const uint64_t nt = n_tiles_of(count, tile);
+  for (uint64_t i = 0; i < nt; ++i) {
     WorkItem &w = s->hs->ring[(pub + i) % cc::srv::kRingCap];
     w.kind = kind;
     w.slot = r.slot;
     w.seq = r.seq;
-    w.n_tiles = n_tiles;
+    w.n_tiles = n_count;
     w.rf = g.rf ? 1u : 0u;
     w.m = g.m;
     w.n = (uint32_t)g.n;
+    w.n_gate = n_gate;
     w.P = (uint64_t)(uintptr_t)g.P;
     w.src = (uint64_t)(uintptr_t)src;
-    w.begin = (uint64_t)i * tile;
+    w.begin = i * tile;
     w.end = w.begin + tile < count ? w.begin + tile : count;
     w.out = (uint64_t)(uintptr_t)r.r.out_dev;
   }
-  std::atomic_thread_fence(std::memory_order_seq_cst);
-  *(volatile unsigned long long *)&s->hs->published = pub + n_tiles;
-  s->in_flight_items += n_tiles;
-  s->stats.tiles_run += n_tiles;
+  pub += nt;
 }
 
-uint64_t tiles_needed(const cc_server *s, uint64_t count) {
-  uint64_t tile = s->cfg.tile_edges;
-  const uint64_t min_tile = (count + (cc::srv::kRingCap / 4) - 1) / (cc::srv::kRingCap / 4);
-  if (tile < min_tile) tile = min_tile;
-  return (count + tile - 1) / tile;
-}
-
-// Starts an insert or query on the executor; false when no slot or ring room.
-bool start_exec(cc_server *s, uint64_t t, GraphState &g) {
-  Req &r = s->reqs[t - 1];
-  const bool insert = r.r.kind == CC_REQ_INSERT;
-  const uint64_t count = insert ? r.r.n_edges : r.r.n_pairs;
+// Starts an insert or query on the executor; false when it must wait (no
+// slot, no ring room, or the executor is being stopped). An insert of one
+// tile validates and applies itself; a longer one publishes validate tiles
+// and then apply tiles that wait on the device until the validation has
+// finished (and apply nothing if it failed).
+bool start_exec(cc_server *s, Req *r, GraphState &g) {
+  const bool insert = r->r.kind == CC_REQ_INSERT;
+  const uint64_t count = insert ? r->r.n_edges : r->r.n_pairs;
   if (count == 0) {
-    complete(s, t, CC_OK);
+    complete(s, r, CC_OK);
     return true;
   }
-  const uint64_t need = tiles_needed(s, count);
+  if (s->exec_stopping) return false;
+  const uint64_t tile = tile_for(s, count, 256);
+  const uint64_t n_work = n_tiles_of(count, tile);
+  const uint64_t vtile = insert && n_work > 1 ? tile_for(s, count, 16384) : 0;
+  const uint64_t n_val = vtile ? n_tiles_of(count, vtile) : 0;
+  const uint64_t need = n_work + n_val;
   if (s->free_slots.empty() || s->in_flight_items + need > cc::srv::kRingCap / 2) return false;
-  r.slot = s->free_slots.back();
+  r->slot = s->free_slots.back();
   s->free_slots.pop_back();
-  s->slot_ticket[r.slot] = t;
-  r.state = kRunning;
-  if (insert) {
-    r.phase = need == 1 ? 2 : 1;  // a single tile validates and applies itself
-    publish_tiles(s, r, need == 1 ? cc::srv::kItemEdges : cc::srv::kItemValidate, count, r.r.edges_dev, g);
+  s->slot_req[r->slot] = r;
+  r->state.store(kRunning);
+  // a fresh sequence number for this slot, never equal to one a previous
+  // user of the slot left in done_seq
+  r->seq = ++s->slot_gen[r->slot];
+  if (r->seq == 0u) r->seq = ++s->slot_gen[r->slot];
+  s->hs->err[r->slot] = 0u;
+  r->n_tiles = (uint32_t)need;
+  unsigned long long pub = s->hs->published;
+  if (!insert) {
+    write_tiles(s, *r, cc::srv::kItemQuery, count, r->r.pairs_dev, g, tile, (uint32_t)n_work, 0, pub);
+  } else if (n_work == 1) {
+    write_tiles(s, *r, cc::srv::kItemEdges, count, r->r.edges_dev, g, tile, 1, 0, pub);
   } else {
-    publish_tiles(s, r, cc::srv::kItemQuery, count, r.r.pairs_dev, g);
+    write_tiles(s, *r, cc::srv::kItemValidate, count, r->r.edges_dev, g, vtile, (uint32_t)n_work, 0, pub);
+    write_tiles(s, *r, cc::srv::kItemApply, count, r->r.edges_dev, g, tile, (uint32_t)n_work, (uint32_t)n_val,
+                pub);
   }
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  *(volatile unsigned long long *)&s->hs->published = pub;
+  s->in_flight_items += need;
+  s->tiles_run += need;
   return true;
 }
 
 // Root selection (f = R), init, hooking pass and flatten of a new graph on
 // the side stream; m and the error word are copied back to pinned memory.
-bool start_new_graph(cc_server *s, uint64_t t, GraphState &g) {
-  Req &r = s->reqs[t - 1];
+bool start_new_graph(cc_server *s, Req *r, GraphState &g) {
+  if (s->side_running.size() >= cc::srv::kMaxSideRunning) return false;
   const bool rf = s->cfg.mode == CC_ROOT_MAXDEG;
-  const uint64_t bytes = graph_bytes(s, r.r.n_vertices, r.r.n_edges, rf);
+  const uint64_t bytes = graph_bytes(r->r.n_vertices, r->r.n_edges, rf);
   uint64_t off = 0;
   if (!s->arena.alloc(bytes, &off)) return false;  // wait for memory
+  s->arena_used = s->arena.used();
   g.live = true;
+  s->resident++;
   g.rf = rf;
-  g.n = r.r.n_vertices;
+  g.n = r->r.n_vertices;
   g.off = off;
   g.bytes = bytes;
   char *p = s->arena_base + off;
@@ -447,58 +556,60 @@ bool start_new_graph(cc_server *s, uint64_t t, GraphState &g) {
   p += align256((size_t)((g.n + 3) / 4 * 4) * 4);
   g.ctrl = reinterpret_cast<cc::Ctrl *>(p);
   p += align256(sizeof(cc::Ctrl));
-  const bool wide = r.r.n_edges >= (1ULL << 31);
+  const bool wide = r->r.n_edges >= (1ULL << 31);
   if (rf) {
     g.cnt = p;
     p += align256((size_t)g.n * (wide ? 8 : 4));
     g.cert = reinterpret_cast<cc::CertScratch *>(p);
   }
-  r.state = kRunning;
+  r->state.store(kRunning);
   cudaStream_t ss = s->side_stream;
   cudaError_t e = cudaMemsetAsync(g.ctrl, 0, sizeof(cc::Ctrl), ss);
   const uint32_t n = (uint32_t)g.n;
-  const cc::EdgeSpan span = cc::split_edges(r.r.edges_dev, r.r.n_edges);
+  const cc::EdgeSpan span = cc::split_edges(r->r.edges_dev, r->r.n_edges);
   int m_src = cc::kMFromHint;
   if (e == cudaSuccess && rf && n) {
-    e = cc::launch_root_select_certified(r.r.edges_dev, r.r.n_edges, span, g.cnt, wide, n, g.cert, g.ctrl, ss);
+    e = cc::launch_root_select_certified(r->r.edges_dev, r->r.n_edges, span, g.cnt, wide, n, g.cert, g.ctrl, ss);
     m_src = cc::kMFromPackedMax;
   }
   if (e == cudaSuccess && n) e = cc::launch_init(rf, g.P, n, g.ctrl, m_src, 0u, ss);
   if (e == cudaSuccess && n) e = cc::launch_edge_pass(rf, 1, 4, 256, span, g.P, n, g.ctrl, false, ss);
-  if (e == cudaSuccess && n) e = cc::launch_flatten(rf, s->cfg.label_space, g.P, n, r.r.labels_dev, g.ctrl, ss);
-  const uint32_t gid = r.graph;
+  if (e == cudaSuccess && n) e = cc::launch_flatten(rf, s->cfg.label_space, g.P, n, r->r.labels_dev, g.ctrl, ss);
+  const uint32_t gid = r->graph;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&s->side_words[2 * gid], &g.ctrl->m, sizeof(uint32_t), cudaMemcpyDeviceToHost, ss);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&s->side_words[2 * gid + 1], &g.ctrl->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ss);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventRecord(r.ev, ss);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(r->ev, ss);
   if (e != cudaSuccess) {
-    complete(s, t, CC_ERR_CUDA);
+    complete(s, r, CC_ERR_CUDA);
     return true;
   }
-  s->side_running.push_back(t);
+  r->t_side = host_ns();
+  s->side_running.push_back(r);
   return true;
 }
 
-bool start_snapshot(cc_server *s, uint64_t t, GraphState &g) {
-  Req &r = s->reqs[t - 1];
-  r.state = kRunning;
+bool start_snapshot(cc_server *s, Req *r, GraphState &g) {
+  if (s->side_running.size() >= cc::srv::kMaxSideRunning) return false;
+  r->state.store(kRunning);
   cudaStream_t ss = s->side_stream;
   cudaError_t e = cudaSuccess;
   if (g.n) {
     cc::srv::k_srv_prep_flatten<<<1, 1, 0, ss>>>(g.ctrl);
     cc::note_launch();
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = cc::launch_flatten(g.rf, s->cfg.label_space, g.P, (uint32_t)g.n, r.r.labels_dev, g.ctrl, ss);
+    if (e == cudaSuccess) e = cc::launch_flatten(g.rf, s->cfg.label_space, g.P, (uint32_t)g.n, r->r.labels_dev, g.ctrl, ss);
   }
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventRecord(r.ev, ss);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(r->ev, ss);
   if (e != cudaSuccess) {
-    complete(s, t, CC_ERR_CUDA);
+    complete(s, r, CC_ERR_CUDA);
     return true;
   }
-  s->side_running.push_back(t);
+  r->t_side = host_ns();
+  s->side_running.push_back(r);
   return true;
 }
 
@@ -511,161 +622,291 @@ int class_of(int kind) {
   }
 }
 
-void finish_graph_request(cc_server *s, GraphState &g) {
+void finish_graph_request(GraphState &g) {
   if (--g.active == 0) g.group = kIdle;
-  (void)s;
 }
 
 // Starts what may start at the head of a graph's queue.
 void try_start(cc_server *s, uint32_t gid) {
   GraphState &g = s->graphs[gid];
   while (!g.fifo.empty()) {
-    const uint64_t t = g.fifo.front();
-    Req &r = s->reqs[t - 1];
-    const int cls = class_of(r.r.kind);
+    Req *r = g.fifo.front();
+    const int cls = class_of(r->r.kind);
     if (g.group == kExclusive) return;
     if (cls == kExclusive) {
       if (g.active) return;
-      if (r.r.kind == CC_REQ_NEW_GRAPH) {
-        if (!start_new_graph(s, t, g)) return;  // no memory yet
+      if (r->r.kind == CC_REQ_NEW_GRAPH) {
+        if (!start_new_graph(s, r, g)) return;  // no memory yet
         g.fifo.pop_front();
-        if (r.state == kRunning) {
+        if (r->state.load() == kRunning) {
           g.group = kExclusive;
           g.active = 1;
         }
         return;
       }
-      // drop
-      if (g.live) s->arena.release(g.off, g.bytes);
+      // drop: every earlier request of the graph has completed
+      if (g.live) {
+        s->arena.release(g.off, g.bytes);
+        s->arena_used = s->arena.used();
+        s->resident--;
+      }
       g.live = false;
       g.fifo.pop_front();
-      complete(s, t, CC_OK);
       {
+        std::lock_guard<std::mutex> lk(s->sub_mu);
         s->id_state[gid] = 0;
         s->free_ids.push_back(gid);
       }
+      complete(s, r, CC_OK);
       continue;
     }
     if (g.active && g.group != cls) return;
-    bool started;
-    if (r.r.kind == CC_REQ_SNAPSHOT)
-      started = start_snapshot(s, t, g);
-    else
-      started = start_exec(s, t, g);
+    const bool started = r->r.kind == CC_REQ_SNAPSHOT ? start_snapshot(s, r, g) : start_exec(s, r, g);
     if (!started) return;
     g.fifo.pop_front();
-    if (r.state == kRunning) {
+    if (r->state.load() == kRunning) {
       g.group = cls;
       g.active++;
     }
   }
 }
 
-void ensure_executor(cc_server *s) {
-  if (s->exec_running) {
-    if (cudaEventQuery(s->exec_ev) == cudaSuccess) s->exec_running = false;
+// Completes the requests whose executor tiles have all finished (their
+// done_seq word carries the request's sequence number).
+bool reap_executor(cc_server *s, std::vector<uint32_t> *touched) {
+  bool any = false;
+  for (uint32_t slot = 0; slot < cc::srv::kSlots; ++slot) {
+    Req *r = s->slot_req[slot];
+    if (!r) continue;
+    if (*(volatile unsigned int *)&s->hs->done_seq[slot] != r->seq) continue;
+    s->in_flight_items -= r->n_tiles;
+    const unsigned int err = *(volatile unsigned int *)&s->hs->err[slot];
+    s->slot_req[slot] = nullptr;
+    // after a gate timeout a late validate tile may still count into this
+    // slot: retire it instead of reusing it
+    if (err != 2u) s->free_slots.push_back(slot);
+    complete(s, r, err == 2u ? CC_ERR_TIMEOUT : (err ? CC_ERR_OUT_OF_RANGE : CC_OK));
+    finish_graph_request(s->graphs[r->graph]);
+    if (touched) touched->push_back(r->graph);
+    any = true;
   }
-  if (!s->exec_running && s->in_flight_items > 0) {
-    const unsigned grid = (unsigned)(cc::num_sms() * s->cfg.executor_blocks_per_sm);
-    cc::srv::k_executor<<<grid, 256, 0, s->exec_stream>>>(s->hs_dev, s->ds,
-                                                         (unsigned long long)s->cfg.idle_timeout_us * 1000ULL);
-    cc::note_launch();
-    cudaEventRecord(s->exec_ev, s->exec_stream);
-    s->exec_running = true;
-    s->stats.executor_launches++;
+  return any;
+}
+
+// Launches the executor when work is in flight; stops it after an idle
+// period; after it has left, rewinds `taken` to `published` (all published
+// items were processed) so that claims made while waiting are forgotten.
+void manage_executor(cc_server *s) {
+  const uint64_t now = host_ns();
+  if (s->exec_running && cudaEventQuery(s->exec_ev) == cudaSuccess) {
+    // the executor has left (asked to, or after its own bounded wait); its
+    // last completions may have become visible only now
+    reap_executor(s, nullptr);
+    if (s->in_flight_items > 0) {
+      // it left without finishing: fail what was in flight (not expected
+      // unless the host stalled for longer than the executor's wait limit)
+      for (uint32_t slot = 0; slot < cc::srv::kSlots; ++slot) {
+        Req *r = s->slot_req[slot];
+        if (!r) continue;
+        s->slot_req[slot] = nullptr;  // retired, not reused
+        s->in_flight_items -= r->n_tiles;
+        complete(s, r, CC_ERR_TIMEOUT);
+        finish_graph_request(s->graphs[r->graph]);
+      }
+    }
+    unsigned long long pub = s->hs->published;
+    cudaMemcpyAsync(&s->ds->taken, &pub, sizeof(pub), cudaMemcpyHostToDevice, s->exec_stream);
+    cudaStreamSynchronize(s->exec_stream);
+    *(volatile unsigned int *)&s->hs->stop = 0u;
+    s->exec_running = false;
+    s->exec_stopping = false;
+  }
+  if (s->in_flight_items > 0) {
+    s->idle_since = 0;
+    if (!s->exec_running) {
+      const unsigned grid = (unsigned)(cc::num_sms() * s->cfg.executor_blocks_per_sm);
+      cc::srv::k_executor<<<grid, 256, 0, s->exec_stream>>>(s->hs_dev, s->ds);
+      cc::note_launch();
+      cudaEventRecord(s->exec_ev, s->exec_stream);
+      s->exec_running = true;
+      s->executor_launches++;
+    }
+  } else if (s->exec_running && !s->exec_stopping) {
+    if (!s->idle_since) s->idle_since = now;
+    if (now - s->idle_since > (uint64_t)s->cfg.idle_timeout_us * 1000ULL) {
+      *(volatile unsigned int *)&s->hs->stop = 1u;
+      s->exec_stopping = true;
+      s->idle_since = 0;
+    }
+  }
+  // Side-stream work starved by the resident executor (a kernel that does
+  // not fit beside it waits for it to leave): drain the executor, which
+  // finishes every published tile first; a later pass relaunches it.
+  if (s->exec_running && !s->exec_stopping) {
+    for (Req *r : s->side_running) {
+      if (now - r->t_side < cc::srv::kSideStarveNs) continue;
+      r->t_side = now;
+      *(volatile unsigned int *)&s->hs->stop = 1u;
+      s->exec_stopping = true;
+      s->idle_since = 0;
+      s->side_drains++;
+      break;
+    }
   }
 }
 
-// One scheduler pass; returns true when anything changed.
-bool scheduler_step(cc_server *s) {
+// One scheduler pass; returns true when a request completed or started.
+bool scheduler_step(cc_server *s, std::vector<Req *> &incoming) {
   bool progress = false;
   std::vector<uint32_t> touched;
-  // 1. new requests into their graphs' queues
-  while (!s->inbox.empty()) {
-    const uint64_t t = s->inbox.front();
-    s->inbox.pop_front();
-    Req &r = s->reqs[t - 1];
-    s->graphs[r.graph].fifo.push_back(t);
-    touched.push_back(r.graph);
+  for (Req *r : incoming) {
+    s->graphs[r->graph].fifo.push_back(r);
+    touched.push_back(r->graph);
     progress = true;
   }
-  // 2. executor completions
-  for (uint32_t slot = 0; slot < cc::srv::kSlots; ++slot) {
-    const uint64_t t = s->slot_ticket[slot];
-    if (!t) continue;
-    Req &r = s->reqs[t - 1];
-    if (*(volatile unsigned int *)&s->hs->done_seq[slot] != r.seq) continue;
-    s->in_flight_items -= r.n_tiles;
-    const bool bad = *(volatile unsigned int *)&s->hs->err[slot] != 0u;
-    GraphState &g = s->graphs[r.graph];
-    if (r.r.kind == CC_REQ_INSERT && r.phase == 1 && !bad) {
-      r.phase = 2;  // validated: apply
-      publish_tiles(s, r, cc::srv::kItemApply, r.r.n_edges, r.r.edges_dev, g);
-      progress = true;
-      continue;
-    }
-    s->slot_ticket[slot] = 0;
-    s->free_slots.push_back(slot);
-    complete(s, t, bad ? CC_ERR_OUT_OF_RANGE : CC_OK);
-    finish_graph_request(s, g);
-    touched.push_back(r.graph);
-    progress = true;
-  }
-  // 3. side-stream completions
+  incoming.clear();
+  if (reap_executor(s, &touched)) progress = true;
+  // side-stream completions
   for (size_t i = 0; i < s->side_running.size();) {
-    const uint64_t t = s->side_running[i];
-    Req &r = s->reqs[t - 1];
-    const cudaError_t q = cudaEventQuery(r.ev);
+    Req *r = s->side_running[i];
+    const cudaError_t q = cudaEventQuery(r->ev);
     if (q == cudaErrorNotReady) {
       ++i;
       continue;
     }
-    cudaEventDestroy(r.ev);
-    r.ev = nullptr;
-    GraphState &g = s->graphs[r.graph];
+    cudaEventDestroy(r->ev);
+    r->ev = nullptr;
+    GraphState &g = s->graphs[r->graph];
     cc_status st = q == cudaSuccess ? CC_OK : CC_ERR_CUDA;
-    if (r.r.kind == CC_REQ_NEW_GRAPH && st == CC_OK) {
-      g.m = s->side_words[2 * r.graph];
-      if (s->side_words[2 * r.graph + 1]) st = CC_ERR_OUT_OF_RANGE;
+    if (r->r.kind == CC_REQ_NEW_GRAPH && st == CC_OK) {
+      g.m = s->side_words[2 * r->graph];
+      if (s->side_words[2 * r->graph + 1]) st = CC_ERR_OUT_OF_RANGE;
     }
-    complete(s, t, st);
-    finish_graph_request(s, g);
-    touched.push_back(r.graph);
+    complete(s, r, st);
+    finish_graph_request(g);
+    touched.push_back(r->graph);
     s->side_running[i] = s->side_running.back();
     s->side_running.pop_back();
     progress = true;
   }
-  // 4. start what may start; graphs waiting for memory are retried too
   for (uint32_t gid : touched) try_start(s, gid);
   for (uint32_t gid = 0; gid < s->graphs.size(); ++gid)
     if (!s->graphs[gid].fifo.empty() && s->graphs[gid].group == kIdle) try_start(s, gid);
-  ensure_executor(s);
+  manage_executor(s);
   return progress;
 }
 
+constexpr uint64_t kShutdownGraceNs = 10ULL * 1000 * 1000 * 1000;  // 10 s
+
 void scheduler_main(cc_server *s) {
   cudaSetDevice(s->device);
+  std::vector<Req *> incoming;
+  uint64_t quit_at = 0;
   while (true) {
-    bool busy;
+    bool quit;
     {
-      std::unique_lock<std::mutex> lk(s->mu);
-      if (scheduler_step(s)) s->cv.notify_all();
-      busy = s->in_flight_items > 0 || !s->side_running.empty();
-      bool queued = !s->inbox.empty();
-      for (auto &g : s->graphs)
-        if (!g.fifo.empty()) {
-          queued = true;
-          break;
-        }
-      if (s->quit && !busy && !queued) break;
-      if (!busy) {
-        // waiting for memory or ordering: retry soon, or at the next submit
-        s->cv.wait_for(lk, queued ? std::chrono::microseconds(100) : std::chrono::milliseconds(2));
-        continue;
-      }
+      std::lock_guard<std::mutex> lk(s->sub_mu);
+      incoming.swap(s->inbox);
+      quit = s->quit;
     }
-    std::this_thread::sleep_for(std::chrono::microseconds(2));  // poll completions
+    if (scheduler_step(s, incoming)) {
+      std::lock_guard<std::mutex> lk(s->done_mu);
+      s->done_cv.notify_all();
+    }
+    const bool busy = s->in_flight_items > 0 || !s->side_running.empty() || s->exec_running;
+    bool queued = false;
+    for (auto &g : s->graphs)
+      if (!g.fifo.empty()) {
+        queued = true;
+        break;
+      }
+    if (quit) {
+      // shutting down: requests still running get a bounded grace period
+      if (!quit_at) quit_at = host_ns();
+      const bool work = s->in_flight_items > 0 || !s->side_running.empty() || queued;
+      if (!work || host_ns() - quit_at > kShutdownGraceNs) break;
+    }
+    if (busy) {
+      std::this_thread::yield();  // poll completions without a timer sleep
+    } else {
+      std::unique_lock<std::mutex> lk(s->sub_mu);
+      if (s->inbox.empty() && !s->quit)
+        s->sub_cv.wait_for(lk, queued ? std::chrono::microseconds(100) : std::chrono::milliseconds(2));
+    }
   }
+  // stop the executor (bounded: its blocks leave at the next look at `stop`)
+  *(volatile unsigned int *)&s->hs->stop = 1u;
+  cudaStreamSynchronize(s->exec_stream);
+  cudaStreamSynchronize(s->side_stream);
+}
+
+// Runs every kernel the server can launch once, on a tiny graph, before the
+// executor exists. With lazy module loading, the first launch of a kernel
+// can wait until the device is idle; the resident executor never is while it
+// works, so a first launch from the scheduler thread would stall both.
+cudaError_t warm_up(cc_server *s) {
+  const bool rf = s->cfg.mode == CC_ROOT_MAXDEG;
+  const uint32_t n = 16;
+  const uint32_t edges_h[8] = {0, 1, 2, 3, 3, 1, 5, 5};
+  uint32_t *P = nullptr, *edges = nullptr, *labels = nullptr;
+  void *cnt = nullptr;
+  cc::CertScratch *cert = nullptr;
+  cc::Ctrl *ctrl = nullptr;
+  cudaStream_t ss = s->side_stream;
+  cudaError_t e = cudaMalloc((void **)&P, 64 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&edges, sizeof(edges_h));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&labels, 64 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&cnt, 64 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&cert, sizeof(cc::CertScratch));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&ctrl, sizeof(cc::Ctrl));
+  if (e == cudaSuccess) e = cudaMemcpy(edges, edges_h, sizeof(edges_h), cudaMemcpyHostToDevice);
+  const cc::EdgeSpan span = cc::split_edges(edges, 4);
+  for (int wide = 0; wide < 2 && e == cudaSuccess; ++wide) {
+    e = cudaMemsetAsync(ctrl, 0, sizeof(cc::Ctrl), ss);
+    int m_src = cc::kMFromHint;
+    if (e == cudaSuccess && rf) {
+      e = cc::launch_root_select_certified(edges, 4, span, cnt, wide != 0, n, cert, ctrl, ss);
+      m_src = cc::kMFromPackedMax;
+    }
+    if (e == cudaSuccess) e = cc::launch_init(rf, P, n, ctrl, m_src, 0u, ss);
+    if (e == cudaSuccess) e = cc::launch_edge_pass(rf, 1, 4, 256, span, P, n, ctrl, false, ss);
+    if (e == cudaSuccess) e = cc::launch_flatten(rf, s->cfg.label_space, P, n, labels, ctrl, ss);
+    if (e == cudaSuccess) e = cc::launch_flatten(rf, s->cfg.label_space, P, n, nullptr, ctrl, ss);
+    if (e == cudaSuccess) {
+      cc::srv::k_srv_prep_flatten<<<1, 1, 0, ss>>>(ctrl);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ss);
+  // The executor prefers the largest shared memory carveout: with the
+  // driver's default choice, the SMs it holds have too little shared memory
+  // left for the side-stream kernels that use 64 KB.
+  static std::atomic<unsigned long long> carveout_set{0};
+  if (e == cudaSuccess)
+    e = cc::ensure_func_attr((const void *)cc::srv::k_executor, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared, carveout_set);
+  // the executor: told to leave before it starts
+  if (e == cudaSuccess) {
+    *(volatile unsigned int *)&s->hs->stop = 1u;
+    cc::srv::k_executor<<<1, 256, 0, s->exec_stream>>>(s->hs_dev, s->ds);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->exec_stream);
+    *(volatile unsigned int *)&s->hs->stop = 0u;
+    if (e == cudaSuccess) e = cudaMemset(&s->ds->taken, 0, sizeof(unsigned long long));
+  }
+  cudaFree(P);
+  cudaFree(edges);
+  cudaFree(labels);
+  cudaFree(cnt);
+  cudaFree(cert);
+  cudaFree(ctrl);
+  return e;
+}
+
+Req *find(cc_server *s, uint64_t ticket) {
+  std::lock_guard<std::mutex> lk(s->sub_mu);
+  if (ticket == 0 || ticket > s->reqs.size()) return nullptr;
+  return s->reqs[ticket - 1].get();
 }
 
 }  // namespace
@@ -676,7 +917,7 @@ void cc_server_config_init(cc_server_config *cfg) {
   if (!cfg) return;
   memset(cfg, 0, sizeof(*cfg));
   cfg->max_graphs = 1024;
-  cfg->executor_blocks_per_sm = 2;
+  cfg->executor_blocks_per_sm = 3;
   cfg->tile_edges = 16384;
   cfg->idle_timeout_us = 20000;
   cfg->mode = CC_ROOT_MAXDEG;
@@ -688,10 +929,10 @@ cc_status cc_server_create(const cc_server_config *cfg_in, cc_server **out) {
   *out = nullptr;
   cc_server_config cfg = *cfg_in;
   if (!cfg.max_graphs) cfg.max_graphs = 1024;
-  if (!cfg.executor_blocks_per_sm) cfg.executor_blocks_per_sm = 2;
+  if (!cfg.executor_blocks_per_sm) cfg.executor_blocks_per_sm = 3;
   if (!cfg.tile_edges) cfg.tile_edges = 16384;
   if (!cfg.idle_timeout_us) cfg.idle_timeout_us = 20000;
-  if (cfg.hbm_budget_bytes == 0 || cfg.executor_blocks_per_sm > 8 ||
+  if (cfg.hbm_budget_bytes == 0 || cfg.executor_blocks_per_sm > 8 || cfg.tile_edges < 256 ||
       (cfg.mode != CC_ROOT_IDENTITY && cfg.mode != CC_ROOT_MAXDEG) ||
       (cfg.label_space != CC_LABEL_MIN_ID && cfg.label_space != CC_LABEL_ROOT_VALUE) || cfg.max_graphs > (1u << 20))
     return CC_ERR_INVALID_ARGUMENT;
@@ -706,7 +947,8 @@ cc_status cc_server_create(const cc_server_config *cfg_in, cc_server **out) {
   if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&s->hs_dev, s->hs, 0);
   if (e == cudaSuccess) e = cudaMalloc((void **)&s->ds, sizeof(DevShared));
   if (e == cudaSuccess) e = cudaMemset(s->ds, 0, sizeof(DevShared));
-  if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->side_words, 2 * (size_t)cfg.max_graphs * sizeof(uint32_t), cudaHostAllocDefault);
+  if (e == cudaSuccess)
+    e = cudaHostAlloc((void **)&s->side_words, 2 * (size_t)cfg.max_graphs * sizeof(uint32_t), cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->exec_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->side_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->exec_ev, cudaEventDisableTiming);
@@ -723,13 +965,24 @@ cc_status cc_server_create(const cc_server_config *cfg_in, cc_server **out) {
     return st;
   }
   memset(s->hs, 0, sizeof(HostShared));
+  if ((e = warm_up(s)) != cudaSuccess) {
+    cudaFree(s->arena_base);
+    cudaFreeHost(s->hs);
+    cudaFree(s->ds);
+    cudaFreeHost(s->side_words);
+    cudaStreamDestroy(s->exec_stream);
+    cudaStreamDestroy(s->side_stream);
+    cudaEventDestroy(s->exec_ev);
+    delete s;
+    return CC_ERR_CUDA;
+  }
   s->arena.reset(cfg.hbm_budget_bytes);
   s->graphs.resize(cfg.max_graphs);
   s->id_state.assign(cfg.max_graphs, 0);
   for (uint32_t i = cfg.max_graphs; i-- > 0;) s->free_ids.push_back(i);
   for (uint32_t i = cc::srv::kSlots; i-- > 0;) s->free_slots.push_back(i);
-  s->slot_ticket.assign(cc::srv::kSlots, 0);
-  s->stats.arena_bytes = cfg.hbm_budget_bytes;
+  s->slot_req.assign(cc::srv::kSlots, nullptr);
+  s->slot_gen.assign(cc::srv::kSlots, 0);
   s->thread = std::thread(scheduler_main, s);
   *out = s;
   return CC_OK;
@@ -744,7 +997,7 @@ cc_status cc_server_submit(cc_server *s, const cc_request *req, uint64_t *ticket
       if (r.n_vertices > 0x7FFFFFFFULL) return CC_ERR_TOO_LARGE;
       if (r.n_edges && (!r.edges_dev || misaligned(r.edges_dev, 8))) return CC_ERR_INVALID_ARGUMENT;
       if (r.labels_dev && misaligned(r.labels_dev, 4)) return CC_ERR_INVALID_ARGUMENT;
-      if (graph_bytes(s, r.n_vertices, r.n_edges, s->cfg.mode == CC_ROOT_MAXDEG) > s->cfg.hbm_budget_bytes)
+      if (graph_bytes(r.n_vertices, r.n_edges, s->cfg.mode == CC_ROOT_MAXDEG) > s->cfg.hbm_budget_bytes)
         return CC_ERR_TOO_LARGE;
       break;
     case CC_REQ_INSERT:
@@ -761,96 +1014,99 @@ cc_status cc_server_submit(cc_server *s, const cc_request *req, uint64_t *ticket
     default:
       return CC_ERR_INVALID_ARGUMENT;
   }
-  std::lock_guard<std::mutex> lk(s->mu);
-  if (s->quit) return CC_ERR_INVALID_ARGUMENT;
-  uint32_t gid = r.graph;
-  if (r.kind == CC_REQ_NEW_GRAPH) {
-    if (s->free_ids.empty()) return CC_ERR_TOO_LARGE;
-    gid = s->free_ids.back();
-    s->free_ids.pop_back();
-    s->id_state[gid] = 1;
-  } else {
-    if (gid >= s->cfg.max_graphs || s->id_state[gid] != 1) return CC_ERR_INVALID_ARGUMENT;
-    if (r.kind == CC_REQ_DROP_GRAPH) s->id_state[gid] = 2;
+  std::unique_ptr<Req> q(new (std::nothrow) Req());
+  if (!q) return CC_ERR_OOM;
+  q->r = r;
+  q->t_submit = host_ns();
+  {
+    std::lock_guard<std::mutex> lk(s->sub_mu);
+    if (s->quit) return CC_ERR_INVALID_ARGUMENT;
+    uint32_t gid = r.graph;
+    if (r.kind == CC_REQ_NEW_GRAPH) {
+      if (s->free_ids.empty()) return CC_ERR_TOO_LARGE;
+      gid = s->free_ids.back();
+      s->free_ids.pop_back();
+      s->id_state[gid] = 1;
+    } else {
+      if (gid >= s->cfg.max_graphs || s->id_state[gid] != 1) return CC_ERR_INVALID_ARGUMENT;
+      if (r.kind == CC_REQ_DROP_GRAPH) s->id_state[gid] = 2;
+    }
+    q->graph = gid;
+    s->reqs.push_back(std::move(q));
+    *ticket = s->reqs.size();
+    s->reqs.back()->ticket = *ticket;
+    s->inbox.push_back(s->reqs.back().get());
   }
-  Req q;
-  q.r = r;
-  q.graph = gid;
-  q.t_submit = host_ns();
-  s->reqs.push_back(q);
-  const uint64_t t = s->reqs.size();
-  s->inbox.push_back(t);
-  s->stats.submitted++;
-  *ticket = t;
-  s->cv.notify_all();
+  s->submitted++;
+  s->sub_cv.notify_one();
   return CC_OK;
 }
 
 cc_status cc_server_poll(cc_server *s, uint64_t ticket, cc_status *result) {
   if (!s || !result) return CC_ERR_INVALID_ARGUMENT;
-  std::lock_guard<std::mutex> lk(s->mu);
-  if (ticket == 0 || ticket > s->reqs.size()) return CC_ERR_INVALID_ARGUMENT;
-  const Req &r = s->reqs[ticket - 1];
-  if (r.state != kDone) return CC_ERR_NOT_READY;
-  *result = r.result;
+  Req *r = find(s, ticket);
+  if (!r) return CC_ERR_INVALID_ARGUMENT;
+  if (r->state.load(std::memory_order_acquire) != kDone) return CC_ERR_NOT_READY;
+  *result = (cc_status)r->result.load();
   return CC_OK;
 }
 
 cc_status cc_server_wait(cc_server *s, uint64_t ticket, uint64_t timeout_ns, cc_status *result) {
   if (!s || !result) return CC_ERR_INVALID_ARGUMENT;
-  std::unique_lock<std::mutex> lk(s->mu);
-  if (ticket == 0 || ticket > s->reqs.size()) return CC_ERR_INVALID_ARGUMENT;
+  Req *r = find(s, ticket);
+  if (!r) return CC_ERR_INVALID_ARGUMENT;
   const auto deadline = std::chrono::steady_clock::now() + std::chrono::nanoseconds(timeout_ns);
-  while (s->reqs[ticket - 1].state != kDone) {
-    if (s->cv.wait_until(lk, deadline) == std::cv_status::timeout && s->reqs[ticket - 1].state != kDone)
+  std::unique_lock<std::mutex> lk(s->done_mu);
+  while (r->state.load(std::memory_order_acquire) != kDone) {
+    if (s->done_cv.wait_until(lk, deadline) == std::cv_status::timeout &&
+        r->state.load(std::memory_order_acquire) != kDone)
       return CC_ERR_TIMEOUT;
   }
-  *result = s->reqs[ticket - 1].result;
+  *result = (cc_status)r->result.load();
   return CC_OK;
 }
 
 cc_status cc_server_result_graph(cc_server *s, uint64_t ticket, uint32_t *graph) {
   if (!s || !graph) return CC_ERR_INVALID_ARGUMENT;
-  std::lock_guard<std::mutex> lk(s->mu);
-  if (ticket == 0 || ticket > s->reqs.size()) return CC_ERR_INVALID_ARGUMENT;
-  *graph = s->reqs[ticket - 1].graph;
+  Req *r = find(s, ticket);
+  if (!r) return CC_ERR_INVALID_ARGUMENT;
+  *graph = r->graph;
   return CC_OK;
 }
 
 cc_status cc_server_latency_ns(cc_server *s, uint64_t ticket, uint64_t *ns) {
   if (!s || !ns) return CC_ERR_INVALID_ARGUMENT;
-  std::lock_guard<std::mutex> lk(s->mu);
-  if (ticket == 0 || ticket > s->reqs.size()) return CC_ERR_INVALID_ARGUMENT;
-  const Req &r = s->reqs[ticket - 1];
-  if (r.state != kDone) return CC_ERR_NOT_READY;
-  *ns = r.t_done - r.t_submit;
+  Req *r = find(s, ticket);
+  if (!r) return CC_ERR_INVALID_ARGUMENT;
+  if (r->state.load(std::memory_order_acquire) != kDone) return CC_ERR_NOT_READY;
+  *ns = r->t_done.load() - r->t_submit;
   return CC_OK;
 }
 
 cc_status cc_server_get_stats(cc_server *s, cc_server_stats *st) {
   if (!s || !st) return CC_ERR_INVALID_ARGUMENT;
-  std::lock_guard<std::mutex> lk(s->mu);
-  *st = s->stats;
-  st->arena_bytes_used = s->arena.used();
-  uint64_t live = 0;
-  for (auto &g : s->graphs) live += g.live;
-  st->resident_graphs = live;
+  st->submitted = s->submitted;
+  st->completed = s->completed;
+  st->failed = s->failed;
+  st->resident_graphs = s->resident;
+  st->arena_bytes_used = s->arena_used;
+  st->arena_bytes = s->cfg.hbm_budget_bytes;
+  st->executor_launches = s->executor_launches;
+  st->tiles_run = s->tiles_run;
+  st->side_drains = s->side_drains;
   return CC_OK;
 }
 
 void cc_server_destroy(cc_server *s) {
   if (!s) return;
   {
-    std::lock_guard<std::mutex> lk(s->mu);
+    std::lock_guard<std::mutex> lk(s->sub_mu);
     s->quit = true;
-    s->cv.notify_all();
   }
+  s->sub_cv.notify_all();
   if (s->thread.joinable()) s->thread.join();
-  *(volatile unsigned int *)&s->hs->stop = 1u;
-  cudaStreamSynchronize(s->exec_stream);
-  cudaStreamSynchronize(s->side_stream);
   for (auto &r : s->reqs)
-    if (r.ev) cudaEventDestroy(r.ev);
+    if (r->ev) cudaEventDestroy(r->ev);
   cudaFree(s->arena_base);
   cudaFreeHost(s->hs);
   cudaFree(s->ds);

@@ -57,6 +57,22 @@ def test_options_layout_matches_header(tmp_path, lib):
                    o.hbm_budget_bytes.offset, o.reserved.offset]
 
 
+def test_batch_and_server_layouts_match_headers(tmp_path, lib):
+    c = tmp_path / "layout2.c"
+    c.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "cc_batch.h"\n#include "cc_server.h"\n'
+                 'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(cc_batch_config),'
+                 'offsetof(cc_batch_config, tile_vertices), sizeof(cc_request), offsetof(cc_request, labels_dev),'
+                 'sizeof(cc_server_config), offsetof(cc_server_config, label_space), sizeof(cc_server_stats));'
+                 'return 0;}\n')
+    exe = tmp_path / "layout2"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(c)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert got == [ctypes.sizeof(lib.cc_batch_config), lib.cc_batch_config.tile_vertices.offset,
+                   ctypes.sizeof(lib.cc_request), lib.cc_request.labels_dev.offset,
+                   ctypes.sizeof(lib.cc_server_config), lib.cc_server_config.label_space.offset,
+                   ctypes.sizeof(lib.cc_server_stats)]
+
+
 def test_defaults_and_status_strings(lib):
     o = lib.cc_options_init()
     assert o.mode == lib.CC_ROOT_MAXDEG and o.root_select == lib.CC_ROOT_SELECT_EXACT

@@ -95,10 +95,13 @@ def run_script(server, script, graphs, one_at_a_time):
         results.append(res)
         if one_at_a_time:
             assert server.wait(t) == cc.CC_OK
-    for t in tickets:
+    out = []
+    for t, res in zip(tickets, results):
         assert server.wait(t) == cc.CC_OK
-    torch.cuda.synchronize()
-    return [None if r is None else r.cpu().numpy() for r in results], tickets
+        # read right after completion, with no device-wide synchronisation:
+        # a completed ticket must mean its outputs are final
+        out.append(None if res is None else res.cpu().numpy())
+    return out, tickets
 
 
 @pytest.mark.parametrize("mode", [cc.CC_ROOT_MAXDEG, cc.CC_ROOT_IDENTITY])
@@ -128,7 +131,7 @@ def test_insert_with_bad_id_is_rejected_whole():
         assert s.wait(t) == cc.CC_OK
         L0 = torch.empty(n, dtype=torch.int32, device="cuda")
         assert s.wait(s.snapshot(g, L0)) == cc.CC_OK
-        for size in (500, 20000):  # one tile, and many tiles (validated first)
+        for size in (100, 500, 20000):  # one tile, and many tiles (validated first)
             bad = graphgen.pairs(n, size, 4, tag=size)
             bad[size // 2, 0] = n + 5
             assert s.wait(s.insert(g, dev(bad))) == cc.CC_ERR_OUT_OF_RANGE
@@ -181,3 +184,59 @@ def test_executor_relaunches_after_idle_and_errors_at_submit():
         with pytest.raises(cc.CCError):
             s.insert(g + 17, dev(e))  # unknown graph
         assert s.latency_ns(t) > 0
+
+
+def test_slot_reuse_completion_is_exact():
+    """Many requests one after another reuse the same executor slots; each
+    result is read as soon as its ticket completes (no device-wide sync)."""
+    n = 1 << 14
+    base = graphgen.rmat(14, 1 << 16, 9, scramble=True)
+    with cc.Server(GB, tile_edges=2048) as s:
+        t, g = s.new_graph(n, dev(base))
+        assert s.wait(t) == cc.CC_OK
+        seen = [base]
+        for i in range(40):
+            ins = graphgen.pairs(n, int(50 + 997 * i), 12, tag=i)  # 1 to 20 tiles
+            assert s.wait(s.insert(g, dev(ins))) == cc.CC_OK
+            seen.append(ins)
+            q = graphgen.pairs(n, 5000, 13, tag=i)
+            out = torch.full((5000,), 9, dtype=torch.uint8, device="cuda")
+            qd = dev(q)
+            torch.cuda.synchronize()
+            assert s.wait(s.query(g, qd, out)) == cc.CC_OK
+            want = oracle.connected(oracle.min_labels(n, np.concatenate(seen)), q)
+            np.testing.assert_array_equal(out.cpu().numpy(), want)
+
+
+
+def test_side_work_is_not_starved_by_a_full_executor():
+    """With 8 executor blocks per SM the executor leaves no room on any SM for
+    the side-stream kernels of a new graph; the host must drain the executor
+    instead of waiting for its (long) idle timeout."""
+    import time
+    n = 1 << 14
+    a = graphgen.rmat(14, 1 << 16, 21, scramble=True)
+    b = graphgen.rmat(13, 1 << 15, 22, scramble=True)
+    with cc.Server(GB, executor_blocks_per_sm=8, idle_timeout_us=5_000_000) as s:
+        ta, ga = s.new_graph(n, dev(a))
+        assert s.wait(ta) == cc.CC_OK
+        q = graphgen.pairs(n, 4000, 23)
+        out = torch.empty(4000, dtype=torch.uint8, device="cuda")
+        qd = dev(q)
+        torch.cuda.synchronize()
+        assert s.wait(s.query(ga, qd, out)) == cc.CC_OK  # the executor is now resident and idle
+        eb = dev(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tb, gb = s.new_graph(1 << 13, eb)
+        assert s.wait(tb, 3.0) == cc.CC_OK
+        assert time.perf_counter() - t0 < 2.0  # far below the 5 s idle timeout
+        Lb = torch.empty(1 << 13, dtype=torch.int32, device="cuda")
+        assert s.wait(s.snapshot(gb, Lb), 3.0) == cc.CC_OK
+        np.testing.assert_array_equal(Lb.cpu().numpy().view(np.uint32), oracle.min_labels(1 << 13, b))
+        out2 = torch.empty(4000, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        assert s.wait(s.query(ga, qd, out2)) == cc.CC_OK
+        want = oracle.connected(oracle.min_labels(n, a), q)
+        np.testing.assert_array_equal(out.cpu().numpy(), want)
+        np.testing.assert_array_equal(out2.cpu().numpy(), want)
