@@ -98,9 +98,10 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
-    """DRAM bytes per edge-pass launch from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
+def profiled_traffic(workload: str, graphs):
+    """DRAM bytes (read + write) per edge-pass launch of each graph, from the
+    committed ncu summary, if it was taken on the current kernel source and
+    covers every graph (else None)."""
     path = os.path.join(ROOT, "profiles", f"edge_pass_{workload}.md")
     if not os.path.exists(path):
         return None
@@ -109,8 +110,8 @@ def profiled_traffic(workload: str):
         for line in f:
             if line.startswith("traffic_per_launch:"):
                 parts = dict(kv.split("=") for kv in line.split(":", 1)[1].split())
-                if parts.get("source_sha") == src:
-                    return {k: float(v) for k, v in parts.items() if k != "source_sha"}
+                if parts.get("source_sha") == src and all(g in parts for g in graphs):
+                    return {g: float(parts[g]) for g in graphs}
     return None
 
 
@@ -322,7 +323,7 @@ def run_ours(args):
     edge_bytes = [EDGE_PASS_BYTES_PER_EDGE * E for _, _, E in graphs]
     achieved = sum(edge_bytes) / (sum(edge_ms) * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = profiled_traffic(args.workload)
+    traffic = profiled_traffic(args.workload, names)
 
     ms_per_step = elapsed_ms / args.steps
     path_bytes = sum(8 * E + 12 * w.n_vertices + 8 * E + 4 * w.n_vertices for w, _, E in graphs)
@@ -399,8 +400,13 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (edge arrays of 2.1 GB and 0.97 GB vs 129 MB L2)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic["dram_bytes"] if traffic else None,
-                         "kernel": "edge pass (k_edge_pass_*)", "peak_source": peak_kind,
+                         "frac": achieved / peak,
+                         "traffic": sum(traffic.values()) / len(traffic) if traffic else None,
+                         "traffic_by_graph": traffic,
+                         "algorithmic_bytes_per_launch": sum(edge_bytes) / len(edge_bytes),
+                         "kernel": "edge pass (k_edge_pass_filtered), one launch per graph per step; "
+                                   "achieved, traffic and algorithmic bytes are means over those launches",
+                         "peak_source": peak_kind,
                          "algorithmic_bytes": "8 B per edge per launch"},
             "phases_ms": {nm: {"root_select": p[0], "init": p[1], "edge_pass": p[2], "flatten": p[3],
                                "total": p[4]} for nm, p in zip(names, phase_ms)},
