@@ -95,15 +95,13 @@ unsigned long long launch_count();
 cudaError_t launch_init(bool rf, uint32_t *P, uint32_t n, Ctrl *ctrl, int m_src, uint32_t m_hint,
                         cudaStream_t s);
 // Scratch of the certified exact root selection (cc_rootsel.cu).
-constexpr uint32_t kCertCand = 2048;     // candidate vertices at most
-constexpr uint32_t kCertSlots = 4096;    // open-addressing table of the candidates
-constexpr uint32_t kCertBuckets = 8192;  // hash buckets of the degree bound
+constexpr uint32_t kCertCand = 4096;     // more candidates than this: no proof is tried
+constexpr uint32_t kCertBuckets = 8192;  // hash buckets of the degree bound, one owner each
 constexpr uint32_t kCertSample = 128;    // the sampled pass keeps 1 group of 1024 edges in this many
 struct CertScratch {
-  uint32_t cand[kCertCand];
-  uint32_t keys[kCertSlots];                  // vertex + 1 (0 = empty)
-  unsigned long long cand_cnt[kCertSlots];    // exact degree of the slot's vertex
-  unsigned long long bucket[kCertBuckets];    // endpoint occurrences per bucket
+  unsigned long long owner[kCertBuckets];     // (sampled count << 32) | ~vertex of the owner; 0 = none
+  unsigned long long cand_cnt[kCertBuckets];  // exact degree of the owner
+  unsigned long long bucket[kCertBuckets];    // endpoint occurrences of the other vertices
 };
 
 // Certified exact root selection: sampled candidates, one exact pass over all

@@ -146,16 +146,20 @@ __global__ void k_finalize_m(Ctrl *ctrl, const uint32_t *skip) {
 
 // ----------------------------------------------------------- certification
 
-// One multiplicative hash gives the bucket (13 bits) and the home slot of the
-// candidate table (its low 12 bits).
+// One multiplicative hash picks the bucket (13 bits) of a vertex. Each bucket
+// has at most one candidate, its owner; every other vertex of the bucket is
+// counted in the bucket's total.
 __device__ __forceinline__ uint32_t bucket_of(uint32_t x) { return (x * 2654435769u) >> 19; }
-__device__ __forceinline__ uint32_t home_slot(uint32_t b) { return b & (kCertSlots - 1u); }
-static_assert(kCertBuckets == 8192 && kCertSlots <= kCertBuckets, "13-bit buckets, slots from their low bits");
+static_assert(kCertBuckets == 8192, "13-bit buckets");
 
-// Candidates: every vertex whose sampled count is at least 1/32 of the largest.
-// Without a dominant hub (largest sampled count below 64) no certificate can
-// succeed, so no candidates are taken and the full histogram runs. The list
-// counter is bumped once per warp, and scanning stops once the list is full.
+// Candidates: every vertex whose sampled count is at least 1/32 of the largest
+// competes for its bucket; the larger sampled count (then the smaller id)
+// owns it. A vertex that loses stays counted in the bucket total, which then
+// bounds its degree too, so the proof stays sound. Without a dominant hub
+// (largest sampled count below 64) no certificate can succeed and nothing is
+// selected. Scanning stops once more than kCertCand candidates are seen: so
+// many near-maximal vertices leave no room for a proof, and the full
+// histogram runs.
 __global__ void __launch_bounds__(256) k_select_candidates(const uint32_t *__restrict__ cnt, uint32_t n,
                                                            Ctrl *ctrl, CertScratch *cs) {
   const uint32_t cmax = (uint32_t)(*(volatile unsigned long long *)&ctrl->maxkey >> 32);
@@ -166,130 +170,118 @@ __global__ void __launch_bounds__(256) k_select_candidates(const uint32_t *__res
   const uint64_t w0 = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
   for (uint64_t base = w0 * 32; base < n; base += warps * 32) {
     const uint64_t v = base + (uint64_t)lane;
-    const bool q = v < n && cnt[v] >= thr;
+    const uint32_t c = v < n ? cnt[v] : 0u;
+    const bool q = c >= thr && c != 0u;
     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, q);
     if (!bal) continue;
-    uint32_t first = 0;
-    if (lane == 0) first = atomicAdd(&ctrl->n_cand, (uint32_t)__popc(bal));
-    first = __shfl_sync(0xFFFFFFFFu, first, 0);
-    if (q) {
-      const uint32_t i = first + (uint32_t)__popc(bal & ((1u << lane) - 1u));
-      if (i < kCertCand) cs->cand[i] = (uint32_t)v;
-    }
-    if (first >= kCertCand) return;  // the list is full (warp-uniform)
+    uint32_t seen = 0;
+    if (lane == 0) seen = atomicAdd(&ctrl->n_cand, (uint32_t)__popc(bal)) + (uint32_t)__popc(bal);
+    seen = __shfl_sync(0xFFFFFFFFu, seen, 0);
+    if (seen > kCertCand) return;  // too many candidates (warp-uniform)
+    if (q)
+      atomicMax(&cs->owner[bucket_of((uint32_t)v)], ((unsigned long long)c << 32) | (uint32_t)~(uint32_t)v);
   }
 }
 
-// The open-addressing table of the candidates (one block; built once, so all
-// blocks of the counting pass agree on the slots).
-__global__ void __launch_bounds__(256) k_build_table(const Ctrl *ctrl, CertScratch *cs) {
-  const uint32_t nc = min(*(const volatile uint32_t *)&ctrl->n_cand, kCertCand);
-  for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) {
-    const uint32_t x = cs->cand[i];
-    uint32_t s = home_slot(bucket_of(x));
-    for (uint32_t probe = 0; probe < kCertSlots; ++probe) {
-      const uint32_t prev = atomicCAS(&cs->keys[s], 0u, x + 1u);
-      if (prev == 0u || prev == x + 1u) break;
-      s = (s + 1u) & (kCertSlots - 1u);
-    }
-  }
-}
-
-// One endpoint: its bucket total, and its exact count when it is a candidate.
+// One endpoint: the owner's exact count, or the bucket total of the others.
 // Ids >= n are counted too; they only make the bound more conservative (the
 // edge pass reports them).
-__device__ __forceinline__ void cert_count(uint32_t x, const uint32_t *keys, uint32_t *cnts, uint32_t *bk) {
+__device__ __forceinline__ void cert_count(uint32_t x, const uint32_t *key, uint32_t *own, uint32_t *bk) {
   const uint32_t b = bucket_of(x);
-  atomicAdd(&bk[b], 1u);
-  uint32_t s = home_slot(b);
-  uint32_t k = keys[s];
-  if (k == 0u) return;  // most endpoints: an empty home slot
-  for (uint32_t probe = 0; probe < kCertSlots; ++probe) {
-    if (k == x + 1u) {
-      atomicAdd(&cnts[s], 1u);
-      return;
-    }
-    s = (s + 1u) & (kCertSlots - 1u);
-    k = keys[s];
-    if (k == 0u) return;
-  }
+  if (key[b] == x + 1u)
+    atomicAdd(&own[b], 1u);
+  else
+    atomicAdd(&bk[b], 1u);
 }
 
-constexpr size_t kCertSmem = (2 * kCertSlots + kCertBuckets) * sizeof(uint32_t);  // 64 KiB
+constexpr size_t kCertSmem = 3 * kCertBuckets * sizeof(uint32_t);  // 96 KiB
 
-// One pass over all edges: exact candidate degrees and bucket totals, counted
-// in shared memory and flushed once per block.
+__device__ __forceinline__ bool cert_skipped(const Ctrl *ctrl) {
+  const uint32_t nc = *(const volatile uint32_t *)&ctrl->n_cand;
+  return nc == 0u || nc > kCertCand;
+}
+
+// One pass over all edges: exact owner degrees and bucket totals, counted in
+// shared memory (32-bit per block) and flushed once per block.
 __global__ void __launch_bounds__(512) k_degree_certify(const uint4 *__restrict__ e4, uint64_t n_quads,
                                                         const uint2 *head, const uint2 *tail, uint32_t n,
                                                         CertScratch *cs, const Ctrl *ctrl) {
   extern __shared__ uint32_t csm[];
-  // no candidates (no dominant hub): the proof cannot succeed, skip the pass
-  if (*(const volatile uint32_t *)&ctrl->n_cand == 0u) return;
-  uint32_t *keys = csm, *cnts = csm + kCertSlots, *bk = csm + 2 * kCertSlots;
-  for (uint32_t i = threadIdx.x; i < kCertSlots; i += blockDim.x) {
-    keys[i] = cs->keys[i];
-    cnts[i] = 0u;
+  if (cert_skipped(ctrl)) return;  // no proof possible: the full histogram runs
+  uint32_t *key = csm, *own = csm + kCertBuckets, *bk = csm + 2 * kCertBuckets;
+  for (uint32_t i = threadIdx.x; i < kCertBuckets; i += blockDim.x) {
+    const unsigned long long o = cs->owner[i];
+    key[i] = o ? (uint32_t)~(uint32_t)o + 1u : 0u;
+    own[i] = 0u;
+    bk[i] = 0u;
   }
-  for (uint32_t i = threadIdx.x; i < kCertBuckets; i += blockDim.x) bk[i] = 0u;
   __syncthreads();
   const uint64_t pol = policy_evict_first();
   const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (t == 0 && head) {
     const uint2 e = ld_edge(head);
-    cert_count(e.x, keys, cnts, bk);
-    cert_count(e.y, keys, cnts, bk);
+    cert_count(e.x, key, own, bk);
+    cert_count(e.y, key, own, bk);
   }
   if (t == 1 % T && tail) {
     const uint2 e = ld_edge(tail);
-    cert_count(e.x, keys, cnts, bk);
-    cert_count(e.y, keys, cnts, bk);
+    cert_count(e.x, key, own, bk);
+    cert_count(e.y, key, own, bk);
   }
-  for (uint64_t q = t; q < n_quads; q += T) {
-    const uint4 e = ld_edges(e4 + q, pol);
-    cert_count(e.x, keys, cnts, bk);
-    cert_count(e.y, keys, cnts, bk);
-    cert_count(e.z, keys, cnts, bk);
-    cert_count(e.w, keys, cnts, bk);
+  uint64_t q = t;
+  for (; q + T < n_quads; q += 2 * T) {  // two loads in flight per thread
+    const uint4 a = ld_edges(e4 + q, pol);
+    const uint4 c = ld_edges(e4 + q + T, pol);
+    cert_count(a.x, key, own, bk);
+    cert_count(a.y, key, own, bk);
+    cert_count(a.z, key, own, bk);
+    cert_count(a.w, key, own, bk);
+    cert_count(c.x, key, own, bk);
+    cert_count(c.y, key, own, bk);
+    cert_count(c.z, key, own, bk);
+    cert_count(c.w, key, own, bk);
+  }
+  if (q < n_quads) {
+    const uint4 a = ld_edges(e4 + q, pol);
+    cert_count(a.x, key, own, bk);
+    cert_count(a.y, key, own, bk);
+    cert_count(a.z, key, own, bk);
+    cert_count(a.w, key, own, bk);
   }
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < kCertSlots; i += blockDim.x)
-    if (cnts[i]) atomicAdd(&cs->cand_cnt[i], (unsigned long long)cnts[i]);
-  for (uint32_t i = threadIdx.x; i < kCertBuckets; i += blockDim.x)
+  for (uint32_t i = threadIdx.x; i < kCertBuckets; i += blockDim.x) {
+    if (own[i]) atomicAdd(&cs->cand_cnt[i], (unsigned long long)own[i]);
     if (bk[i]) atomicAdd(&cs->bucket[i], (unsigned long long)bk[i]);
+  }
 }
 
-// The proof (one block): D = best candidate degree; bound = the largest
-// bucket total left after removing the candidates' own occurrences. D > bound
-// means every non-candidate has degree < D.
+// The proof (one block): D = best owner degree (ties to the smaller id);
+// bound = the largest bucket total of non-owners. D > bound means every other
+// vertex has degree < D.
 __global__ void __launch_bounds__(256) k_certify_decide(const CertScratch *cs, Ctrl *ctrl) {
-  extern __shared__ unsigned long long rem[];  // kCertBuckets
-  for (uint32_t b = threadIdx.x; b < kCertBuckets; b += blockDim.x) rem[b] = cs->bucket[b];
-  __syncthreads();
-  unsigned long long best = 0;
+  unsigned long long best = 0, bound = 0;
   bool wide = false;
-  for (uint32_t s = threadIdx.x; s < kCertSlots; s += blockDim.x) {
-    const uint32_t k = cs->keys[s];
-    if (!k) continue;
-    const uint32_t x = k - 1u;
-    const unsigned long long c = cs->cand_cnt[s];
-    atomicAdd(&rem[bucket_of(x)], (unsigned long long)(0ULL - c));
+  const bool skip = cert_skipped(ctrl);
+  for (uint32_t b = threadIdx.x; b < kCertBuckets && !skip; b += blockDim.x) {
+    const unsigned long long o = cs->owner[b];
+    const unsigned long long t = cs->bucket[b];
+    bound = t > bound ? t : bound;
+    if (!o) continue;
+    const unsigned long long c = cs->cand_cnt[b];
     if (c >= (1ULL << 32)) {
       wide = true;
       continue;
     }
-    const unsigned long long key = (c << 32) | (uint32_t)~x;
-    best = key > best ? key : best;
+    const unsigned long long k = (c << 32) | (uint32_t)o;  // low half: ~vertex
+    best = k > best ? k : best;
   }
-  __syncthreads();
-  unsigned long long bound = 0;
-  for (uint32_t b = threadIdx.x; b < kCertBuckets; b += blockDim.x) bound = rem[b] > bound ? rem[b] : bound;
   const int any_wide = __syncthreads_or(wide);
   best = block_max_u64(best);
   bound = block_max_u64(bound);
   if (threadIdx.x == 0) {
     const unsigned long long D = best >> 32;
-    if (!any_wide && best != 0ULL && D > bound) {
+    if (!skip && !any_wide && best != 0ULL && D > bound) {
       ctrl->maxkey = best;
       ctrl->cert = 1u;
     } else {
@@ -344,26 +336,21 @@ cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges
       cudaSuccess)
     return err;
   if ((err = launch_argmax_u32(c32, n, ctrl, s)) != cudaSuccess) return err;
-  // 2. candidates and their table
+  // 2. candidates: the owners of their buckets
   const unsigned gsel = clamp_grid(((uint64_t)n + 255) / 256, persistent_cap((const void *)k_select_candidates, 256, 0));
   k_select_candidates<<<gsel, 256, 0, s>>>(c32, n, ctrl, cs);
   note_launch();
-  k_build_table<<<1, 256, 0, s>>>(ctrl, cs);
-  note_launch();
   // 3. the exact pass in shared memory
-  static std::atomic<unsigned long long> smem_set_certify{0}, smem_set_decide{0};
+  static std::atomic<unsigned long long> smem_set_certify{0};
   if ((err = ensure_func_attr((const void *)k_degree_certify, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)kCertSmem, smem_set_certify)) != cudaSuccess)
-    return err;
-  if ((err = ensure_func_attr((const void *)k_certify_decide, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(kCertBuckets * sizeof(unsigned long long)), smem_set_decide)) != cudaSuccess)
     return err;
   const unsigned gcert = clamp_grid((e.n_quads + 511) / 512, persistent_cap((const void *)k_degree_certify, 512, kCertSmem));
   k_degree_certify<<<gcert, 512, kCertSmem, s>>>(e.quads, e.n_quads, e.head, e.tail, n, cs, ctrl);
   note_launch();
-  // 4. the proof
-  // one small block, so it fits beside resident kernels (the serving executor)
-  k_certify_decide<<<1, 256, kCertBuckets * sizeof(unsigned long long), s>>>(cs, ctrl);
+  // 4. the proof (one small block, so it fits beside resident kernels such as
+  // the serving executor)
+  k_certify_decide<<<1, 256, 0, s>>>(cs, ctrl);
   note_launch();
   // 5. full histogram, skipped when certified
   const uint32_t *skip = &ctrl->cert;

@@ -71,3 +71,61 @@ def test_fullsize_against_oracle_values(name):
         g.run(e, L)
         g.sync()
         assert sha_tensor(L) == gold["labels_min_id_sha256"]
+
+
+def sha_chunked(t, rows=1 << 27) -> str:
+    """SHA-256 of a large device tensor, copied to the host in pieces."""
+    h = hashlib.sha256()
+    for i in range(0, t.shape[0], rows):
+        h.update(t[i:i + rows].contiguous().cpu().numpy().view(np.uint8))
+    return h.hexdigest()
+
+
+def test_fullsize_rmat28_against_oracle_values():
+    """R-MAT scale 28, edge factor 16: 2^32 edges (34.4 GB, 64-bit edge counts,
+    64-bit root-selection counters), run as the benchmark runs it."""
+    path = os.path.join(GOLDEN, "rmat28_ef16.json")
+    if not os.path.exists(path):
+        pytest.skip("tests/golden/rmat28_ef16.json not generated")
+    with open(path) as f:
+        gold = json.load(f)
+    w = graphgen.WORKLOADS["rmat28_ef16"]
+    n = w.n_vertices
+    need = 8 * w.n_edges + 24 * n + (4 << 30)
+    if torch.cuda.get_device_properties(0).total_memory < need:
+        pytest.skip("needs about 45 GB of device memory")
+    e = w.device_edges()
+    torch.cuda.synchronize()
+    assert e.shape[0] == gold["n_edges"] == 1 << 32
+    assert sha_chunked(e) == gold["edges_sha256"], "device generator drifted from the host generator"
+    L = torch.empty(n, dtype=torch.int32, device="cuda")
+    with cc.Graph(n, **bench.BENCH_OPTIONS) as g:
+        for _ in range(2):
+            g.run(e, L)
+            g.sync()
+            assert sha_chunked(L) == gold["labels_min_id_sha256"]
+            assert g.num_components() == gold["num_components"]
+            assert g.root_vertex() == gold["max_degree_vertex"]
+        sample = torch.tensor(gold["sample_vertices"], dtype=torch.int64, device="cuda")
+        assert L[sample].cpu().tolist() == gold["sample_min_id_labels"]
+        Ll = L.long()
+        for i in range(0, e.shape[0], 1 << 28):  # every edge inside one class, in pieces
+            ev = e[i:i + (1 << 28)].long()
+            assert bool((Ll[ev[:, 0]] == Ll[ev[:, 1]]).all())
+            del ev
+        ar = torch.arange(n, device="cuda")
+        assert bool((Ll <= ar).all())
+        assert bool((Ll[Ll] == Ll).all())
+        del ar
+        q = graphgen.pairs_dev(n, 1 << 20, 78)
+        out = torch.empty(q.shape[0], dtype=torch.uint8, device="cuda")
+        g.connected(q, out)
+        g.sync()
+        ql = q.long()
+        assert bool((out.bool() == (Ll[ql[:, 0]] == Ll[ql[:, 1]])).all())
+        del Ll
+    opts = dict(bench.BENCH_OPTIONS, label_space=cc.CC_LABEL_ROOT_VALUE)
+    with cc.Graph(n, **opts) as g:
+        g.run(e, L)
+        g.sync()
+        assert sha_chunked(L) == gold["labels_root_value_sha256"]
