@@ -133,6 +133,20 @@ bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0;
 
 // Root selection (f = R with no hint): the certified exact selection, or the
 // argmax of a histogram over the sampled groups. Leaves m in ctrl->maxkey.
+// The root-select histogram: n counters of 4 bytes, or 8 when wide.
+cudaError_t ensure_cnt(cc_graph *g, bool wide, cudaStream_t s) {
+  const size_t need = (size_t)g->n * (wide ? 8 : 4);
+  if (g->cnt_bytes >= need) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  dev_free(g, g->cnt, g->cnt_bytes);
+  g->cnt = nullptr;
+  g->cnt_bytes = 0;
+  if ((e = dev_alloc(g, &g->cnt, need)) != cudaSuccess) return e;
+  g->cnt_bytes = need;
+  return cudaSuccess;
+}
+
 cc_status root_select(cc_graph *g, const uint32_t *edges, uint64_t n_edges, const cc::EdgeSpan &span,
                       cudaStream_t s, int *m_src) {
   const uint32_t n = (uint32_t)g->n;
@@ -140,14 +154,7 @@ cc_status root_select(cc_graph *g, const uint32_t *edges, uint64_t n_edges, cons
   const bool sampled = g->opt.root_select == CC_ROOT_SELECT_SAMPLED && stride > 1;
   const bool wide = !sampled && n_edges >= (1ULL << 31);
   const size_t need = (size_t)n * (wide ? 8 : 4);
-  if (g->cnt_bytes < need) {
-    CC_TRY(cudaStreamSynchronize(s));
-    dev_free(g, g->cnt, g->cnt_bytes);
-    g->cnt = nullptr;
-    g->cnt_bytes = 0;
-    CC_TRY(dev_alloc(g, &g->cnt, need));
-    g->cnt_bytes = need;
-  }
+  CC_TRY(ensure_cnt(g, wide, s));
   *m_src = cc::kMFromPackedMax;
   if (sampled) {
     CC_TRY(cudaMemsetAsync(g->cnt, 0, need, s));
@@ -341,7 +348,7 @@ cc_status cc_run(cc_graph *g, const uint32_t *edges_dev, uint64_t n_edges, uint3
   CC_TRY(cc::launch_init(g->rf, g->P, n, g->ctrl, m_src, hint, s));
   record(g, 2, s);
   CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), span, g->P, n, g->ctrl,
-                              false, s));
+                              nullptr, s));
   record(g, 3, s);
   CC_TRY(cc::launch_flatten(g->rf, g->opt.label_space, g->P, n, L_out_dev, g->ctrl, s));
   record(g, 4, s);
@@ -361,35 +368,52 @@ cc_status cc_run_host(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges,
   const uint32_t n = (uint32_t)g->n;
   if (L_out_host && !g->label_dev) CC_TRY(dev_alloc(g, (void **)&g->label_dev, (size_t)n * 4));
   // When m is known before the edges arrive (identity, or a hint), the edge
-  // pass runs on each chunk as soon as it lands; otherwise the root selection
-  // needs every edge first, and the copies only overlap each other.
+  // pass runs on each chunk as soon as it lands. Exact selection takes the
+  // chunked route: a speculative m' from the first chunk, hooking and the
+  // certificate's counts per chunk, and a rerun only when m' was not the
+  // exact answer. Sampled selection needs every edge first.
   const bool select = g->rf && g->opt.root_hint == CC_ROOT_AUTO;
+  const bool chunked = select && g->opt.root_select != CC_ROOT_SELECT_SAMPLED;
   const uint32_t hint = (g->rf && !select) ? (uint32_t)g->opt.root_hint : 0u;
+  const bool wide = n_edges >= (1ULL << 31);
+  if (chunked) CC_TRY(ensure_cnt(g, wide, s));
   if (!select) CC_TRY(cc::launch_init(g->rf, g->P, n, g->ctrl, cc::kMFromHint, hint, s));
   // the copy stream starts after everything already enqueued on s
   CC_TRY(cudaEventRecord(g->copy_ev, s));
   CC_TRY(cudaStreamWaitEvent(g->copy_stream, g->copy_ev, 0));
+  const uint32_t *no_spec = &g->ctrl->skip[cc::kSkipSpec];
   for (uint64_t off = 0; off < n_edges; off += kHostChunk) {
     const uint64_t cnt = (n_edges - off) < kHostChunk ? (n_edges - off) : kHostChunk;
     CC_TRY(cudaMemcpyAsync(g->staging + 2 * off, edges_host + 2 * off, cnt * 8, cudaMemcpyHostToDevice,
                            g->copy_stream));
-    if (!select) {
-      CC_TRY(cudaEventRecord(g->copy_ev, g->copy_stream));
-      CC_TRY(cudaStreamWaitEvent(s, g->copy_ev, 0));
-      CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g),
-                                  cc::split_edges(g->staging + 2 * off, cnt), g->P, n, g->ctrl, false, s));
-    }
-  }
-  if (select) {
+    if (select && !chunked) continue;
     CC_TRY(cudaEventRecord(g->copy_ev, g->copy_stream));
     CC_TRY(cudaStreamWaitEvent(s, g->copy_ev, 0));
-    const cc::EdgeSpan all = cc::split_edges(g->staging, n_edges);
+    const cc::EdgeSpan chunk = cc::split_edges(g->staging + 2 * off, cnt);
+    if (chunked && off == 0) {
+      CC_TRY(cc::chunked_select_begin(g->staging, cnt, g->cnt, wide, n, g->cert, g->ctrl, s));
+      CC_TRY(cc::launch_init(true, g->P, n, g->ctrl, cc::kMFromPackedMax, 0u, s, no_spec));
+    }
+    if (chunked) CC_TRY(cc::chunked_select_chunk(chunk, g->cnt, wide, n, g->cert, g->ctrl, s));
+    CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), chunk, g->P, n, g->ctrl,
+                                chunked ? no_spec : nullptr, s));
+  }
+  const cc::EdgeSpan all = cc::split_edges(g->staging, n_edges);
+  if (chunked) {
+    if (n_edges == 0) CC_TRY(cc::chunked_select_begin(g->staging, 0, g->cnt, wide, n, g->cert, g->ctrl, s));
+    CC_TRY(cc::chunked_select_end(all, g->cnt, wide, n, g->cert, g->ctrl, s));
+    const uint32_t *held = &g->ctrl->skip[cc::kSkipRerun];
+    CC_TRY(cc::launch_init(true, g->P, n, g->ctrl, cc::kMFromPackedMax, 0u, s, held));
+    CC_TRY(cc::launch_edge_pass(true, eff_filter(g), eff_ept(g), eff_block(g), all, g->P, n, g->ctrl, held, s));
+  } else if (select) {
+    CC_TRY(cudaEventRecord(g->copy_ev, g->copy_stream));
+    CC_TRY(cudaStreamWaitEvent(s, g->copy_ev, 0));
     int m_src = cc::kMFromHint;
     cc_status st = root_select(g, g->staging, n_edges, all, s, &m_src);
     if (st != CC_OK) return st;
     CC_TRY(cc::launch_init(g->rf, g->P, n, g->ctrl, m_src, hint, s));
     CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), all, g->P, n, g->ctrl,
-                                false, s));
+                                nullptr, s));
   }
   CC_TRY(cc::launch_flatten(g->rf, g->opt.label_space, g->P, n, L_out_host ? g->label_dev : nullptr,
                             g->ctrl, s));
@@ -410,7 +434,7 @@ cc_status cc_stream_insert(cc_graph *g, const uint32_t *edges_dev, uint64_t n_ed
   CC_TRY(cudaMemsetAsync(&g->ctrl->reject, 0, sizeof(uint32_t), s));
   CC_TRY(cc::launch_validate(span, (uint32_t)g->n, g->ctrl, s));
   CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), span, g->P,
-                              (uint32_t)g->n, g->ctrl, true, s));
+                              (uint32_t)g->n, g->ctrl, &g->ctrl->reject, s));
   g->ncomp_fresh = false;
   return CC_OK;
 }

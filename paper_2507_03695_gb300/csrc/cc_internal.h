@@ -35,6 +35,7 @@ struct alignas(128) Ctrl {
   uint32_t reject;            // the insert batch being applied failed validation
   uint32_t n_cand;            // root select: candidates found by the sampled pass
   uint32_t cert;              // root select: 1 when the candidate pass proved the argmax
+  uint32_t skip[4];           // chunked root select: skip words (kSkip*), set on the device
   unsigned long long stats[4];  // optional edge-pass counters
 };
 static_assert(offsetof(Ctrl, q_u) % 8 == 0, "the query pair is loaded with an 8-byte access");
@@ -92,8 +93,10 @@ inline uint64_t persistent_cap(const void *kernel, int block, size_t smem) {
 void note_launch();
 unsigned long long launch_count();
 
+// skip: when not null and the word it points to is nonzero at run time, the
+// kernel does nothing (device-side choice between enqueued alternatives).
 cudaError_t launch_init(bool rf, uint32_t *P, uint32_t n, Ctrl *ctrl, int m_src, uint32_t m_hint,
-                        cudaStream_t s);
+                        cudaStream_t s, const uint32_t *skip = nullptr);
 // Scratch of the certified exact root selection (cc_rootsel.cu).
 constexpr uint32_t kCertCand = 4096;     // more candidates than this: no proof is tried
 constexpr uint32_t kCertBuckets = 8192;  // hash buckets of the degree bound, one owner each
@@ -103,6 +106,27 @@ struct CertScratch {
   unsigned long long cand_cnt[kCertBuckets];  // exact degree of the owner
   unsigned long long bucket[kCertBuckets];    // endpoint occurrences of the other vertices
 };
+
+// Chunked exact root selection, for edges that arrive in chunks (host input):
+// a dense sample of the first chunk picks candidates and a speculative m'.
+// With a plausible hub, every chunk is hooked under m' as it lands while the
+// certificate's counts accumulate; without one, every chunk adds to the full
+// histogram instead. After the last chunk the device decides: m' proved exact
+// (keep the hooking), or the exact m is known (certificate or histogram) and
+// init plus one edge pass over all edges run again. Kernels read the Ctrl
+// skip words, so the host enqueues every alternative without waiting.
+enum : int {
+  kSkipSpec = 0,      // nonzero: no speculation (init under m' and the per-chunk edge passes skip)
+  kSkipHist = 1,      // nonzero: speculating (the per-chunk histogram and its argmax skip)
+  kSkipRerun = 2,     // nonzero: m' was exact (the final init and edge pass skip)
+  kSkipFullHist = 3,  // nonzero unless speculation failed without a certificate
+};
+cudaError_t chunked_select_begin(const uint32_t *chunk0, uint64_t n0, void *cnt, bool wide, uint32_t n,
+                                 CertScratch *cs, Ctrl *ctrl, cudaStream_t s);
+cudaError_t chunked_select_chunk(const EdgeSpan &chunk, void *cnt, bool wide, uint32_t n, CertScratch *cs,
+                                 Ctrl *ctrl, cudaStream_t s);
+cudaError_t chunked_select_end(const EdgeSpan &all, void *cnt, bool wide, uint32_t n, CertScratch *cs,
+                               Ctrl *ctrl, cudaStream_t s);
 
 // Certified exact root selection: sampled candidates, one exact pass over all
 // edges counting candidate degrees and bucket totals in shared memory, a
@@ -119,7 +143,7 @@ cudaError_t launch_degree_sampled_u32(const uint2 *edges, uint64_t n_edges, uint
                                       uint32_t stride, uint32_t *cnt, uint32_t n, cudaStream_t s);
 cudaError_t launch_argmax_u32(const uint32_t *cnt, uint32_t n, Ctrl *ctrl, cudaStream_t s);
 cudaError_t launch_edge_pass(bool rf, int filter, int ept, int block, const EdgeSpan &e, uint32_t *P,
-                             uint32_t n, Ctrl *ctrl, bool check_reject, cudaStream_t s);
+                             uint32_t n, Ctrl *ctrl, const uint32_t *skip, cudaStream_t s);
 cudaError_t launch_validate(const EdgeSpan &e, uint32_t n, Ctrl *ctrl, cudaStream_t s);
 cudaError_t launch_flatten(bool rf, int label_space, uint32_t *P, uint32_t n, uint32_t *L, Ctrl *ctrl,
                            cudaStream_t s);

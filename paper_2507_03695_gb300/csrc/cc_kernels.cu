@@ -24,7 +24,8 @@ int g_num_sms = 0;
 
 template <class F>
 __global__ void __launch_bounds__(256) k_init(uint32_t *__restrict__ P, uint32_t n, Ctrl *ctrl,
-                                              int m_src, uint32_t m_hint) {
+                                              int m_src, uint32_t m_hint, const uint32_t *skip) {
+  if (skip && ld_volatile_u32(skip)) return;
   uint32_t m = 0;
   if (F::kRF) {
     if (m_src == kMFromHint)
@@ -89,8 +90,8 @@ template <class F, int Q>
 __global__ void __launch_bounds__(512) k_edge_pass_direct(const uint4 *__restrict__ e4,
                                                           uint64_t n_quads, const uint2 *head,
                                                           const uint2 *tail, uint32_t *P,
-                                                          uint32_t n, Ctrl *ctrl, int check_reject) {
-  if (check_reject && ld_volatile_u32(&ctrl->reject)) return;
+                                                          uint32_t n, Ctrl *ctrl, const uint32_t *skip) {
+  if (skip && ld_volatile_u32(skip)) return;
   const F fn = F::load(ctrl);
   uint32_t *const S = slots<F>(P);
   const uint64_t pol = policy_evict_first();
@@ -131,9 +132,9 @@ __global__ void __launch_bounds__(512) k_edge_pass_filtered(const uint4 *__restr
                                                             uint64_t n_quads, const uint2 *head,
                                                             const uint2 *tail, uint32_t *P,
                                                             uint32_t n, Ctrl *ctrl,
-                                                            int check_reject) {
+                                                            const uint32_t *skip) {
   extern __shared__ uint32_t ring_smem[];
-  if (check_reject && ld_volatile_u32(&ctrl->reject)) return;
+  if (skip && ld_volatile_u32(skip)) return;
   const F fn = F::load(ctrl);
   uint32_t *const S = slots<F>(P);
   const uint64_t pol = policy_evict_first();
@@ -386,14 +387,14 @@ EdgeSpan split_edges(const uint32_t *edges, uint64_t n_edges) {
 }
 
 cudaError_t launch_init(bool rf, uint32_t *P, uint32_t n, Ctrl *ctrl, int m_src, uint32_t m_hint,
-                        cudaStream_t s) {
+                        cudaStream_t s, const uint32_t *skip) {
   const uint64_t work = n / 4u + 1u;
   if (rf) {
     const unsigned g = clamp_grid((work + 255) / 256, persistent_cap((const void *)k_init<RootR>, 256, 0));
-    k_init<RootR><<<g, 256, 0, s>>>(P, n, ctrl, m_src, m_hint); note_launch();
+    k_init<RootR><<<g, 256, 0, s>>>(P, n, ctrl, m_src, m_hint, skip); note_launch();
   } else {
     const unsigned g = clamp_grid((work + 255) / 256, persistent_cap((const void *)k_init<RootId>, 256, 0));
-    k_init<RootId><<<g, 256, 0, s>>>(P, n, ctrl, m_src, m_hint); note_launch();
+    k_init<RootId><<<g, 256, 0, s>>>(P, n, ctrl, m_src, m_hint, skip); note_launch();
   }
   return cudaGetLastError();
 }
@@ -401,7 +402,7 @@ cudaError_t launch_init(bool rf, uint32_t *P, uint32_t n, Ctrl *ctrl, int m_src,
 namespace {
 template <class F, int Q>
 cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, uint32_t n, Ctrl *ctrl,
-                        bool check_reject, cudaStream_t s) {
+                        const uint32_t *skip, cudaStream_t s) {
   const uint64_t per_block = (uint64_t)block * Q;
   if (filter) {
     const size_t smem = (size_t)(block / 32) * 4 * kRing * sizeof(uint32_t);
@@ -410,33 +411,33 @@ cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, u
                   "the ring of a 1024-thread block fits the default dynamic shared memory limit");
     const unsigned g = clamp_grid((e.n_quads + per_block - 1) / per_block, persistent_cap(k, block, smem));
     k_edge_pass_filtered<F, Q><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
-                                                      check_reject ? 1 : 0); note_launch();
+                                                      skip); note_launch();
   } else {
     const void *k = (const void *)k_edge_pass_direct<F, Q>;
     const unsigned g = clamp_grid((e.n_quads + per_block - 1) / per_block, persistent_cap(k, block, 0));
     k_edge_pass_direct<F, Q><<<g, block, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
-                                                 check_reject ? 1 : 0); note_launch();
+                                                 skip); note_launch();
   }
   return cudaGetLastError();
 }
 
 template <class F>
 cudaError_t edge_pass_f(int filter, int ept, int block, const EdgeSpan &e, uint32_t *P, uint32_t n,
-                        Ctrl *ctrl, bool check_reject, cudaStream_t s) {
+                        Ctrl *ctrl, const uint32_t *skip, cudaStream_t s) {
   switch (ept) {
-    case 2: return edge_pass_q<F, 1>(filter, block, e, P, n, ctrl, check_reject, s);
-    case 8: return edge_pass_q<F, 4>(filter, block, e, P, n, ctrl, check_reject, s);
-    default: return edge_pass_q<F, 2>(filter, block, e, P, n, ctrl, check_reject, s);
+    case 2: return edge_pass_q<F, 1>(filter, block, e, P, n, ctrl, skip, s);
+    case 8: return edge_pass_q<F, 4>(filter, block, e, P, n, ctrl, skip, s);
+    default: return edge_pass_q<F, 2>(filter, block, e, P, n, ctrl, skip, s);
   }
 }
 }  // namespace
 
 cudaError_t launch_edge_pass(bool rf, int filter, int ept, int block, const EdgeSpan &e, uint32_t *P,
-                             uint32_t n, Ctrl *ctrl, bool check_reject, cudaStream_t s) {
+                             uint32_t n, Ctrl *ctrl, const uint32_t *skip, cudaStream_t s) {
   if (block != 128 && block != 256 && block != 512) block = 256;
   if (e.n_quads == 0 && !e.head && !e.tail) return cudaSuccess;
-  return rf ? edge_pass_f<RootR>(filter, ept, block, e, P, n, ctrl, check_reject, s)
-            : edge_pass_f<RootId>(filter, ept, block, e, P, n, ctrl, check_reject, s);
+  return rf ? edge_pass_f<RootR>(filter, ept, block, e, P, n, ctrl, skip, s)
+            : edge_pass_f<RootId>(filter, ept, block, e, P, n, ctrl, skip, s);
 }
 
 cudaError_t launch_validate(const EdgeSpan &e, uint32_t n, Ctrl *ctrl, cudaStream_t s) {

@@ -291,6 +291,28 @@ __global__ void __launch_bounds__(256) k_certify_decide(const CertScratch *cs, C
   }
 }
 
+// Chunked selection: after the first chunk's candidates are known, decide
+// whether to speculate (a hub that a certificate can prove).
+__global__ void k_spec_begin(Ctrl *ctrl) {
+  const uint32_t nc = *(volatile uint32_t *)&ctrl->n_cand;
+  const bool spec = nc != 0u && nc <= kCertCand;
+  ctrl->skip[kSkipSpec] = spec ? 0u : 1u;
+  ctrl->skip[kSkipHist] = spec ? 1u : 0u;
+  ctrl->skip[kSkipRerun] = 0u;
+  ctrl->skip[kSkipFullHist] = 1u;
+}
+
+// After the certificate's decision: did the speculative m' (planted by the
+// first init, ctrl->m) turn out to be the exact maximum-degree vertex?
+__global__ void k_spec_end(Ctrl *ctrl) {
+  const bool spec = *(volatile uint32_t *)&ctrl->skip[kSkipSpec] == 0u;
+  const bool cert = *(volatile uint32_t *)&ctrl->cert != 0u;
+  const uint32_t best = ~(uint32_t)(*(volatile unsigned long long *)&ctrl->maxkey);
+  const bool held = spec && cert && best == *(volatile uint32_t *)&ctrl->m;
+  ctrl->skip[kSkipRerun] = held ? 1u : 0u;
+  ctrl->skip[kSkipFullHist] = (spec && !cert) ? 0u : 1u;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
@@ -377,6 +399,110 @@ cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges
     note_launch();
   }
   return cudaGetLastError();
+}
+
+// ------------------------------------------------- chunked root selection
+
+namespace {
+constexpr uint32_t kChunk0Sample = 16;  // the first chunk keeps 1 group of 1024 edges in 16
+
+cudaError_t launch_histogram(const EdgeSpan &e, void *cnt, bool wide, uint32_t n, const uint32_t *skip,
+                             cudaStream_t s) {
+  const unsigned gd = clamp_grid((e.n_quads + 255) / 256, persistent_cap((const void *)k_degree<uint32_t>, 256, 0));
+  if (wide)
+    k_degree<unsigned long long><<<gd, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail,
+                                                    static_cast<unsigned long long *>(cnt), n, skip);
+  else
+    k_degree<uint32_t><<<gd, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, static_cast<uint32_t *>(cnt), n,
+                                          skip);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero(void *cnt, bool wide, uint32_t n, const uint32_t *skip, cudaStream_t s) {
+  const unsigned gz = clamp_grid(((uint64_t)n + 255) / 256, persistent_cap((const void *)k_zero_cnt<uint32_t>, 256, 0));
+  if (wide)
+    k_zero_cnt<unsigned long long><<<gz, 256, 0, s>>>(static_cast<unsigned long long *>(cnt), n, skip);
+  else
+    k_zero_cnt<uint32_t><<<gz, 256, 0, s>>>(static_cast<uint32_t *>(cnt), n, skip);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// argmax of a complete histogram into ctrl->maxkey (64-bit counts: through
+// maxcnt, m_sel and k_finalize_m)
+cudaError_t launch_hist_argmax(void *cnt, bool wide, uint32_t n, Ctrl *ctrl, const uint32_t *skip,
+                               cudaStream_t s) {
+  const unsigned gz = clamp_grid(((uint64_t)n + 255) / 256, persistent_cap((const void *)k_zero_cnt<uint32_t>, 256, 0));
+  if (wide) {
+    unsigned long long *c64 = static_cast<unsigned long long *>(cnt);
+    k_maxcnt_u64<<<gz, 256, 0, s>>>(c64, n, ctrl, skip);
+    note_launch();
+    k_minid_u64<<<gz, 256, 0, s>>>(c64, n, ctrl, skip);
+    note_launch();
+    k_finalize_m<<<1, 1, 0, s>>>(ctrl, skip);
+    note_launch();
+  } else {
+    k_argmax_u32<<<gz, 256, 0, s>>>(static_cast<const uint32_t *>(cnt), n, ctrl, skip);
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t chunked_select_begin(const uint32_t *chunk0, uint64_t n0, void *cnt, bool wide, uint32_t n,
+                                 CertScratch *cs, Ctrl *ctrl, cudaStream_t s) {
+  cudaError_t err;
+  if ((err = cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(uint32_t), s)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(cs, 0, sizeof(CertScratch), s)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(&ctrl->maxkey, 0, 2 * sizeof(unsigned long long), s)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(&ctrl->m_sel, 0xFF, sizeof(uint32_t), s)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(&ctrl->n_cand, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) return err;
+  uint32_t *c32 = static_cast<uint32_t *>(cnt);
+  if ((err = launch_degree_sampled_u32(reinterpret_cast<const uint2 *>(chunk0), n0, 0, kChunk0Sample, c32, n, s)) !=
+      cudaSuccess)
+    return err;
+  if ((err = launch_argmax_u32(c32, n, ctrl, s)) != cudaSuccess) return err;
+  const unsigned gsel = clamp_grid(((uint64_t)n + 255) / 256, persistent_cap((const void *)k_select_candidates, 256, 0));
+  k_select_candidates<<<gsel, 256, 0, s>>>(c32, n, ctrl, cs);
+  note_launch();
+  k_spec_begin<<<1, 1, 0, s>>>(ctrl);
+  note_launch();
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  // without speculation the chunks build the full histogram: start it at zero
+  return launch_zero(cnt, wide, n, &ctrl->skip[kSkipHist], s);
+}
+
+cudaError_t chunked_select_chunk(const EdgeSpan &chunk, void *cnt, bool wide, uint32_t n, CertScratch *cs,
+                                 Ctrl *ctrl, cudaStream_t s) {
+  cudaError_t err;
+  if ((err = launch_histogram(chunk, cnt, wide, n, &ctrl->skip[kSkipHist], s)) != cudaSuccess) return err;
+  static std::atomic<unsigned long long> smem_set_certify{0};
+  if ((err = ensure_func_attr((const void *)k_degree_certify, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kCertSmem, smem_set_certify)) != cudaSuccess)
+    return err;
+  const unsigned gcert =
+      clamp_grid((chunk.n_quads + 511) / 512, persistent_cap((const void *)k_degree_certify, 512, kCertSmem));
+  k_degree_certify<<<gcert, 512, kCertSmem, s>>>(chunk.quads, chunk.n_quads, chunk.head, chunk.tail, n, cs, ctrl);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t chunked_select_end(const EdgeSpan &all, void *cnt, bool wide, uint32_t n, CertScratch *cs,
+                               Ctrl *ctrl, cudaStream_t s) {
+  cudaError_t err;
+  k_certify_decide<<<1, 256, 0, s>>>(cs, ctrl);
+  note_launch();
+  k_spec_end<<<1, 1, 0, s>>>(ctrl);
+  note_launch();
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  // no speculation: the chunks built the full histogram
+  if ((err = launch_hist_argmax(cnt, wide, n, ctrl, &ctrl->skip[kSkipHist], s)) != cudaSuccess) return err;
+  // speculation without a certificate: the full histogram over all edges now
+  const uint32_t *full = &ctrl->skip[kSkipFullHist];
+  if ((err = launch_zero(cnt, wide, n, full, s)) != cudaSuccess) return err;
+  if ((err = launch_histogram(all, cnt, wide, n, full, s)) != cudaSuccess) return err;
+  return launch_hist_argmax(cnt, wide, n, ctrl, full, s);
 }
 
 }  // namespace cc

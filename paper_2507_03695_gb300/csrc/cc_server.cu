@@ -573,7 +573,7 @@ bool start_new_graph(cc_server *s, Req *r, GraphState &g) {
     m_src = cc::kMFromPackedMax;
   }
   if (e == cudaSuccess && n) e = cc::launch_init(rf, g.P, n, g.ctrl, m_src, 0u, ss);
-  if (e == cudaSuccess && n) e = cc::launch_edge_pass(rf, 1, 4, 256, span, g.P, n, g.ctrl, false, ss);
+  if (e == cudaSuccess && n) e = cc::launch_edge_pass(rf, 1, 4, 256, span, g.P, n, g.ctrl, nullptr, ss);
   if (e == cudaSuccess && n) e = cc::launch_flatten(rf, s->cfg.label_space, g.P, n, r->r.labels_dev, g.ctrl, ss);
   const uint32_t gid = r->graph;
   if (e == cudaSuccess)
@@ -869,7 +869,7 @@ cudaError_t warm_up(cc_server *s) {
       m_src = cc::kMFromPackedMax;
     }
     if (e == cudaSuccess) e = cc::launch_init(rf, P, n, ctrl, m_src, 0u, ss);
-    if (e == cudaSuccess) e = cc::launch_edge_pass(rf, 1, 4, 256, span, P, n, ctrl, false, ss);
+    if (e == cudaSuccess) e = cc::launch_edge_pass(rf, 1, 4, 256, span, P, n, ctrl, nullptr, ss);
     if (e == cudaSuccess) e = cc::launch_flatten(rf, s->cfg.label_space, P, n, labels, ctrl, ss);
     if (e == cudaSuccess) e = cc::launch_flatten(rf, s->cfg.label_space, P, n, nullptr, ctrl, ss);
     if (e == cudaSuccess) {

@@ -279,6 +279,57 @@ def test_run_host_buffers(mode, select):
             cc.cc_run_host(g.h, host, E + 1, L)
 
 
+def _chunked_case(kind):
+    """Host inputs of several 2^24-edge copy chunks, built so that each route
+    of the chunked exact root selection in cc_run_host is taken."""
+    C = 1 << 24
+    if kind == "rmat":  # dominant hub, certified from the first chunk: the speculation holds
+        return 1 << 20, graphgen.rmat(20, 3 * C + 77, 61, scramble=True)
+    if kind == "er":  # no hub: every chunk feeds the full histogram
+        return 1 << 22, graphgen.er(1 << 22, 2 * C + 5, 62)
+    n = 1 << 20
+    e = graphgen.er(n, 2 * C + 123, 63)  # background: degree about 64
+    rng = np.random.default_rng(64)
+    first = rng.permutation(C)[:50000]
+    later = C + rng.permutation(len(e) - C)[:100000]
+    h1, h2 = 777, 4242
+
+    def star(h, idx):
+        e[idx, 0] = h
+        e[idx, 1] = rng.integers(0, n, size=len(idx), dtype=np.uint32)
+
+    if kind == "late_hub":  # the true hub never appears in the first chunk: no certificate
+        star(h1, first[:20000])
+        star(h2, later)
+    else:  # two hubs: the first chunk's leader is not the overall one (certificate, rerun)
+        star(h1, first[:30000])
+        star(h2, first[30000:50000])
+        star(h2, later[:40000])
+    return n, e
+
+
+@pytest.mark.parametrize("kind", ["rmat", "er", "late_hub", "two_hubs"])
+def test_run_host_chunked_selection(kind):
+    n, e = _chunked_case(kind)
+    E = len(e)
+    m = oracle.max_degree_vertex(n, e)
+    if kind == "late_hub":
+        assert m == 4242
+    if kind == "two_hubs":
+        assert m == 4242
+    host = torch.from_numpy(e.view(np.int32)).pin_memory()
+    L = torch.empty(n, dtype=torch.int32).pin_memory()
+    with cc.Graph(n, E) as g:
+        for _ in range(2):  # the second run reuses every buffer
+            cc.cc_run_host(g.h, host, None, L)
+            np.testing.assert_array_equal(L.numpy().view(np.uint32), oracle.min_labels(n, e))
+            assert g.root_vertex() == m
+    with cc.Graph(n, E, label_space=cc.CC_LABEL_ROOT_VALUE) as g:
+        cc.cc_run_host(g.h, host, None, L)
+        assert g.root_vertex() == m
+        np.testing.assert_array_equal(L.numpy().view(np.uint32), oracle.root_value_labels(n, e, m))
+
+
 def test_phase_times_and_budget():
     n = 1 << 16
     e = graphgen.rmat(16, 1 << 20, 1, scramble=False)
