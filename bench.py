@@ -398,7 +398,8 @@ def run_ours(args):
                        "root_function": "R of Eq. 1 (max-degree vertex planted as 0)",
                        "root_select": "exact degree histogram", "labels": "min vertex id",
                        "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (edge arrays of 2.1 GB and 0.97 GB vs 129 MB L2)"},
+                       "l2": "inputs larger than L2 (edge arrays of "
+                             + " and ".join(f"{8 * E / 1e9:.2f} GB" for _, _, E in graphs) + " vs 129 MB L2)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
                          "traffic": sum(traffic.values()) / len(traffic) if traffic else None,

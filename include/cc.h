@@ -82,11 +82,21 @@ typedef enum cc_root_select {
 
 /* Warp-level pre-filter of the edge pass: an edge whose endpoints already
  * hold the same parent value is dropped before any root search; survivors are
- * compacted so that whole warps search roots together. */
+ * compacted so that whole warps search roots together.
+ *
+ * CC_FILTER_BITMAP adds the zero-tree bitmap: one bit per vertex (n / 8
+ * bytes of device memory), set once the vertex is known to belong to the tree
+ * of root value 0 (the planted vertex m under R; vertex 0 under the identity).
+ * The filter then skips the parent load of such an endpoint. It pays off when
+ * P is larger than the GPU's L2 and most edges lie in m's component (the
+ * skewed graphs that Zero Planting, Section IV, targets). CC_FILTER_AUTO uses
+ * it under R with exact root selection when P exceeds 128 MiB, and only on
+ * runs whose selection certified a dominant hub (decided on the device). */
 typedef enum cc_filter {
   CC_FILTER_AUTO = 0,
   CC_FILTER_ON = 1,
-  CC_FILTER_OFF = 2
+  CC_FILTER_OFF = 2,
+  CC_FILTER_BITMAP = 3
 } cc_filter;
 
 /* Label written to L. */

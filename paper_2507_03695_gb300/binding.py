@@ -31,7 +31,7 @@ CC_ERR_NOT_READY = 8
 # cc_root_mode / cc_root_select / cc_filter / cc_label_space
 CC_ROOT_IDENTITY, CC_ROOT_MAXDEG = 0, 1
 CC_ROOT_SELECT_EXACT, CC_ROOT_SELECT_SAMPLED = 0, 1
-CC_FILTER_AUTO, CC_FILTER_ON, CC_FILTER_OFF = 0, 1, 2
+CC_FILTER_AUTO, CC_FILTER_ON, CC_FILTER_OFF, CC_FILTER_BITMAP = 0, 1, 2, 3
 CC_LABEL_MIN_ID, CC_LABEL_ROOT_VALUE = 0, 1
 
 

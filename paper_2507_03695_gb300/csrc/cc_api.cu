@@ -39,12 +39,25 @@ struct cc_graph {
   bool timed_run = false;
   bool ncomp_fresh = false;
   uint64_t owned = 0;
+  uint32_t *z = nullptr;   // zero-tree bitmap (one bit per name), or null
+  size_t z_bytes = 0;
+  bool z_forced = false;   // CC_FILTER_BITMAP: always used
+  bool z_auto_ok = false;  // the last run's exact selection left ctrl->cert meaningful
 };
 
 namespace {
 
 constexpr uint64_t kMaxVertices = 0x7FFFFFFFULL;
 constexpr uint64_t kHostChunk = 1ULL << 24;  // edges per cc_run_host copy chunk
+constexpr uint64_t kZMinBytes = 128ULL << 20;  // CC_FILTER_AUTO: P at least this large gets the bitmap
+
+// Bitmap bytes for names 0 .. n (n + 1 names under R), whole 32-bit words.
+size_t z_bytes_for(uint64_t n) { return (size_t)((n + 1 + 31) / 32) * 4; }
+
+bool wants_z(const cc_options &o, uint64_t n) {
+  if (o.filter == CC_FILTER_BITMAP) return true;
+  return o.filter == CC_FILTER_AUTO && o.mode == CC_ROOT_MAXDEG && (uint64_t)n * 4 >= kZMinBytes;
+}
 
 struct DeviceGuard {
   int prev = -1;
@@ -75,7 +88,7 @@ cc_status from_cuda(cudaError_t e) {
 bool opts_valid(const cc_options &o) {
   if (o.mode != CC_ROOT_IDENTITY && o.mode != CC_ROOT_MAXDEG) return false;
   if (o.root_select != CC_ROOT_SELECT_EXACT && o.root_select != CC_ROOT_SELECT_SAMPLED) return false;
-  if (o.filter < CC_FILTER_AUTO || o.filter > CC_FILTER_OFF) return false;
+  if (o.filter < CC_FILTER_AUTO || o.filter > CC_FILTER_BITMAP) return false;
   if (o.label_space != CC_LABEL_MIN_ID && o.label_space != CC_LABEL_ROOT_VALUE) return false;
   if (o.block_size != 0 && o.block_size != 128 && o.block_size != 256 && o.block_size != 512)
     return false;
@@ -247,7 +260,7 @@ cc_status cc_create(uint64_t n_vertices, uint64_t n_edges_capacity, const cc_opt
   const bool rf = o.mode == CC_ROOT_MAXDEG;
   const size_t need = p_bytes(n_vertices) +
                       (rf ? (size_t)n_vertices * 4 + sizeof(cc::CertScratch) : 0) + sizeof(Ctrl) +
-                      (size_t)n_edges_capacity * 8;
+                      (size_t)n_edges_capacity * 8 + (wants_z(o, n_vertices) ? z_bytes_for(n_vertices) : 0);
   if (o.hbm_budget_bytes && need > o.hbm_budget_bytes) return CC_ERR_OOM;
 
   cc_graph *g = new (std::nothrow) cc_graph();
@@ -281,6 +294,12 @@ cc_status cc_create(uint64_t n_vertices, uint64_t n_edges_capacity, const cc_opt
       if ((e = dev_alloc(g, (void **)&g->staging, (size_t)n_edges_capacity * 8)) != cudaSuccess) break;
       g->capacity = n_edges_capacity;
     }
+    if (n_vertices && wants_z(o, n_vertices)) {
+      if ((e = dev_alloc(g, (void **)&g->z, z_bytes_for(n_vertices))) != cudaSuccess) break;
+      g->z_bytes = z_bytes_for(n_vertices);
+      g->z_forced = o.filter == CC_FILTER_BITMAP;
+      if ((e = cudaMemset(g->z, 0, g->z_bytes)) != cudaSuccess) break;
+    }
     if ((e = cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking)) != cudaSuccess) break;
     if ((e = cudaEventCreateWithFlags(&g->copy_ev, cudaEventDisableTiming)) != cudaSuccess) break;
     if ((e = cudaMemset(g->ctrl, 0, sizeof(Ctrl))) != cudaSuccess) break;
@@ -312,6 +331,7 @@ void cc_destroy(cc_graph *g) {
   dev_free(g, g->ctrl, sizeof(Ctrl));
   dev_free(g, g->staging, (size_t)g->capacity * 8);
   dev_free(g, g->label_dev, (size_t)g->n * 4);
+  dev_free(g, g->z, g->z_bytes);
   if (g->host_ctrl) cudaFreeHost(g->host_ctrl);
   if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
   if (g->copy_ev) cudaEventDestroy(g->copy_ev);
@@ -346,9 +366,16 @@ cc_status cc_run(cc_graph *g, const uint32_t *edges_dev, uint64_t n_edges, uint3
   }
   record(g, 1, s);
   CC_TRY(cc::launch_init(g->rf, g->P, n, g->ctrl, m_src, hint, s));
+  // the zero-tree bitmap starts empty with every init; without a forced
+  // bitmap it is used when this run's exact selection certified a hub
+  const bool exact = g->rf && g->opt.root_hint == CC_ROOT_AUTO && g->opt.root_select != CC_ROOT_SELECT_SAMPLED;
+  if (g->z) CC_TRY(cudaMemsetAsync(g->z, 0, g->z_bytes, s));
+  g->z_auto_ok = exact && !g->z_forced;
+  uint32_t *Z = (g->z && (g->z_forced || exact)) ? g->z : nullptr;
+  const uint32_t *zsel = (Z && !g->z_forced) ? &g->ctrl->cert : nullptr;
   record(g, 2, s);
   CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), span, g->P, n, g->ctrl,
-                              nullptr, s));
+                              nullptr, s, Z, zsel));
   record(g, 3, s);
   CC_TRY(cc::launch_flatten(g->rf, g->opt.label_space, g->P, n, L_out_dev, g->ctrl, s));
   record(g, 4, s);
@@ -377,6 +404,11 @@ cc_status cc_run_host(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges,
   const uint32_t hint = (g->rf && !select) ? (uint32_t)g->opt.root_hint : 0u;
   const bool wide = n_edges >= (1ULL << 31);
   if (chunked) CC_TRY(ensure_cnt(g, wide, s));
+  // the zero-tree bitmap starts empty; a forced bitmap is used throughout,
+  // an automatic one for the final pass when the certificate allows
+  if (g->z) CC_TRY(cudaMemsetAsync(g->z, 0, g->z_bytes, s));
+  g->z_auto_ok = chunked && !g->z_forced;
+  uint32_t *Zf = g->z_forced ? g->z : nullptr;
   if (!select) CC_TRY(cc::launch_init(g->rf, g->P, n, g->ctrl, cc::kMFromHint, hint, s));
   // the copy stream starts after everything already enqueued on s
   CC_TRY(cudaEventRecord(g->copy_ev, s));
@@ -396,7 +428,7 @@ cc_status cc_run_host(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges,
     }
     if (chunked) CC_TRY(cc::chunked_select_chunk(chunk, g->cnt, wide, n, g->cert, g->ctrl, s));
     CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), chunk, g->P, n, g->ctrl,
-                                chunked ? no_spec : nullptr, s));
+                                chunked ? no_spec : nullptr, s, Zf));
   }
   const cc::EdgeSpan all = cc::split_edges(g->staging, n_edges);
   if (chunked) {
@@ -404,7 +436,12 @@ cc_status cc_run_host(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges,
     CC_TRY(cc::chunked_select_end(all, g->cnt, wide, n, g->cert, g->ctrl, s));
     const uint32_t *held = &g->ctrl->skip[cc::kSkipRerun];
     CC_TRY(cc::launch_init(true, g->P, n, g->ctrl, cc::kMFromPackedMax, 0u, s, held));
-    CC_TRY(cc::launch_edge_pass(true, eff_filter(g), eff_ept(g), eff_block(g), all, g->P, n, g->ctrl, held, s));
+    // a rerun starts from a fresh P in which another vertex holds name 0, so
+    // a forced bitmap must start empty again (when m' held, the reset only
+    // forgets bits: an empty bitmap is always valid)
+    if (Zf) CC_TRY(cudaMemsetAsync(Zf, 0, g->z_bytes, s));
+    CC_TRY(cc::launch_edge_pass(true, eff_filter(g), eff_ept(g), eff_block(g), all, g->P, n, g->ctrl, held, s,
+                                g->z, Zf ? nullptr : &g->ctrl->cert));
   } else if (select) {
     CC_TRY(cudaEventRecord(g->copy_ev, g->copy_stream));
     CC_TRY(cudaStreamWaitEvent(s, g->copy_ev, 0));
@@ -413,7 +450,7 @@ cc_status cc_run_host(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges,
     if (st != CC_OK) return st;
     CC_TRY(cc::launch_init(g->rf, g->P, n, g->ctrl, m_src, hint, s));
     CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), all, g->P, n, g->ctrl,
-                                nullptr, s));
+                                nullptr, s, Zf));
   }
   CC_TRY(cc::launch_flatten(g->rf, g->opt.label_space, g->P, n, L_out_host ? g->label_dev : nullptr,
                             g->ctrl, s));
@@ -433,8 +470,10 @@ cc_status cc_stream_insert(cc_graph *g, const uint32_t *edges_dev, uint64_t n_ed
   const cc::EdgeSpan span = cc::split_edges(edges_dev, n_edges);
   CC_TRY(cudaMemsetAsync(&g->ctrl->reject, 0, sizeof(uint32_t), s));
   CC_TRY(cc::launch_validate(span, (uint32_t)g->n, g->ctrl, s));
+  uint32_t *Z = (g->z && (g->z_forced || g->z_auto_ok)) ? g->z : nullptr;
+  const uint32_t *zsel = (Z && !g->z_forced) ? &g->ctrl->cert : nullptr;
   CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), span, g->P,
-                              (uint32_t)g->n, g->ctrl, &g->ctrl->reject, s));
+                              (uint32_t)g->n, g->ctrl, &g->ctrl->reject, s, Z, zsel));
   g->ncomp_fresh = false;
   return CC_OK;
 }
@@ -592,6 +631,8 @@ cc_status cc_restore(cc_graph *g, const void *host_buf, uint64_t bytes) {
   if (g->n) CC_TRY(cudaMemcpy(g->P, (const char *)host_buf + sizeof(h), g->n * 4, cudaMemcpyHostToDevice));
   g->host_ctrl->m = h.m;
   CC_TRY(cudaMemcpy(&g->ctrl->m, &g->host_ctrl->m, sizeof(uint32_t), cudaMemcpyHostToDevice));
+  if (g->z) CC_TRY(cudaMemset(g->z, 0, g->z_bytes));  // the restored P has its own trees
+  g->z_auto_ok = false;
   g->ncomp_fresh = false;
   return CC_OK;
 }

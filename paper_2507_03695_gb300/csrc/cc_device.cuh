@@ -166,12 +166,13 @@ __device__ __forceinline__ uint32_t root_name(uint32_t *S, uint32_t c, uint32_t 
 // parent, and the search resumes from that root (the current roots, not the
 // original endpoints). Any moment at which both sides show the same parent
 // name proves a common tree and ends the edge, which includes the case of
-// both endpoints already holding 0.
+// both endpoints already holding 0. Returns true when the edge is known to
+// end in the tree of name 0 (both endpoints then belong to it for good).
 template <bool kCG = false>
-__device__ __forceinline__ void unite(uint32_t *S, uint32_t cu, uint32_t pu, uint32_t cv, uint32_t pv) {
+__device__ __forceinline__ bool unite(uint32_t *S, uint32_t cu, uint32_t pu, uint32_t cv, uint32_t pv) {
   if (pu != pv) CC_STAT(0);
   while (true) {
-    if (pu == pv) return;
+    if (pu == pv) return pu == 0u;
     while (pu != cu) {
       if (pu == 0u) {
         cu = 0u;
@@ -182,7 +183,7 @@ __device__ __forceinline__ void unite(uint32_t *S, uint32_t cu, uint32_t pu, uin
       if (pw != pu) stP(S + cu, pw);
       cu = pu;
       pu = pw;
-      if (pu == pv) return;
+      if (pu == pv) return pu == 0u;
     }
     while (pv != cv) {
       if (pv == 0u) {
@@ -194,17 +195,17 @@ __device__ __forceinline__ void unite(uint32_t *S, uint32_t cu, uint32_t pu, uin
       if (pw != pv) stP(S + cv, pw);
       cv = pv;
       pv = pw;
-      if (pu == pv) return;
+      if (pu == pv) return pu == 0u;
     }
-    if (pu == pv) return;  // same root
+    if (pu == pv) return pu == 0u;  // same root
     CC_STAT(2);
     if (pu < pv) {
       const uint32_t old = atomicCAS(S + cv, pv, pu);
-      if (old == pv) return;
+      if (old == pv) return pu == 0u;
       pv = old;  // that root was hooked meanwhile: continue from it
     } else {
       const uint32_t old = atomicCAS(S + cu, pu, pv);
-      if (old == pu) return;
+      if (old == pu) return pv == 0u;
       pu = old;
     }
     CC_STAT(3);
@@ -220,16 +221,32 @@ __device__ __forceinline__ void unite(uint32_t *S, uint32_t cu, uint32_t pu, uin
 // and whenever 32 are queued the whole warp resolves them together, one per
 // lane, so root searches run in dense warps. At most 31 survivors are carried
 // between appends, so 64 entries suffice. All lanes of the warp must call
-// push() and drain() together.
+// push() and drain() together. With a zero-tree bitmap Z (below), an edge that
+// ends in the tree of name 0 marks both endpoint names in it.
 constexpr int kRing = 64;
+
+// The zero-tree bitmap: bit c set means the vertex named c belongs to the
+// tree of name 0 (the planted vertex m under R). Bits are only ever set, and
+// only after a walk or a parent value proved the fact, which holds for good
+// because name 0 is never hooked; a stale 0 bit only costs the parent load
+// it would have saved.
+__device__ __forceinline__ bool zbit(const uint32_t *Z, uint32_t c) {
+  uint32_t w;
+  asm volatile("ld.global.u32 %0, [%1];" : "=r"(w) : "l"(Z + (c >> 5)) : "memory");
+  return (w >> (c & 31u)) & 1u;
+}
+
+__device__ __forceinline__ void zset(uint32_t *Z, uint32_t c) { atomicOr(Z + (c >> 5), 1u << (c & 31u)); }
 
 struct WarpRing {
   uint32_t *cu, *pu, *cv, *pv;
+  uint32_t *Z;  // zero-tree bitmap, or null
   uint32_t head, tail;
   uint32_t lane, lt_mask;
 
   // ring storage for this warp out of 4 * kRing words per warp
-  __device__ __forceinline__ void init(uint32_t *smem_words) {
+  __device__ __forceinline__ void init(uint32_t *smem_words, uint32_t *zero_tree = nullptr) {
+    Z = zero_tree;
     const uint32_t wid = threadIdx.x >> 5;
     cu = smem_words + wid * (4 * kRing);
     pu = cu + kRing;
@@ -257,7 +274,10 @@ struct WarpRing {
       const uint32_t slot = (head + lane) & (kRing - 1);
       const uint32_t sa = cu[slot], spa = pu[slot], sb = cv[slot], spb = pv[slot];
       __syncwarp();
-      unite<kCG>(S, sa, spa, sb, spb);
+      if (unite<kCG>(S, sa, spa, sb, spb) && Z) {
+        zset(Z, sa);
+        zset(Z, sb);
+      }
       head += 32u;
     }
   }
@@ -267,7 +287,11 @@ struct WarpRing {
     __syncwarp();
     if (lane < tail - head) {
       const uint32_t slot = (head + lane) & (kRing - 1);
-      unite<kCG>(S, cu[slot], pu[slot], cv[slot], pv[slot]);
+      const uint32_t a = cu[slot], b = cv[slot];
+      if (unite<kCG>(S, a, pu[slot], b, pv[slot]) && Z) {
+        zset(Z, a);
+        zset(Z, b);
+      }
     }
     head = tail;
     __syncwarp();

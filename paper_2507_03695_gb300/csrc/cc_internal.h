@@ -142,8 +142,12 @@ cudaError_t launch_degree_u32(const EdgeSpan &e, uint32_t *cnt, uint32_t n, cuda
 cudaError_t launch_degree_sampled_u32(const uint2 *edges, uint64_t n_edges, uint64_t edge_base,
                                       uint32_t stride, uint32_t *cnt, uint32_t n, cudaStream_t s);
 cudaError_t launch_argmax_u32(const uint32_t *cnt, uint32_t n, Ctrl *ctrl, cudaStream_t s);
+// Z: the zero-tree bitmap (one bit per name, zeroed at every init), or null.
+// With Z and zsel null only the zero-tree instance runs; with both, the device
+// picks the zero-tree instance when *zsel is nonzero, the plain one otherwise.
 cudaError_t launch_edge_pass(bool rf, int filter, int ept, int block, const EdgeSpan &e, uint32_t *P,
-                             uint32_t n, Ctrl *ctrl, const uint32_t *skip, cudaStream_t s);
+                             uint32_t n, Ctrl *ctrl, const uint32_t *skip, cudaStream_t s,
+                             uint32_t *Z = nullptr, const uint32_t *zsel = nullptr);
 cudaError_t launch_validate(const EdgeSpan &e, uint32_t n, Ctrl *ctrl, cudaStream_t s);
 cudaError_t launch_flatten(bool rf, int label_space, uint32_t *P, uint32_t n, uint32_t *L, Ctrl *ctrl,
                            cudaStream_t s);

@@ -127,19 +127,33 @@ __global__ void __launch_bounds__(512) k_edge_pass_direct(const uint4 *__restric
 // Filtered form: the parent loads of a warp's edges feed the warp ring
 // (cc_device.cuh), which drops edges whose endpoints already share a parent
 // and resolves the survivors in dense warps.
-template <class F, int Q>
+//
+// kZ: the zero-tree bitmap Z (one bit per name, 1/32 of P) stands in front of
+// P. An endpoint whose bit is set belongs to the tree of name 0, so its parent
+// value is taken as 0 without loading P; an edge with both bits set costs no
+// parent load at all. When P is larger than L2 and the giant component hangs
+// under name 0 (R with a dominant hub), this turns most random DRAM reads of
+// P into L2 hits on Z. Bits are set when a parent value of 0 is read and when
+// an edge ends in the tree of name 0.
+//
+// zsel chooses between the two instances at run time: with zsel null both
+// run as launched; otherwise the kZ instance runs only when *zsel is nonzero
+// and the plain one only when it is zero (the host launches both).
+template <class F, int Q, bool kZ>
 __global__ void __launch_bounds__(512) k_edge_pass_filtered(const uint4 *__restrict__ e4,
                                                             uint64_t n_quads, const uint2 *head,
                                                             const uint2 *tail, uint32_t *P,
                                                             uint32_t n, Ctrl *ctrl,
-                                                            const uint32_t *skip) {
+                                                            const uint32_t *skip, uint32_t *Z,
+                                                            const uint32_t *zsel) {
   extern __shared__ uint32_t ring_smem[];
   if (skip && ld_volatile_u32(skip)) return;
+  if (zsel && ((ld_volatile_u32(zsel) != 0u) != kZ)) return;
   const F fn = F::load(ctrl);
   uint32_t *const S = slots<F>(P);
   const uint64_t pol = policy_evict_first();
   WarpRing ring;
-  ring.init(ring_smem);
+  ring.init(ring_smem, kZ ? Z : nullptr);
   const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (t == 0 && head) single_edge(P, fn, head, n, ctrl);
@@ -159,10 +173,38 @@ __global__ void __launch_bounds__(512) k_edge_pass_filtered(const uint4 *__restr
     for (int j = 0; j < Q; ++j) {
       guard(e[j].x, e[j].y, n, ctrl);
       guard(e[j].z, e[j].w, n, ctrl);
-      p[4 * j + 0] = ldP(P + e[j].x);
-      p[4 * j + 1] = ldP(P + e[j].y);
-      p[4 * j + 2] = ldP(P + e[j].z);
-      p[4 * j + 3] = ldP(P + e[j].w);
+    }
+    if (kZ) {
+      uint32_t z = 0;  // bit i: endpoint i is known to be in the tree of name 0
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        z |= (uint32_t)zbit(Z, fn.f(e[j].x)) << (4 * j + 0);
+        z |= (uint32_t)zbit(Z, fn.f(e[j].y)) << (4 * j + 1);
+        z |= (uint32_t)zbit(Z, fn.f(e[j].z)) << (4 * j + 2);
+        z |= (uint32_t)zbit(Z, fn.f(e[j].w)) << (4 * j + 3);
+      }
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        p[4 * j + 0] = (z >> (4 * j + 0)) & 1u ? 0u : ldP(P + e[j].x);
+        p[4 * j + 1] = (z >> (4 * j + 1)) & 1u ? 0u : ldP(P + e[j].y);
+        p[4 * j + 2] = (z >> (4 * j + 2)) & 1u ? 0u : ldP(P + e[j].z);
+        p[4 * j + 3] = (z >> (4 * j + 3)) & 1u ? 0u : ldP(P + e[j].w);
+      }
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        if (!((z >> (4 * j + 0)) & 1u) && p[4 * j + 0] == 0u) zset(Z, fn.f(e[j].x));
+        if (!((z >> (4 * j + 1)) & 1u) && p[4 * j + 1] == 0u) zset(Z, fn.f(e[j].y));
+        if (!((z >> (4 * j + 2)) & 1u) && p[4 * j + 2] == 0u) zset(Z, fn.f(e[j].z));
+        if (!((z >> (4 * j + 3)) & 1u) && p[4 * j + 3] == 0u) zset(Z, fn.f(e[j].w));
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        p[4 * j + 0] = ldP(P + e[j].x);
+        p[4 * j + 1] = ldP(P + e[j].y);
+        p[4 * j + 2] = ldP(P + e[j].z);
+        p[4 * j + 3] = ldP(P + e[j].w);
+      }
     }
 #pragma unroll
     for (int k = 0; k < 2 * Q; ++k) {
@@ -402,16 +444,23 @@ cudaError_t launch_init(bool rf, uint32_t *P, uint32_t n, Ctrl *ctrl, int m_src,
 namespace {
 template <class F, int Q>
 cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, uint32_t n, Ctrl *ctrl,
-                        const uint32_t *skip, cudaStream_t s) {
+                        const uint32_t *skip, uint32_t *Z, const uint32_t *zsel, cudaStream_t s) {
   const uint64_t per_block = (uint64_t)block * Q;
   if (filter) {
     const size_t smem = (size_t)(block / 32) * 4 * kRing * sizeof(uint32_t);
-    const void *k = (const void *)k_edge_pass_filtered<F, Q>;
     static_assert((1024 / 32) * 4 * kRing * sizeof(uint32_t) <= 48 * 1024,
                   "the ring of a 1024-thread block fits the default dynamic shared memory limit");
-    const unsigned g = clamp_grid((e.n_quads + per_block - 1) / per_block, persistent_cap(k, block, smem));
-    k_edge_pass_filtered<F, Q><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
-                                                      skip); note_launch();
+    const uint64_t want = (e.n_quads + per_block - 1) / per_block;
+    if (Z) {  // the zero-tree instance (alone, or chosen on the device by *zsel)
+      const unsigned g = clamp_grid(want, persistent_cap((const void *)k_edge_pass_filtered<F, Q, true>, block, smem));
+      k_edge_pass_filtered<F, Q, true><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
+                                                              skip, Z, zsel); note_launch();
+    }
+    if (!Z || zsel) {
+      const unsigned g = clamp_grid(want, persistent_cap((const void *)k_edge_pass_filtered<F, Q, false>, block, smem));
+      k_edge_pass_filtered<F, Q, false><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
+                                                               skip, nullptr, Z ? zsel : nullptr); note_launch();
+    }
   } else {
     const void *k = (const void *)k_edge_pass_direct<F, Q>;
     const unsigned g = clamp_grid((e.n_quads + per_block - 1) / per_block, persistent_cap(k, block, 0));
@@ -423,21 +472,22 @@ cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, u
 
 template <class F>
 cudaError_t edge_pass_f(int filter, int ept, int block, const EdgeSpan &e, uint32_t *P, uint32_t n,
-                        Ctrl *ctrl, const uint32_t *skip, cudaStream_t s) {
+                        Ctrl *ctrl, const uint32_t *skip, uint32_t *Z, const uint32_t *zsel, cudaStream_t s) {
   switch (ept) {
-    case 2: return edge_pass_q<F, 1>(filter, block, e, P, n, ctrl, skip, s);
-    case 8: return edge_pass_q<F, 4>(filter, block, e, P, n, ctrl, skip, s);
-    default: return edge_pass_q<F, 2>(filter, block, e, P, n, ctrl, skip, s);
+    case 2: return edge_pass_q<F, 1>(filter, block, e, P, n, ctrl, skip, Z, zsel, s);
+    case 8: return edge_pass_q<F, 4>(filter, block, e, P, n, ctrl, skip, Z, zsel, s);
+    default: return edge_pass_q<F, 2>(filter, block, e, P, n, ctrl, skip, Z, zsel, s);
   }
 }
 }  // namespace
 
 cudaError_t launch_edge_pass(bool rf, int filter, int ept, int block, const EdgeSpan &e, uint32_t *P,
-                             uint32_t n, Ctrl *ctrl, const uint32_t *skip, cudaStream_t s) {
+                             uint32_t n, Ctrl *ctrl, const uint32_t *skip, cudaStream_t s, uint32_t *Z,
+                             const uint32_t *zsel) {
   if (block != 128 && block != 256 && block != 512) block = 256;
   if (e.n_quads == 0 && !e.head && !e.tail) return cudaSuccess;
-  return rf ? edge_pass_f<RootR>(filter, ept, block, e, P, n, ctrl, skip, s)
-            : edge_pass_f<RootId>(filter, ept, block, e, P, n, ctrl, skip, s);
+  return rf ? edge_pass_f<RootR>(filter, ept, block, e, P, n, ctrl, skip, Z, zsel, s)
+            : edge_pass_f<RootId>(filter, ept, block, e, P, n, ctrl, skip, Z, zsel, s);
 }
 
 cudaError_t launch_validate(const EdgeSpan &e, uint32_t n, Ctrl *ctrl, cudaStream_t s) {

@@ -46,7 +46,7 @@ def rmat16():
 
 
 @pytest.mark.parametrize("mode", [cc.CC_ROOT_MAXDEG, cc.CC_ROOT_IDENTITY])
-@pytest.mark.parametrize("flt", [cc.CC_FILTER_ON, cc.CC_FILTER_OFF])
+@pytest.mark.parametrize("flt", [cc.CC_FILTER_ON, cc.CC_FILTER_OFF, cc.CC_FILTER_BITMAP])
 @pytest.mark.parametrize("ept", [2, 4, 8])
 @pytest.mark.parametrize("block", [128, 256, 512])
 def test_rmat16_every_variant(rmat16, mode, flt, ept, block):
@@ -177,11 +177,12 @@ def test_connected_queries(rmat16):
 
 
 @pytest.mark.parametrize("mode", [cc.CC_ROOT_MAXDEG, cc.CC_ROOT_IDENTITY])
-def test_incremental_inserts_equal_union(mode):
+@pytest.mark.parametrize("flt", [cc.CC_FILTER_AUTO, cc.CC_FILTER_BITMAP])
+def test_incremental_inserts_equal_union(mode, flt):
     n = 1 << 16
     base = graphgen.rmat(16, 1 << 17, 21, scramble=True)
     batches = [graphgen.pairs(n, k, 30 + i) for i, k in enumerate([1, 1000, 7, 40000, 3, 12345])]
-    with cc.Graph(n, mode=mode) as g:
+    with cc.Graph(n, mode=mode, filter=flt) as g:
         L = torch.empty(n, dtype=torch.int32, device="cuda")
         g.run(dev_edges(base), L)
         seen = [base]
@@ -194,7 +195,7 @@ def test_incremental_inserts_equal_union(mode):
             np.testing.assert_array_equal(L.cpu().numpy().view(np.uint32), want)
             assert g.num_components() == oracle.num_components(want)
     # inserts on a fresh handle, without any cc_run
-    with cc.Graph(n, mode=mode) as g:
+    with cc.Graph(n, mode=mode, filter=flt) as g:
         L = torch.empty(n, dtype=torch.int32, device="cuda")
         for b in batches:
             g.insert(dev_edges(b))
@@ -309,7 +310,8 @@ def _chunked_case(kind):
 
 
 @pytest.mark.parametrize("kind", ["rmat", "er", "late_hub", "two_hubs"])
-def test_run_host_chunked_selection(kind):
+@pytest.mark.parametrize("flt", [cc.CC_FILTER_AUTO, cc.CC_FILTER_BITMAP])
+def test_run_host_chunked_selection(kind, flt):
     n, e = _chunked_case(kind)
     E = len(e)
     m = oracle.max_degree_vertex(n, e)
@@ -319,15 +321,74 @@ def test_run_host_chunked_selection(kind):
         assert m == 4242
     host = torch.from_numpy(e.view(np.int32)).pin_memory()
     L = torch.empty(n, dtype=torch.int32).pin_memory()
-    with cc.Graph(n, E) as g:
+    want = oracle.min_labels(n, e)
+    with cc.Graph(n, E, filter=flt) as g:
         for _ in range(2):  # the second run reuses every buffer
             cc.cc_run_host(g.h, host, None, L)
-            np.testing.assert_array_equal(L.numpy().view(np.uint32), oracle.min_labels(n, e))
+            np.testing.assert_array_equal(L.numpy().view(np.uint32), want)
             assert g.root_vertex() == m
-    with cc.Graph(n, E, label_space=cc.CC_LABEL_ROOT_VALUE) as g:
+        # inserts after a host run keep the bitmap consistent
+        extra = graphgen.pairs(n, 5000, 65)
+        g.insert(dev_edges(extra))
+        Ld = torch.empty(n, dtype=torch.int32, device="cuda")
+        g.labels(Ld)
+        g.sync()
+        np.testing.assert_array_equal(Ld.cpu().numpy().view(np.uint32),
+                                      oracle.min_labels(n, np.concatenate([e, extra])))
+    with cc.Graph(n, E, filter=flt, label_space=cc.CC_LABEL_ROOT_VALUE) as g:
         cc.cc_run_host(g.h, host, None, L)
         assert g.root_vertex() == m
         np.testing.assert_array_equal(L.numpy().view(np.uint32), oracle.root_value_labels(n, e, m))
+
+
+@pytest.fixture(scope="module")
+def rmat25():
+    """R-MAT scale 25 with edge factor 4 (P of 128 MiB), two insert batches and
+    a G(n, m) on the same vertex count, with their oracle labels."""
+    n = 1 << 25
+    e = graphgen.rmat(25, 1 << 27, 66, scramble=True)
+    extra = graphgen.pairs(n, 1 << 22, 67)
+    more = graphgen.pairs(n, 1 << 20, 68)
+    er = graphgen.er(n, 1 << 26, 69)
+    return dict(n=n, e=e, extra=extra, more=more, er=er, m=oracle.max_degree_vertex(n, e),
+                want=oracle.min_labels(n, e), want2=oracle.min_labels(n, np.concatenate([e, extra])),
+                want3=oracle.min_labels(n, np.concatenate([e, extra, more])), want_er=oracle.min_labels(n, er))
+
+
+@pytest.mark.parametrize("flt", [cc.CC_FILTER_AUTO, cc.CC_FILTER_BITMAP, cc.CC_FILTER_ON])
+def test_zero_tree_bitmap_large(rmat25, flt):
+    """CC_FILTER_AUTO allocates the zero-tree bitmap for this size and the
+    certified hub selects it on the device; the G(n, m) gets the bitmap too
+    but no certificate, so the plain instance runs. Everything equals the
+    oracle, also after inserts and a restore."""
+    r = rmat25
+    n = r["n"]
+    with cc.Graph(n, filter=flt) as g:
+        L = torch.empty(n, dtype=torch.int32, device="cuda")
+        d = dev_edges(r["e"])
+        for _ in range(2):
+            g.run(d, L)
+            g.sync()
+            np.testing.assert_array_equal(L.cpu().numpy().view(np.uint32), r["want"])
+        assert g.root_vertex() == r["m"]
+        if flt != cc.CC_FILTER_ON:
+            assert cc.cc_device_bytes(g.h) >= 4 * n + n // 8
+        g.insert(dev_edges(r["extra"]))
+        g.labels(L)
+        g.sync()
+        np.testing.assert_array_equal(L.cpu().numpy().view(np.uint32), r["want2"])
+        buf = cc.cc_checkpoint(g.h)
+        g.run(d, L)
+        cc.cc_restore(g.h, buf)
+        g.insert(dev_edges(r["more"]))
+        g.labels(L)
+        g.sync()
+        np.testing.assert_array_equal(L.cpu().numpy().view(np.uint32), r["want3"])
+    with cc.Graph(n, filter=flt) as g:
+        L = torch.empty(n, dtype=torch.int32, device="cuda")
+        g.run(dev_edges(r["er"]), L)
+        g.sync()
+        np.testing.assert_array_equal(L.cpu().numpy().view(np.uint32), r["want_er"])
 
 
 def test_phase_times_and_budget():
