@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(512) k_edge_pass_filtered(const uint4 *__restr
 
 __global__ void __launch_bounds__(256) k_validate(const uint4 *__restrict__ e4, uint64_t n_quads,
                                                   const uint2 *head, const uint2 *tail, uint32_t n,
-                                                  Ctrl *ctrl) {
+                                                  Ctrl *ctrl, uint32_t *reject) {
   const uint64_t pol = policy_evict_first();
   const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(256) k_validate(const uint4 *__restrict__ e4, 
     bad |= (e.x >= n) | (e.y >= n) | (e.z >= n) | (e.w >= n);
   }
   if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) {
-    atomicOr(&ctrl->reject, 1u);
+    atomicOr(reject, 1u);
     set_err(ctrl, kErrRange);
   }
 }
@@ -490,10 +490,11 @@ cudaError_t launch_edge_pass(bool rf, int filter, int ept, int block, const Edge
             : edge_pass_f<RootId>(filter, ept, block, e, P, n, ctrl, skip, Z, zsel, s);
 }
 
-cudaError_t launch_validate(const EdgeSpan &e, uint32_t n, Ctrl *ctrl, cudaStream_t s) {
+cudaError_t launch_validate(const EdgeSpan &e, uint32_t n, Ctrl *ctrl, cudaStream_t s, uint32_t *reject) {
   if (e.n_quads == 0 && !e.head && !e.tail) return cudaSuccess;
   const unsigned g = clamp_grid((e.n_quads + 255) / 256, persistent_cap((const void *)k_validate, 256, 0));
-  k_validate<<<g, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, n, ctrl); note_launch();
+  k_validate<<<g, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, n, ctrl, reject ? reject : &ctrl->reject);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -49,6 +49,13 @@ constexpr size_t kMaxSideRunning = 16;
 // makes the host drain the executor once, so that kernels that cannot fit
 // beside it get the SMs.
 constexpr uint64_t kSideStarveNs = 20ULL * 1000 * 1000;
+// Inserts of at least this many edges run on a side stream as one validated,
+// full-occupancy edge pass beside the executor instead of as executor tiles.
+constexpr uint64_t kSideInsertMin = 1ULL << 18;
+// Side streams; a graph's side work always goes to the same one, in order.
+constexpr uint32_t kSideStreams = 4;
+// Graphs whose parent array reaches this size keep a zero-tree bitmap.
+constexpr uint64_t kZMinBytes = 128ULL << 20;
 
 struct alignas(16) WorkItem {
   uint32_t kind, slot, seq, n_tiles;  // n_tiles: tiles that count towards completion
@@ -382,6 +389,7 @@ struct Req {
   uint32_t slot = UINT32_MAX, seq = 0, n_tiles = 0;
   cudaEvent_t ev = nullptr;
   uint64_t t_side = 0;  // side-stream work issued (or the executor last drained for it) at
+  int flag = -1;        // side insert: index of its pinned rejection word
 };
 
 struct GraphState {
@@ -392,6 +400,8 @@ struct GraphState {
   void *cnt = nullptr;
   cc::CertScratch *cert = nullptr;
   cc::Ctrl *ctrl = nullptr;
+  uint32_t *Z = nullptr;  // zero-tree bitmap (large graphs under R), or null
+  uint64_t z_bytes = 0;
   uint32_t m = 0;
   std::deque<Req *> fifo;
   int group = kIdle;
@@ -408,8 +418,13 @@ struct cc_server {
   HostShared *hs_dev = nullptr;
   DevShared *ds = nullptr;
   cudaStream_t exec_stream = nullptr, side_stream = nullptr;
+  cudaStream_t side_streams[cc::srv::kSideStreams] = {};  // [0] is side_stream
   cudaEvent_t exec_ev = nullptr;
   uint32_t *side_words = nullptr;  // pinned: per-graph m and error word read back after admission
+  uint32_t *side_flags = nullptr;  // pinned: one rejection word per running side insert
+  uint32_t *side_reject = nullptr; // device: the same words, written by validation
+  std::vector<int> free_flags;
+  uint32_t next_side = 0;          // round-robin stream of side inserts
   // submission side (sub_mu): request objects, the inbox, graph ids
   std::mutex sub_mu;
   std::condition_variable sub_cv;
@@ -438,10 +453,18 @@ struct cc_server {
 
 namespace {
 
+bool wants_z(uint64_t n, bool rf) { return rf && n * 4 >= cc::srv::kZMinBytes; }
+uint64_t z_bytes_for(uint64_t n) { return (n + 1 + 31) / 32 * 4; }
+
 uint64_t graph_bytes(uint64_t n, uint64_t n_edges, bool rf) {
   size_t b = align256((size_t)((n + 3) / 4 * 4) * 4) + align256(sizeof(cc::Ctrl));
   if (rf) b += align256((size_t)n * (n_edges >= (1ULL << 31) ? 8 : 4)) + align256(sizeof(cc::CertScratch));
+  if (wants_z(n, rf)) b += align256(z_bytes_for(n));
   return b;
+}
+
+cudaStream_t side_stream_of(const cc_server *s, uint32_t gid) {
+  return s->side_streams[gid % cc::srv::kSideStreams];
 }
 
 void complete(cc_server *s, Req *r, cc_status st) {
@@ -561,10 +584,18 @@ bool start_new_graph(cc_server *s, Req *r, GraphState &g) {
     g.cnt = p;
     p += align256((size_t)g.n * (wide ? 8 : 4));
     g.cert = reinterpret_cast<cc::CertScratch *>(p);
+    p += align256(sizeof(cc::CertScratch));
+  }
+  g.Z = nullptr;
+  g.z_bytes = 0;
+  if (wants_z(g.n, rf)) {
+    g.Z = reinterpret_cast<uint32_t *>(p);
+    g.z_bytes = z_bytes_for(g.n);
   }
   r->state.store(kRunning);
-  cudaStream_t ss = s->side_stream;
+  cudaStream_t ss = side_stream_of(s, r->graph);
   cudaError_t e = cudaMemsetAsync(g.ctrl, 0, sizeof(cc::Ctrl), ss);
+  if (e == cudaSuccess && g.Z) e = cudaMemsetAsync(g.Z, 0, g.z_bytes, ss);
   const uint32_t n = (uint32_t)g.n;
   const cc::EdgeSpan span = cc::split_edges(r->r.edges_dev, r->r.n_edges);
   int m_src = cc::kMFromHint;
@@ -573,7 +604,8 @@ bool start_new_graph(cc_server *s, Req *r, GraphState &g) {
     m_src = cc::kMFromPackedMax;
   }
   if (e == cudaSuccess && n) e = cc::launch_init(rf, g.P, n, g.ctrl, m_src, 0u, ss);
-  if (e == cudaSuccess && n) e = cc::launch_edge_pass(rf, 1, 4, 256, span, g.P, n, g.ctrl, nullptr, ss);
+  if (e == cudaSuccess && n)
+    e = cc::launch_edge_pass(rf, 1, 4, 256, span, g.P, n, g.ctrl, nullptr, ss, g.Z, g.Z ? &g.ctrl->cert : nullptr);
   if (e == cudaSuccess && n) e = cc::launch_flatten(rf, s->cfg.label_space, g.P, n, r->r.labels_dev, g.ctrl, ss);
   const uint32_t gid = r->graph;
   if (e == cudaSuccess)
@@ -594,7 +626,7 @@ bool start_new_graph(cc_server *s, Req *r, GraphState &g) {
 bool start_snapshot(cc_server *s, Req *r, GraphState &g) {
   if (s->side_running.size() >= cc::srv::kMaxSideRunning) return false;
   r->state.store(kRunning);
-  cudaStream_t ss = s->side_stream;
+  cudaStream_t ss = side_stream_of(s, r->graph);
   cudaError_t e = cudaSuccess;
   if (g.n) {
     cc::srv::k_srv_prep_flatten<<<1, 1, 0, ss>>>(g.ctrl);
@@ -605,6 +637,40 @@ bool start_snapshot(cc_server *s, Req *r, GraphState &g) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(r->ev, ss);
   if (e != cudaSuccess) {
+    complete(s, r, CC_ERR_CUDA);
+    return true;
+  }
+  r->t_side = host_ns();
+  s->side_running.push_back(r);
+  return true;
+}
+
+// A large insert as one validated, full-occupancy edge pass on a side
+// stream: validation sets the request's own rejection word, the edge pass
+// skips itself when it is set, and the word is copied to the request's pinned
+// flag. Inserts commute, so large inserts of one graph may run on different
+// streams at once, and executor tiles of the same graph meanwhile.
+bool start_side_insert(cc_server *s, Req *r, GraphState &g) {
+  if (s->side_running.size() >= cc::srv::kMaxSideRunning || s->free_flags.empty()) return false;
+  r->flag = s->free_flags.back();
+  s->free_flags.pop_back();
+  s->side_flags[r->flag] = 0u;
+  r->state.store(kRunning);
+  cudaStream_t ss = s->side_streams[s->next_side++ % cc::srv::kSideStreams];
+  const uint32_t n = (uint32_t)g.n;
+  const cc::EdgeSpan span = cc::split_edges(r->r.edges_dev, r->r.n_edges);
+  uint32_t *rej = s->side_reject + r->flag;
+  cudaError_t e = cudaMemsetAsync(rej, 0, sizeof(uint32_t), ss);
+  if (e == cudaSuccess) e = cc::launch_validate(span, n, g.ctrl, ss, rej);
+  if (e == cudaSuccess)
+    e = cc::launch_edge_pass(g.rf, 1, 4, 256, span, g.P, n, g.ctrl, rej, ss, g.Z, g.Z ? &g.ctrl->cert : nullptr);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&s->side_flags[r->flag], rej, sizeof(uint32_t), cudaMemcpyDeviceToHost, ss);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(r->ev, ss);
+  if (e != cudaSuccess) {
+    s->free_flags.push_back(r->flag);
+    r->flag = -1;
     complete(s, r, CC_ERR_CUDA);
     return true;
   }
@@ -661,7 +727,13 @@ void try_start(cc_server *s, uint32_t gid) {
       continue;
     }
     if (g.active && g.group != cls) return;
-    const bool started = r->r.kind == CC_REQ_SNAPSHOT ? start_snapshot(s, r, g) : start_exec(s, r, g);
+    bool started;
+    if (r->r.kind == CC_REQ_SNAPSHOT)
+      started = start_snapshot(s, r, g);
+    else if (r->r.kind == CC_REQ_INSERT && r->r.n_edges >= cc::srv::kSideInsertMin && g.n)
+      started = start_side_insert(s, r, g);
+    else
+      started = start_exec(s, r, g);
     if (!started) return;
     g.fifo.pop_front();
     if (r->state.load() == kRunning) {
@@ -733,7 +805,9 @@ void manage_executor(cc_server *s) {
     }
   } else if (s->exec_running && !s->exec_stopping) {
     if (!s->idle_since) s->idle_since = now;
-    if (now - s->idle_since > (uint64_t)s->cfg.idle_timeout_us * 1000ULL) {
+    // idle: leave after the idle timeout, or at once while side-stream work
+    // runs, so that it gets every SM (the executor is relaunched on demand)
+    if (!s->side_running.empty() || now - s->idle_since > (uint64_t)s->cfg.idle_timeout_us * 1000ULL) {
       *(volatile unsigned int *)&s->hs->stop = 1u;
       s->exec_stopping = true;
       s->idle_since = 0;
@@ -781,6 +855,11 @@ bool scheduler_step(cc_server *s, std::vector<Req *> &incoming) {
     if (r->r.kind == CC_REQ_NEW_GRAPH && st == CC_OK) {
       g.m = s->side_words[2 * r->graph];
       if (s->side_words[2 * r->graph + 1]) st = CC_ERR_OUT_OF_RANGE;
+    }
+    if (r->flag >= 0) {
+      if (st == CC_OK && *(volatile uint32_t *)&s->side_flags[r->flag]) st = CC_ERR_OUT_OF_RANGE;
+      s->free_flags.push_back(r->flag);
+      r->flag = -1;
     }
     complete(s, r, st);
     finish_graph_request(g);
@@ -837,7 +916,21 @@ void scheduler_main(cc_server *s) {
   // stop the executor (bounded: its blocks leave at the next look at `stop`)
   *(volatile unsigned int *)&s->hs->stop = 1u;
   cudaStreamSynchronize(s->exec_stream);
-  cudaStreamSynchronize(s->side_stream);
+  for (cudaStream_t st : s->side_streams) cudaStreamSynchronize(st);
+}
+
+// Frees what cc_server_create allocated (any subset of it).
+void release_resources(cc_server *s) {
+  if (s->arena_base) cudaFree(s->arena_base);
+  if (s->hs) cudaFreeHost(s->hs);
+  if (s->ds) cudaFree(s->ds);
+  if (s->side_words) cudaFreeHost(s->side_words);
+  if (s->side_flags) cudaFreeHost(s->side_flags);
+  if (s->side_reject) cudaFree(s->side_reject);
+  if (s->exec_stream) cudaStreamDestroy(s->exec_stream);
+  for (cudaStream_t st : s->side_streams)
+    if (st) cudaStreamDestroy(st);
+  if (s->exec_ev) cudaEventDestroy(s->exec_ev);
 }
 
 // Runs every kernel the server can launch once, on a tiny graph, before the
@@ -848,12 +941,13 @@ cudaError_t warm_up(cc_server *s) {
   const bool rf = s->cfg.mode == CC_ROOT_MAXDEG;
   const uint32_t n = 16;
   const uint32_t edges_h[8] = {0, 1, 2, 3, 3, 1, 5, 5};
-  uint32_t *P = nullptr, *edges = nullptr, *labels = nullptr;
+  uint32_t *P = nullptr, *edges = nullptr, *labels = nullptr, *Z = nullptr;
   void *cnt = nullptr;
   cc::CertScratch *cert = nullptr;
   cc::Ctrl *ctrl = nullptr;
   cudaStream_t ss = s->side_stream;
   cudaError_t e = cudaMalloc((void **)&P, 64 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&Z, 64 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc((void **)&edges, sizeof(edges_h));
   if (e == cudaSuccess) e = cudaMalloc((void **)&labels, 64 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&cnt, 64 * sizeof(unsigned long long));
@@ -870,6 +964,11 @@ cudaError_t warm_up(cc_server *s) {
     }
     if (e == cudaSuccess) e = cc::launch_init(rf, P, n, ctrl, m_src, 0u, ss);
     if (e == cudaSuccess) e = cc::launch_edge_pass(rf, 1, 4, 256, span, P, n, ctrl, nullptr, ss);
+    // a side insert: validation, then both edge-pass instances (plain and
+    // zero-tree, one chosen on the device)
+    if (e == cudaSuccess) e = cudaMemsetAsync(Z, 0, 64 * sizeof(uint32_t), ss);
+    if (e == cudaSuccess) e = cc::launch_validate(span, n, ctrl, ss);
+    if (e == cudaSuccess) e = cc::launch_edge_pass(rf, 1, 4, 256, span, P, n, ctrl, &ctrl->reject, ss, Z, &ctrl->cert);
     if (e == cudaSuccess) e = cc::launch_flatten(rf, s->cfg.label_space, P, n, labels, ctrl, ss);
     if (e == cudaSuccess) e = cc::launch_flatten(rf, s->cfg.label_space, P, n, nullptr, ctrl, ss);
     if (e == cudaSuccess) {
@@ -895,6 +994,7 @@ cudaError_t warm_up(cc_server *s) {
     if (e == cudaSuccess) e = cudaMemset(&s->ds->taken, 0, sizeof(unsigned long long));
   }
   cudaFree(P);
+  cudaFree(Z);
   cudaFree(edges);
   cudaFree(labels);
   cudaFree(cnt);
@@ -949,33 +1049,27 @@ cc_status cc_server_create(const cc_server_config *cfg_in, cc_server **out) {
   if (e == cudaSuccess) e = cudaMemset(s->ds, 0, sizeof(DevShared));
   if (e == cudaSuccess)
     e = cudaHostAlloc((void **)&s->side_words, 2 * (size_t)cfg.max_graphs * sizeof(uint32_t), cudaHostAllocDefault);
+  if (e == cudaSuccess)
+    e = cudaHostAlloc((void **)&s->side_flags, cc::srv::kMaxSideRunning * sizeof(uint32_t), cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&s->side_reject, cc::srv::kMaxSideRunning * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->exec_stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->side_stream, cudaStreamNonBlocking);
+  for (cudaStream_t &st : s->side_streams)
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  s->side_stream = s->side_streams[0];
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->exec_ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cc_status st = e == cudaErrorMemoryAllocation ? CC_ERR_OOM : CC_ERR_CUDA;
-    if (s->arena_base) cudaFree(s->arena_base);
-    if (s->hs) cudaFreeHost(s->hs);
-    if (s->ds) cudaFree(s->ds);
-    if (s->side_words) cudaFreeHost(s->side_words);
-    if (s->exec_stream) cudaStreamDestroy(s->exec_stream);
-    if (s->side_stream) cudaStreamDestroy(s->side_stream);
-    if (s->exec_ev) cudaEventDestroy(s->exec_ev);
+    release_resources(s);
     delete s;
     return st;
   }
   memset(s->hs, 0, sizeof(HostShared));
   if ((e = warm_up(s)) != cudaSuccess) {
-    cudaFree(s->arena_base);
-    cudaFreeHost(s->hs);
-    cudaFree(s->ds);
-    cudaFreeHost(s->side_words);
-    cudaStreamDestroy(s->exec_stream);
-    cudaStreamDestroy(s->side_stream);
-    cudaEventDestroy(s->exec_ev);
+    release_resources(s);
     delete s;
     return CC_ERR_CUDA;
   }
+  for (int i = (int)cc::srv::kMaxSideRunning; i-- > 0;) s->free_flags.push_back(i);
   s->arena.reset(cfg.hbm_budget_bytes);
   s->graphs.resize(cfg.max_graphs);
   s->id_state.assign(cfg.max_graphs, 0);
@@ -1107,13 +1201,7 @@ void cc_server_destroy(cc_server *s) {
   if (s->thread.joinable()) s->thread.join();
   for (auto &r : s->reqs)
     if (r->ev) cudaEventDestroy(r->ev);
-  cudaFree(s->arena_base);
-  cudaFreeHost(s->hs);
-  cudaFree(s->ds);
-  cudaFreeHost(s->side_words);
-  cudaStreamDestroy(s->exec_stream);
-  cudaStreamDestroy(s->side_stream);
-  cudaEventDestroy(s->exec_ev);
+  release_resources(s);
   delete s;
 }
 

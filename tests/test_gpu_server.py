@@ -40,7 +40,7 @@ def make_script(seed):
         n = graphs[k]
         kind = rng.choice(["insert", "query", "snapshot"], p=[0.45, 0.45, 0.10])
         if kind == "insert":
-            size = int(10 ** rng.uniform(0, 5.3))  # 1 .. 200K edges (1 to 13 tiles)
+            size = int(10 ** rng.uniform(0, 5.9))  # 1 .. 800K edges: executor tiles, or a side insert from 2^18
             script.append((k, "insert", graphgen.pairs(n, size, 7, tag=i)))
         elif kind == "query":
             script.append((k, "query", graphgen.pairs(n, 3000, 8, tag=i)))
@@ -131,7 +131,7 @@ def test_insert_with_bad_id_is_rejected_whole():
         assert s.wait(t) == cc.CC_OK
         L0 = torch.empty(n, dtype=torch.int32, device="cuda")
         assert s.wait(s.snapshot(g, L0)) == cc.CC_OK
-        for size in (100, 500, 20000):  # one tile, and many tiles (validated first)
+        for size in (100, 500, 20000, 300000):  # one tile, many tiles (validated first), a side insert
             bad = graphgen.pairs(n, size, 4, tag=size)
             bad[size // 2, 0] = n + 5
             assert s.wait(s.insert(g, dev(bad))) == cc.CC_ERR_OUT_OF_RANGE
@@ -240,3 +240,31 @@ def test_side_work_is_not_starved_by_a_full_executor():
         want = oracle.connected(oracle.min_labels(n, a), q)
         np.testing.assert_array_equal(out.cpu().numpy(), want)
         np.testing.assert_array_equal(out2.cpu().numpy(), want)
+
+
+def test_large_graph_side_inserts_and_zero_tree():
+    """A resident graph whose parent array exceeds 128 MiB keeps a zero-tree
+    bitmap; large inserts run as side-stream edge passes (with the bitmap)
+    while small inserts and queries run in the executor."""
+    n = 1 << 25
+    base = graphgen.rmat(25, 1 << 26, 31, scramble=True)
+    ins = [graphgen.pairs(n, k, 32, tag=i) for i, k in enumerate([1 << 21, 1000, 1 << 19, 50, 1 << 20])]
+    q = graphgen.pairs(n, 100000, 33)
+    with cc.Server(4 * GB) as s:
+        t, g = s.new_graph(n, dev(base))
+        tickets = [t]
+        for b in ins:
+            tickets.append(s.insert(g, dev(b)))
+        out = torch.full((len(q),), 7, dtype=torch.uint8, device="cuda")
+        qd = dev(q)
+        L = torch.empty(n, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        tq = s.query(g, qd, out)
+        ts = s.snapshot(g, L)
+        for tk in tickets + [tq, ts]:
+            assert s.wait(tk, 120) == cc.CC_OK
+        want = oracle.min_labels(n, np.concatenate([base] + ins))
+        np.testing.assert_array_equal(L.cpu().numpy().view(np.uint32), want)
+        np.testing.assert_array_equal(out.cpu().numpy(), oracle.connected(want, q))
+        assert s.stats()["failed"] == 0
+
