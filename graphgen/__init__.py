@@ -321,5 +321,8 @@ GRID8K = grid_workload("grid8192x8192_p0.9", 8192, 8192, 3)
 RMAT28 = rmat_workload("rmat28_ef16", 28, 16, 4, scramble=True)
 BATCH_GRAPHS, BATCH_SEED = 4096, 5
 RMAT26 = rmat_workload("rmat26_ef16", 26, 16, 6, scramble=True)
+# A profiling case for the zero-tree edge pass: the parent array (268 MB) is
+# larger than L2 while the edges (2.1 GB) stay a few GB.
+RMAT26_EF4 = rmat_workload("rmat26_ef4", 26, 4, 7, scramble=True)
 
-WORKLOADS = {w.name: w for w in (RMAT16, RMAT24, GRID8K, RMAT28, RMAT26)}
+WORKLOADS = {w.name: w for w in (RMAT16, RMAT24, GRID8K, RMAT28, RMAT26, RMAT26_EF4)}

@@ -444,26 +444,29 @@ cudaError_t launch_init(bool rf, uint32_t *P, uint32_t n, Ctrl *ctrl, int m_src,
 namespace {
 template <class F, int Q>
 cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, uint32_t n, Ctrl *ctrl,
-                        const uint32_t *skip, uint32_t *Z, const uint32_t *zsel, cudaStream_t s) {
+                        const uint32_t *skip, uint32_t *Z, const uint32_t *zsel, bool one_shot, cudaStream_t s) {
   const uint64_t per_block = (uint64_t)block * Q;
+  // one-shot grids (one iteration per block) let blocks retire continuously,
+  // so that kernels of other streams get SMs while this one runs
+  const uint64_t cap_big = 0x7FFFFFFFull;
   if (filter) {
     const size_t smem = (size_t)(block / 32) * 4 * kRing * sizeof(uint32_t);
     static_assert((1024 / 32) * 4 * kRing * sizeof(uint32_t) <= 48 * 1024,
                   "the ring of a 1024-thread block fits the default dynamic shared memory limit");
     const uint64_t want = (e.n_quads + per_block - 1) / per_block;
     if (Z) {  // the zero-tree instance (alone, or chosen on the device by *zsel)
-      const unsigned g = clamp_grid(want, persistent_cap((const void *)k_edge_pass_filtered<F, Q, true>, block, smem));
+      const unsigned g = clamp_grid(want, one_shot ? cap_big : persistent_cap((const void *)k_edge_pass_filtered<F, Q, true>, block, smem));
       k_edge_pass_filtered<F, Q, true><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
                                                               skip, Z, zsel); note_launch();
     }
     if (!Z || zsel) {
-      const unsigned g = clamp_grid(want, persistent_cap((const void *)k_edge_pass_filtered<F, Q, false>, block, smem));
+      const unsigned g = clamp_grid(want, one_shot ? cap_big : persistent_cap((const void *)k_edge_pass_filtered<F, Q, false>, block, smem));
       k_edge_pass_filtered<F, Q, false><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
                                                                skip, nullptr, Z ? zsel : nullptr); note_launch();
     }
   } else {
     const void *k = (const void *)k_edge_pass_direct<F, Q>;
-    const unsigned g = clamp_grid((e.n_quads + per_block - 1) / per_block, persistent_cap(k, block, 0));
+    const unsigned g = clamp_grid((e.n_quads + per_block - 1) / per_block, one_shot ? cap_big : persistent_cap(k, block, 0));
     k_edge_pass_direct<F, Q><<<g, block, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
                                                  skip); note_launch();
   }
@@ -472,22 +475,23 @@ cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, u
 
 template <class F>
 cudaError_t edge_pass_f(int filter, int ept, int block, const EdgeSpan &e, uint32_t *P, uint32_t n,
-                        Ctrl *ctrl, const uint32_t *skip, uint32_t *Z, const uint32_t *zsel, cudaStream_t s) {
+                        Ctrl *ctrl, const uint32_t *skip, uint32_t *Z, const uint32_t *zsel, bool one_shot,
+                        cudaStream_t s) {
   switch (ept) {
-    case 2: return edge_pass_q<F, 1>(filter, block, e, P, n, ctrl, skip, Z, zsel, s);
-    case 8: return edge_pass_q<F, 4>(filter, block, e, P, n, ctrl, skip, Z, zsel, s);
-    default: return edge_pass_q<F, 2>(filter, block, e, P, n, ctrl, skip, Z, zsel, s);
+    case 2: return edge_pass_q<F, 1>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, s);
+    case 8: return edge_pass_q<F, 4>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, s);
+    default: return edge_pass_q<F, 2>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, s);
   }
 }
 }  // namespace
 
 cudaError_t launch_edge_pass(bool rf, int filter, int ept, int block, const EdgeSpan &e, uint32_t *P,
                              uint32_t n, Ctrl *ctrl, const uint32_t *skip, cudaStream_t s, uint32_t *Z,
-                             const uint32_t *zsel) {
+                             const uint32_t *zsel, bool one_shot) {
   if (block != 128 && block != 256 && block != 512) block = 256;
   if (e.n_quads == 0 && !e.head && !e.tail) return cudaSuccess;
-  return rf ? edge_pass_f<RootR>(filter, ept, block, e, P, n, ctrl, skip, Z, zsel, s)
-            : edge_pass_f<RootId>(filter, ept, block, e, P, n, ctrl, skip, Z, zsel, s);
+  return rf ? edge_pass_f<RootR>(filter, ept, block, e, P, n, ctrl, skip, Z, zsel, one_shot, s)
+            : edge_pass_f<RootId>(filter, ept, block, e, P, n, ctrl, skip, Z, zsel, one_shot, s);
 }
 
 cudaError_t launch_validate(const EdgeSpan &e, uint32_t n, Ctrl *ctrl, cudaStream_t s, uint32_t *reject) {

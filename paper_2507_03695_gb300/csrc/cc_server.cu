@@ -605,7 +605,8 @@ bool start_new_graph(cc_server *s, Req *r, GraphState &g) {
   }
   if (e == cudaSuccess && n) e = cc::launch_init(rf, g.P, n, g.ctrl, m_src, 0u, ss);
   if (e == cudaSuccess && n)
-    e = cc::launch_edge_pass(rf, 1, 4, 256, span, g.P, n, g.ctrl, nullptr, ss, g.Z, g.Z ? &g.ctrl->cert : nullptr);
+    e = cc::launch_edge_pass(rf, 1, 4, 256, span, g.P, n, g.ctrl, nullptr, ss, g.Z, g.Z ? &g.ctrl->cert : nullptr,
+                             true);
   if (e == cudaSuccess && n) e = cc::launch_flatten(rf, s->cfg.label_space, g.P, n, r->r.labels_dev, g.ctrl, ss);
   const uint32_t gid = r->graph;
   if (e == cudaSuccess)
@@ -663,7 +664,8 @@ bool start_side_insert(cc_server *s, Req *r, GraphState &g) {
   cudaError_t e = cudaMemsetAsync(rej, 0, sizeof(uint32_t), ss);
   if (e == cudaSuccess) e = cc::launch_validate(span, n, g.ctrl, ss, rej);
   if (e == cudaSuccess)
-    e = cc::launch_edge_pass(g.rf, 1, 4, 256, span, g.P, n, g.ctrl, rej, ss, g.Z, g.Z ? &g.ctrl->cert : nullptr);
+    e = cc::launch_edge_pass(g.rf, 1, 4, 256, span, g.P, n, g.ctrl, rej, ss, g.Z, g.Z ? &g.ctrl->cert : nullptr,
+                             true);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&s->side_flags[r->flag], rej, sizeof(uint32_t), cudaMemcpyDeviceToHost, ss);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
@@ -1052,9 +1054,13 @@ cc_status cc_server_create(const cc_server_config *cfg_in, cc_server **out) {
   if (e == cudaSuccess)
     e = cudaHostAlloc((void **)&s->side_flags, cc::srv::kMaxSideRunning * sizeof(uint32_t), cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaMalloc((void **)&s->side_reject, cc::srv::kMaxSideRunning * sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->exec_stream, cudaStreamNonBlocking);
+  // the executor's stream has the highest priority, so that its blocks are
+  // placed ahead of waiting side-stream blocks whenever SMs free up
+  int prio_low = 0, prio_high = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->exec_stream, cudaStreamNonBlocking, prio_high);
   for (cudaStream_t &st : s->side_streams)
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio_low);
   s->side_stream = s->side_streams[0];
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->exec_ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
