@@ -80,14 +80,10 @@ inline cudaError_t ensure_func_attr(const void *kernel, cudaFuncAttribute attr, 
   return e;
 }
 
-// Blocks that fit on the whole GPU at once for this kernel and block size.
-inline uint64_t persistent_cap(const void *kernel, int block, size_t smem) {
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, smem) != cudaSuccess ||
-      occ < 1)
-    occ = 1;
-  return (uint64_t)num_sms() * (uint64_t)occ;
-}
+// Blocks that fit on the whole GPU at once for this kernel and block size
+// (the occupancy query is cached per kernel, block size, shared memory and
+// device: it costs microseconds of host time, and launches are frequent).
+uint64_t persistent_cap(const void *kernel, int block, size_t smem);
 
 // Process-wide count of kernel launches issued by the library.
 void note_launch();
@@ -105,6 +101,7 @@ struct CertScratch {
   unsigned long long owner[kCertBuckets];     // (sampled count << 32) | ~vertex of the owner; 0 = none
   unsigned long long cand_cnt[kCertBuckets];  // exact degree of the owner
   unsigned long long bucket[kCertBuckets];    // endpoint occurrences of the other vertices
+  unsigned int blocks_done;                   // counting blocks finished (the last one decides)
 };
 
 // Chunked exact root selection, for edges that arrive in chunks (host input):

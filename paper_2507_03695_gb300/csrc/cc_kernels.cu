@@ -10,6 +10,8 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <map>
+#include <mutex>
 
 #include "cc_device.cuh"
 #include "cc_internal.h"
@@ -295,6 +297,56 @@ __device__ __forceinline__ uint32_t flatten_one(uint32_t *S, const F fn, uint32_
   return root_name(S, cv, pv);
 }
 
+// 16-byte load of four consecutive parent values.
+__device__ __forceinline__ uint4 ldP4(const uint32_t *p) {
+  uint4 r;
+  asm volatile("ld.global.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p) : "memory");
+  return r;
+}
+
+// Root names of W vertices (names c, parent values pc), walked in lock step:
+// each round issues the next parent load of every walk still running, so the
+// dependent chains overlap instead of following one another. Path splitting
+// as in root_name(); r receives the root names.
+template <int W>
+__device__ __forceinline__ void root_names_lockstep(uint32_t *S, uint32_t (&c)[W], uint32_t (&pc)[W],
+                                                    uint32_t (&r)[W], unsigned long long &roots) {
+  unsigned running = 0;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    if (pc[k] == c[k]) {
+      ++roots;
+      r[k] = pc[k];
+    } else if (pc[k] == 0u) {
+      r[k] = 0u;
+    } else {
+      running |= 1u << k;
+    }
+  }
+  while (running) {
+    uint32_t pw[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k)
+      if (running & (1u << k)) pw[k] = ldP(S + pc[k]);
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      if (!(running & (1u << k))) continue;
+      if (pw[k] == pc[k]) {  // pc[k] is a root
+        r[k] = pc[k];
+        running &= ~(1u << k);
+        continue;
+      }
+      stP(S + c[k], pw[k]);  // the parent is not a root: split past it
+      c[k] = pc[k];
+      pc[k] = pw[k];
+      if (pc[k] == 0u) {  // the permanent root
+        r[k] = 0u;
+        running &= ~(1u << k);
+      }
+    }
+  }
+}
+
 // Four consecutive vertices per thread: 16-byte loads of P, 16-byte stores of
 // the compressed names (only when one changed; every name written is a valid
 // ancestor, and roots are never changed) and of the labels.
@@ -310,24 +362,20 @@ __global__ void __launch_bounds__(256) k_flatten4(uint32_t *P, uint32_t n, uint3
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n4;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t v = (uint32_t)(4 * i);
-    uint4 p;
-    asm volatile("ld.global.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(p.x), "=r"(p.y), "=r"(p.z), "=r"(p.w)
-                 : "l"(P + v)
-                 : "memory");
-    uint4 c;
-    c.x = flatten_one(S, fn, v, p.x, roots);
-    c.y = flatten_one(S, fn, v + 1u, p.y, roots);
-    c.z = flatten_one(S, fn, v + 2u, p.z, roots);
-    c.w = flatten_one(S, fn, v + 3u, p.w, roots);
-    if (c.x != p.x || c.y != p.y || c.z != p.z || c.w != p.w)
-      asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(P + v), "r"(c.x), "r"(c.y), "r"(c.z),
-                   "r"(c.w)
+    const uint4 p = ldP4(P + v);
+    uint32_t c[4] = {fn.f(v), fn.f(v + 1u), fn.f(v + 2u), fn.f(v + 3u)};
+    uint32_t pc[4] = {p.x, p.y, p.z, p.w};
+    uint32_t r[4];
+    root_names_lockstep<4>(S, c, pc, r, roots);
+    const uint4 cq = make_uint4(r[0], r[1], r[2], r[3]);
+    if (cq.x != p.x || cq.y != p.y || cq.z != p.z || cq.w != p.w)
+      asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(P + v), "r"(cq.x), "r"(cq.y), "r"(cq.z),
+                   "r"(cq.w)
                    : "memory");
     if (L)
       __stcs(reinterpret_cast<uint4 *>(L + v),
-             make_uint4(label_of<F, LABEL>(c.x, gmin), label_of<F, LABEL>(c.y, gmin),
-                        label_of<F, LABEL>(c.z, gmin), label_of<F, LABEL>(c.w, gmin)));
+             make_uint4(label_of<F, LABEL>(cq.x, gmin), label_of<F, LABEL>(cq.y, gmin),
+                        label_of<F, LABEL>(cq.z, gmin), label_of<F, LABEL>(cq.w, gmin)));
   }
   // the last n % 4 vertices
   if (blockIdx.x == 0 && threadIdx.x < (n & 3u)) {
@@ -404,6 +452,37 @@ std::atomic<unsigned long long> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+uint64_t persistent_cap(const void *kernel, int block, size_t smem) {
+  struct Key {
+    const void *k;
+    int block, dev;
+    size_t smem;
+    bool operator<(const Key &o) const {
+      if (k != o.k) return k < o.k;
+      if (block != o.block) return block < o.block;
+      if (dev != o.dev) return dev < o.dev;
+      return smem < o.smem;
+    }
+  };
+  static std::mutex mu;
+  static std::map<Key, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const Key key{kernel, block, dev, smem};
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return (uint64_t)num_sms() * (uint64_t)it->second;
+  }
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, smem) != cudaSuccess || occ < 1) occ = 1;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = occ;
+  }
+  return (uint64_t)num_sms() * (uint64_t)occ;
+}
 
 int num_sms() {
   if (g_num_sms == 0) {

@@ -47,26 +47,39 @@ __global__ void __launch_bounds__(256) k_zero_cnt(C *cnt, uint32_t n, const uint
     cnt[v] = (C)0;
 }
 
+// Edge idx lies in a sampled group of k_degree_sampled (1 group of 1024 in
+// stride, counted from the start of the edge array); stride 0: never.
+__device__ __forceinline__ bool in_sample(uint64_t idx, uint32_t stride) {
+  return stride != 0u && ((idx >> 10) % stride) == 0u;
+}
+
+// Degree histogram. With stride nonzero, the edges of the sampled groups are
+// left out: added to the sampled counts, the result is the full histogram.
 template <typename C>
 __global__ void __launch_bounds__(256) k_degree(const uint4 *__restrict__ e4, uint64_t n_quads,
                                                 const uint2 *head, const uint2 *tail,
-                                                C *__restrict__ cnt, uint32_t n, const uint32_t *skip) {
+                                                C *__restrict__ cnt, uint32_t n, const uint32_t *skip,
+                                                uint32_t stride) {
   if (skipped(skip)) return;
   const uint64_t pol = policy_evict_first();
   const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (t == 0 && head) {
+  const uint64_t h = head ? 1u : 0u;  // edge index of the first quad's first edge
+  if (t == 0 && head && !in_sample(0, stride)) {
     uint2 e = ld_edge(head);
     count_edge(cnt, n, e.x, e.y);
   }
-  if (t == 1 % T && tail) {
+  if (t == 1 % T && tail && !in_sample(h + 2 * n_quads, stride)) {
     uint2 e = ld_edge(tail);
     count_edge(cnt, n, e.x, e.y);
   }
   for (uint64_t q = t; q < n_quads; q += T) {
+    const uint64_t i0 = h + 2 * q;
+    const bool s0 = in_sample(i0, stride), s1 = in_sample(i0 + 1, stride);
+    if (s0 && s1) continue;
     const uint4 e = ld_edges(e4 + q, pol);
-    count_edge(cnt, n, e.x, e.y);
-    count_edge(cnt, n, e.z, e.w);
+    if (!s0) count_edge(cnt, n, e.x, e.y);
+    if (!s1) count_edge(cnt, n, e.z, e.w);
   }
 }
 
@@ -201,13 +214,61 @@ __device__ __forceinline__ bool cert_skipped(const Ctrl *ctrl) {
   return nc == 0u || nc > kCertCand;
 }
 
+// The proof, by one block: D = best owner degree (ties to the smaller id);
+// bound = the largest bucket total of non-owners. D > bound means every other
+// vertex has degree < D. Reads through L2: other blocks wrote the totals.
+__device__ void certify_decide_block(const CertScratch *cs, Ctrl *ctrl) {
+  unsigned long long best = 0, bound = 0;
+  bool wide = false;
+  const bool skip = cert_skipped(ctrl);
+  for (uint32_t b = threadIdx.x; b < kCertBuckets && !skip; b += blockDim.x) {
+    const unsigned long long o = __ldcg(&cs->owner[b]);
+    const unsigned long long t = __ldcg(&cs->bucket[b]);
+    bound = t > bound ? t : bound;
+    if (!o) continue;
+    const unsigned long long c = __ldcg(&cs->cand_cnt[b]);
+    if (c >= (1ULL << 32)) {
+      wide = true;
+      continue;
+    }
+    const unsigned long long k = (c << 32) | (uint32_t)o;  // low half: ~vertex
+    best = k > best ? k : best;
+  }
+  const int any_wide = __syncthreads_or(wide);
+  best = block_max_u64(best);
+  bound = block_max_u64(bound);
+  if (threadIdx.x == 0) {
+    const unsigned long long D = best >> 32;
+    if (!skip && !any_wide && best != 0ULL && D > bound) {
+      ctrl->maxkey = best;
+      ctrl->cert = 1u;
+    } else {
+      ctrl->maxkey = 0ULL;
+      ctrl->cert = 0u;
+    }
+  }
+}
+
+// The proof as its own launch (after counting passes over several chunks).
+__global__ void __launch_bounds__(256) k_certify_decide(const CertScratch *cs, Ctrl *ctrl) {
+  certify_decide_block(cs, ctrl);
+}
+
 // One pass over all edges: exact owner degrees and bucket totals, counted in
 // shared memory (32-bit per block) and flushed once per block.
+// decide: the last block to finish also takes the decision (one pass over
+// all edges); otherwise k_certify_decide runs after the last chunk.
 __global__ void __launch_bounds__(512) k_degree_certify(const uint4 *__restrict__ e4, uint64_t n_quads,
                                                         const uint2 *head, const uint2 *tail, uint32_t n,
-                                                        CertScratch *cs, const Ctrl *ctrl) {
+                                                        CertScratch *cs, Ctrl *ctrl, int decide) {
   extern __shared__ uint32_t csm[];
-  if (cert_skipped(ctrl)) return;  // no proof possible: the full histogram runs
+  if (cert_skipped(ctrl)) {  // no proof possible: the full histogram runs
+    if (decide && blockIdx.x == 0 && threadIdx.x == 0) {
+      ctrl->maxkey = 0ULL;
+      ctrl->cert = 0u;
+    }
+    return;
+  }
   uint32_t *key = csm, *own = csm + kCertBuckets, *bk = csm + 2 * kCertBuckets;
   for (uint32_t i = threadIdx.x; i < kCertBuckets; i += blockDim.x) {
     const unsigned long long o = cs->owner[i];
@@ -254,41 +315,15 @@ __global__ void __launch_bounds__(512) k_degree_certify(const uint4 *__restrict_
     if (own[i]) atomicAdd(&cs->cand_cnt[i], (unsigned long long)own[i]);
     if (bk[i]) atomicAdd(&cs->bucket[i], (unsigned long long)bk[i]);
   }
-}
-
-// The proof (one block): D = best owner degree (ties to the smaller id);
-// bound = the largest bucket total of non-owners. D > bound means every other
-// vertex has degree < D.
-__global__ void __launch_bounds__(256) k_certify_decide(const CertScratch *cs, Ctrl *ctrl) {
-  unsigned long long best = 0, bound = 0;
-  bool wide = false;
-  const bool skip = cert_skipped(ctrl);
-  for (uint32_t b = threadIdx.x; b < kCertBuckets && !skip; b += blockDim.x) {
-    const unsigned long long o = cs->owner[b];
-    const unsigned long long t = cs->bucket[b];
-    bound = t > bound ? t : bound;
-    if (!o) continue;
-    const unsigned long long c = cs->cand_cnt[b];
-    if (c >= (1ULL << 32)) {
-      wide = true;
-      continue;
-    }
-    const unsigned long long k = (c << 32) | (uint32_t)o;  // low half: ~vertex
-    best = k > best ? k : best;
-  }
-  const int any_wide = __syncthreads_or(wide);
-  best = block_max_u64(best);
-  bound = block_max_u64(bound);
-  if (threadIdx.x == 0) {
-    const unsigned long long D = best >> 32;
-    if (!skip && !any_wide && best != 0ULL && D > bound) {
-      ctrl->maxkey = best;
-      ctrl->cert = 1u;
-    } else {
-      ctrl->maxkey = 0ULL;
-      ctrl->cert = 0u;
-    }
-  }
+  if (!decide) return;
+  __shared__ unsigned s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&cs->blocks_done, 1u) == gridDim.x - 1u;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  certify_decide_block(cs, ctrl);
 }
 
 // Chunked selection: after the first chunk's candidates are known, decide
@@ -319,7 +354,7 @@ __global__ void k_spec_end(Ctrl *ctrl) {
 
 cudaError_t launch_degree_u32(const EdgeSpan &e, uint32_t *cnt, uint32_t n, cudaStream_t s) {
   const unsigned g = clamp_grid((e.n_quads + 255) / 256, persistent_cap((const void *)k_degree<uint32_t>, 256, 0));
-  k_degree<uint32_t><<<g, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, cnt, n, nullptr);
+  k_degree<uint32_t><<<g, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, cnt, n, nullptr, 0u);
   note_launch();
   return cudaGetLastError();
 }
@@ -368,11 +403,8 @@ cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges
                               (int)kCertSmem, smem_set_certify)) != cudaSuccess)
     return err;
   const unsigned gcert = clamp_grid((e.n_quads + 511) / 512, persistent_cap((const void *)k_degree_certify, 512, kCertSmem));
-  k_degree_certify<<<gcert, 512, kCertSmem, s>>>(e.quads, e.n_quads, e.head, e.tail, n, cs, ctrl);
-  note_launch();
-  // 4. the proof (one small block, so it fits beside resident kernels such as
-  // the serving executor)
-  k_certify_decide<<<1, 256, 0, s>>>(cs, ctrl);
+  // 4. the proof: taken by the counting pass's last block
+  k_degree_certify<<<gcert, 512, kCertSmem, s>>>(e.quads, e.n_quads, e.head, e.tail, n, cs, ctrl, 1);
   note_launch();
   // 5. full histogram, skipped when certified
   const uint32_t *skip = &ctrl->cert;
@@ -382,7 +414,7 @@ cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges
     unsigned long long *c64 = static_cast<unsigned long long *>(cnt);
     k_zero_cnt<unsigned long long><<<gz, 256, 0, s>>>(c64, n, skip);
     note_launch();
-    k_degree<unsigned long long><<<gd, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, c64, n, skip);
+    k_degree<unsigned long long><<<gd, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, c64, n, skip, 0u);
     note_launch();
     k_maxcnt_u64<<<gz, 256, 0, s>>>(c64, n, ctrl, skip);
     note_launch();
@@ -391,9 +423,8 @@ cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges
     k_finalize_m<<<1, 1, 0, s>>>(ctrl, skip);
     note_launch();
   } else {
-    k_zero_cnt<uint32_t><<<gz, 256, 0, s>>>(c32, n, skip);
-    note_launch();
-    k_degree<uint32_t><<<gd, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, c32, n, skip);
+    // the sampled counts are kept: only the edges outside the sample are added
+    k_degree<uint32_t><<<gd, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, c32, n, skip, kCertSample);
     note_launch();
     k_argmax_u32<<<gz, 256, 0, s>>>(c32, n, ctrl, skip);
     note_launch();
@@ -411,10 +442,10 @@ cudaError_t launch_histogram(const EdgeSpan &e, void *cnt, bool wide, uint32_t n
   const unsigned gd = clamp_grid((e.n_quads + 255) / 256, persistent_cap((const void *)k_degree<uint32_t>, 256, 0));
   if (wide)
     k_degree<unsigned long long><<<gd, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail,
-                                                    static_cast<unsigned long long *>(cnt), n, skip);
+                                                    static_cast<unsigned long long *>(cnt), n, skip, 0u);
   else
     k_degree<uint32_t><<<gd, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, static_cast<uint32_t *>(cnt), n,
-                                          skip);
+                                          skip, 0u);
   note_launch();
   return cudaGetLastError();
 }
@@ -483,7 +514,7 @@ cudaError_t chunked_select_chunk(const EdgeSpan &chunk, void *cnt, bool wide, ui
     return err;
   const unsigned gcert =
       clamp_grid((chunk.n_quads + 511) / 512, persistent_cap((const void *)k_degree_certify, 512, kCertSmem));
-  k_degree_certify<<<gcert, 512, kCertSmem, s>>>(chunk.quads, chunk.n_quads, chunk.head, chunk.tail, n, cs, ctrl);
+  k_degree_certify<<<gcert, 512, kCertSmem, s>>>(chunk.quads, chunk.n_quads, chunk.head, chunk.tail, n, cs, ctrl, 0);
   note_launch();
   return cudaGetLastError();
 }

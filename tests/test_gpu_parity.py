@@ -100,11 +100,14 @@ def test_random_ragged(n, m, misalign):
     rng = np.random.default_rng(n * 7919 + m)
     e = rng.integers(0, n, size=(m, 2)).astype(np.uint32)
     want = oracle.min_labels(n, e)
+    m_want = oracle.max_degree_vertex(n, e)
     for mode in (cc.CC_ROOT_MAXDEG, cc.CC_ROOT_IDENTITY):
         for flt in (cc.CC_FILTER_ON, cc.CC_FILTER_OFF):
-            got, ncomp, _ = run_labels(n, e, misalign, mode=mode, filter=flt)
+            got, ncomp, m = run_labels(n, e, misalign, mode=mode, filter=flt)
             np.testing.assert_array_equal(got, want)
             assert ncomp == oracle.num_components(want)
+            if mode == cc.CC_ROOT_MAXDEG:  # no hub: the full histogram (sample + the rest) decides
+                assert m == m_want
 
 
 def test_empty_vertex_set():
