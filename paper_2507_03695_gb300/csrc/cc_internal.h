@@ -142,8 +142,8 @@ cudaError_t launch_argmax_u32(const uint32_t *cnt, uint32_t n, Ctrl *ctrl, cudaS
 // Z: the zero-tree bitmap (one bit per name, zeroed at every init), or null.
 // With Z and zsel null only the zero-tree instance runs; with both, the device
 // picks the zero-tree instance when *zsel is nonzero, the plain one otherwise.
-// one_shot: one grid iteration per block instead of a persistent grid (for
-// work that shares the GPU with a resident kernel).
+// one_shot: short-lived blocks (a few grid iterations each) instead of a
+// persistent grid (for work that shares the GPU with a resident kernel).
 cudaError_t launch_edge_pass(bool rf, int filter, int ept, int block, const EdgeSpan &e, uint32_t *P,
                              uint32_t n, Ctrl *ctrl, const uint32_t *skip, cudaStream_t s,
                              uint32_t *Z = nullptr, const uint32_t *zsel = nullptr, bool one_shot = false);

@@ -521,18 +521,24 @@ cudaError_t launch_init(bool rf, uint32_t *P, uint32_t n, Ctrl *ctrl, int m_src,
 }
 
 namespace {
+constexpr uint64_t kMinWaves = 8;
+
 template <class F, int Q>
 cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, uint32_t n, Ctrl *ctrl,
                         const uint32_t *skip, uint32_t *Z, const uint32_t *zsel, bool one_shot, cudaStream_t s) {
   const uint64_t per_block = (uint64_t)block * Q;
-  // one-shot grids (one iteration per block) let blocks retire continuously,
-  // so that kernels of other streams get SMs while this one runs
+  // At least kMinWaves grid iterations per thread: when a whole graph fits
+  // one wave, every edge reads P before any hooking and duplicate hub edges
+  // then CAS the same roots at once (R-MAT scale 16: 97% of the CAS failed);
+  // later waves find most edges already joined. one_shot: no cap at the
+  // resident blocks, so blocks retire after their kMinWaves iterations and
+  // kernels of other streams get SMs while this one runs.
+  const uint64_t want = (e.n_quads + per_block * kMinWaves - 1) / (per_block * kMinWaves);
   const uint64_t cap_big = 0x7FFFFFFFull;
   if (filter) {
     const size_t smem = (size_t)(block / 32) * 4 * kRing * sizeof(uint32_t);
     static_assert((1024 / 32) * 4 * kRing * sizeof(uint32_t) <= 48 * 1024,
                   "the ring of a 1024-thread block fits the default dynamic shared memory limit");
-    const uint64_t want = (e.n_quads + per_block - 1) / per_block;
     if (Z) {  // the zero-tree instance (alone, or chosen on the device by *zsel)
       const unsigned g = clamp_grid(want, one_shot ? cap_big : persistent_cap((const void *)k_edge_pass_filtered<F, Q, true>, block, smem));
       k_edge_pass_filtered<F, Q, true><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
@@ -545,7 +551,7 @@ cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, u
     }
   } else {
     const void *k = (const void *)k_edge_pass_direct<F, Q>;
-    const unsigned g = clamp_grid((e.n_quads + per_block - 1) / per_block, one_shot ? cap_big : persistent_cap(k, block, 0));
+    const unsigned g = clamp_grid(want, one_shot ? cap_big : persistent_cap(k, block, 0));
     k_edge_pass_direct<F, Q><<<g, block, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
                                                  skip); note_launch();
   }
