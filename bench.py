@@ -91,11 +91,27 @@ def measured_peaks():
 
 
 def kernel_source_sha() -> str:
+    """Hash of the edge-pass kernel's device code: csrc/cc_device.cuh and the
+    text of the k_edge_pass_filtered definition in csrc/cc_kernels.cu (host
+    launch code elsewhere in that file does not change the kernel's traffic)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2507_03695_gb300", "csrc")
-    for name in ("cc_device.cuh", "cc_kernels.cu"):
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
+    with open(os.path.join(csrc, "cc_device.cuh"), "rb") as f:
+        h.update(f.read())
+    with open(os.path.join(csrc, "cc_kernels.cu")) as f:
+        text = f.read()
+    start = text.index("__global__ void __launch_bounds__(512) k_edge_pass_filtered(")
+    start = text.rindex("template", 0, start)
+    depth, i = 0, text.index("{", start)
+    while True:
+        if text[i] == "{":
+            depth += 1
+        elif text[i] == "}":
+            depth -= 1
+            if depth == 0:
+                break
+        i += 1
+    h.update(text[start:i + 1].encode())
     return h.hexdigest()[:16]
 
 
