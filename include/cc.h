@@ -110,6 +110,19 @@ typedef enum cc_label_space {
   CC_LABEL_ROOT_VALUE = 1
 } cc_label_space;
 
+/* Initial Push (Algorithm 4, Section IV): before the edge pass, every
+ * neighbour of the planted vertex m is hooked directly under it (root value
+ * 0), so that the pass starts with m's star formed. Only with f = R and
+ * automatic exact root selection: the neighbours of the sampled argmax m' are
+ * gathered by the selection's counting pass (no extra read of the edges) and
+ * pushed only when m' turns out to be the exact m. The gathered list takes up
+ * to min(n, 2^23) * 4 bytes of device memory; a longer list skips the push. */
+typedef enum cc_initial_push {
+  CC_PUSH_AUTO = 0, /* the library's choice: off (it paid only on some graphs) */
+  CC_PUSH_ON = 1,
+  CC_PUSH_OFF = 2
+} cc_initial_push;
+
 #define CC_ROOT_AUTO UINT64_MAX
 
 typedef struct cc_options {
@@ -123,7 +136,9 @@ typedef struct cc_options {
   int32_t sample_stride;     /* sampled root select keeps 1 group in k; 0 = 16     */
   int32_t timing;            /* nonzero: record per-phase times (cc_phase_times)  */
   uint64_t hbm_budget_bytes; /* device bytes the handle may own; 0 = free memory  */
-  uint64_t reserved[4];      /* must be zero                                       */
+  int32_t initial_push;      /* cc_initial_push, default CC_PUSH_AUTO              */
+  int32_t reserved32;        /* must be zero                                       */
+  uint64_t reserved[3];      /* must be zero                                       */
 } cc_options;
 
 /* Fills *opt with the defaults above. */

@@ -32,6 +32,7 @@ CC_ERR_NOT_READY = 8
 CC_ROOT_IDENTITY, CC_ROOT_MAXDEG = 0, 1
 CC_ROOT_SELECT_EXACT, CC_ROOT_SELECT_SAMPLED = 0, 1
 CC_FILTER_AUTO, CC_FILTER_ON, CC_FILTER_OFF, CC_FILTER_BITMAP = 0, 1, 2, 3
+CC_PUSH_AUTO, CC_PUSH_ON, CC_PUSH_OFF = 0, 1, 2
 CC_LABEL_MIN_ID, CC_LABEL_ROOT_VALUE = 0, 1
 
 
@@ -40,7 +41,7 @@ class cc_options(ctypes.Structure):
         ("mode", _i32), ("root_select", _i32), ("root_hint", _u64), ("filter", _i32),
         ("label_space", _i32), ("block_size", _i32), ("edges_per_thread", _i32),
         ("sample_stride", _i32), ("timing", _i32), ("hbm_budget_bytes", _u64),
-        ("reserved", _u64 * 4),
+        ("initial_push", _i32), ("reserved32", _i32), ("reserved", _u64 * 3),
     ]
 
 

@@ -39,6 +39,8 @@ struct cc_graph {
   bool timed_run = false;
   bool ncomp_fresh = false;
   uint64_t owned = 0;
+  uint32_t *push = nullptr;  // Initial Push list (push_cap entries), or null
+  uint32_t push_cap = 0;
   uint32_t *z = nullptr;   // zero-tree bitmap (one bit per name), or null
   size_t z_bytes = 0;
   bool z_forced = false;   // CC_FILTER_BITMAP: always used
@@ -53,6 +55,16 @@ constexpr uint64_t kZMinBytes = 128ULL << 20;  // CC_FILTER_AUTO: P at least thi
 
 // Bitmap bytes for names 0 .. n (n + 1 names under R), whole 32-bit words.
 size_t z_bytes_for(uint64_t n) { return (size_t)((n + 1 + 31) / 32) * 4; }
+
+// Initial Push: on request only.
+bool wants_push(const cc_options &o) {
+  return o.mode == CC_ROOT_MAXDEG && o.root_hint == CC_ROOT_AUTO && o.root_select != CC_ROOT_SELECT_SAMPLED &&
+         o.initial_push == CC_PUSH_ON;
+}
+uint32_t push_cap_for(uint64_t n) {
+  const uint64_t c = n < (1ULL << 23) ? n : (1ULL << 23);
+  return (uint32_t)((c + cc::kPushLanes - 1) / cc::kPushLanes * cc::kPushLanes);
+}
 
 bool wants_z(const cc_options &o, uint64_t n) {
   if (o.filter == CC_FILTER_BITMAP) return true;
@@ -89,6 +101,7 @@ bool opts_valid(const cc_options &o) {
   if (o.mode != CC_ROOT_IDENTITY && o.mode != CC_ROOT_MAXDEG) return false;
   if (o.root_select != CC_ROOT_SELECT_EXACT && o.root_select != CC_ROOT_SELECT_SAMPLED) return false;
   if (o.filter < CC_FILTER_AUTO || o.filter > CC_FILTER_BITMAP) return false;
+  if (o.initial_push < CC_PUSH_AUTO || o.initial_push > CC_PUSH_OFF || o.reserved32) return false;
   if (o.label_space != CC_LABEL_MIN_ID && o.label_space != CC_LABEL_ROOT_VALUE) return false;
   if (o.block_size != 0 && o.block_size != 128 && o.block_size != 256 && o.block_size != 512)
     return false;
@@ -177,7 +190,8 @@ cc_status root_select(cc_graph *g, const uint32_t *edges, uint64_t n_edges, cons
     CC_TRY(cc::launch_argmax_u32((const uint32_t *)g->cnt, n, g->ctrl, s));
     return CC_OK;
   }
-  CC_TRY(cc::launch_root_select_certified(edges, n_edges, span, g->cnt, wide, n, g->cert, g->ctrl, s));
+  CC_TRY(cc::launch_root_select_certified(edges, n_edges, span, g->cnt, wide, n, g->cert, g->ctrl, s, g->push,
+                                         g->push_cap));
   return CC_OK;
 }
 
@@ -260,7 +274,8 @@ cc_status cc_create(uint64_t n_vertices, uint64_t n_edges_capacity, const cc_opt
   const bool rf = o.mode == CC_ROOT_MAXDEG;
   const size_t need = p_bytes(n_vertices) +
                       (rf ? (size_t)n_vertices * 4 + sizeof(cc::CertScratch) : 0) + sizeof(Ctrl) +
-                      (size_t)n_edges_capacity * 8 + (wants_z(o, n_vertices) ? z_bytes_for(n_vertices) : 0);
+                      (size_t)n_edges_capacity * 8 + (wants_z(o, n_vertices) ? z_bytes_for(n_vertices) : 0) +
+                      (wants_push(o) ? (size_t)push_cap_for(n_vertices) * 4 : 0);
   if (o.hbm_budget_bytes && need > o.hbm_budget_bytes) return CC_ERR_OOM;
 
   cc_graph *g = new (std::nothrow) cc_graph();
@@ -293,6 +308,10 @@ cc_status cc_create(uint64_t n_vertices, uint64_t n_edges_capacity, const cc_opt
     if (n_edges_capacity) {
       if ((e = dev_alloc(g, (void **)&g->staging, (size_t)n_edges_capacity * 8)) != cudaSuccess) break;
       g->capacity = n_edges_capacity;
+    }
+    if (n_vertices && wants_push(o)) {
+      g->push_cap = push_cap_for(n_vertices);
+      if ((e = dev_alloc(g, (void **)&g->push, (size_t)g->push_cap * 4)) != cudaSuccess) break;
     }
     if (n_vertices && wants_z(o, n_vertices)) {
       if ((e = dev_alloc(g, (void **)&g->z, z_bytes_for(n_vertices))) != cudaSuccess) break;
@@ -332,6 +351,7 @@ void cc_destroy(cc_graph *g) {
   dev_free(g, g->staging, (size_t)g->capacity * 8);
   dev_free(g, g->label_dev, (size_t)g->n * 4);
   dev_free(g, g->z, g->z_bytes);
+  dev_free(g, g->push, (size_t)g->push_cap * 4);
   if (g->host_ctrl) cudaFreeHost(g->host_ctrl);
   if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
   if (g->copy_ev) cudaEventDestroy(g->copy_ev);
@@ -366,6 +386,7 @@ cc_status cc_run(cc_graph *g, const uint32_t *edges_dev, uint64_t n_edges, uint3
   }
   record(g, 1, s);
   CC_TRY(cc::launch_init(g->rf, g->P, n, g->ctrl, m_src, hint, s));
+  if (g->push) CC_TRY(cc::launch_initial_push(g->P, n, g->push, g->push_cap, g->cert, g->ctrl, s));
   // the zero-tree bitmap starts empty with every init; without a forced
   // bitmap it is used when this run's exact selection certified a hub
   const bool exact = g->rf && g->opt.root_hint == CC_ROOT_AUTO && g->opt.root_select != CC_ROOT_SELECT_SAMPLED;

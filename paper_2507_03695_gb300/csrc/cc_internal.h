@@ -102,7 +102,13 @@ struct CertScratch {
   unsigned long long cand_cnt[kCertBuckets];  // exact degree of the owner
   unsigned long long bucket[kCertBuckets];    // endpoint occurrences of the other vertices
   unsigned int blocks_done;                   // counting blocks finished (the last one decides)
+  // Initial Push (Algorithm 4): neighbours of the sampled argmax m', appended
+  // through kPushLanes counters, each owning a segment of the push buffer
+  unsigned int push_cnt[256];
+  unsigned int push_m;         // m' + 1 (0: no push list was gathered)
+  unsigned int push_overflow;  // a segment filled up: the push is skipped
 };
+constexpr uint32_t kPushLanes = 256;
 
 // Chunked exact root selection, for edges that arrive in chunks (host input):
 // a dense sample of the first chunk picks candidates and a speculative m'.
@@ -131,9 +137,17 @@ cudaError_t chunked_select_end(const EdgeSpan &all, void *cnt, bool wide, uint32
 // full histogram as a fallback that runs only when the proof fails.
 // cnt holds n counters of 4 bytes (8 when wide); afterwards ctrl->maxkey
 // encodes m ((deg << 32) | ~m for the init kernel).
+// push_buf (push_cap entries, a multiple of kPushLanes), when not null,
+// receives the neighbours of the sampled argmax during the counting pass, for
+// launch_initial_push after init.
 cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges, const EdgeSpan &e,
                                          void *cnt, bool wide, uint32_t n, CertScratch *cs, Ctrl *ctrl,
-                                         cudaStream_t s);
+                                         cudaStream_t s, uint32_t *push_buf = nullptr, uint32_t push_cap = 0);
+// Initial Push (Algorithm 4): right after init, when the planted m is the
+// vertex whose neighbours were gathered, every gathered neighbour x != m gets
+// P[x] = 0 (name 0 is m): x, still a root, is hooked under m.
+cudaError_t launch_initial_push(uint32_t *P, uint32_t n, const uint32_t *push_buf, uint32_t push_cap,
+                                const CertScratch *cs, const Ctrl *ctrl, cudaStream_t s);
 
 cudaError_t launch_degree_u32(const EdgeSpan &e, uint32_t *cnt, uint32_t n, cudaStream_t s);
 cudaError_t launch_degree_sampled_u32(const uint2 *edges, uint64_t n_edges, uint64_t edge_base,

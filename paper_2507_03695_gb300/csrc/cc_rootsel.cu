@@ -258,9 +258,30 @@ __global__ void __launch_bounds__(256) k_certify_decide(const CertScratch *cs, C
 // shared memory (32-bit per block) and flushed once per block.
 // decide: the last block to finish also takes the decision (one pass over
 // all edges); otherwise k_certify_decide runs after the last chunk.
+// With push_buf, the other endpoint of every edge incident to the sampled
+// argmax m' (read from ctrl->maxkey before the decision) is appended to the
+// push list.
+__device__ __forceinline__ void push_neighbour(uint32_t a, uint32_t b, uint32_t mp, uint32_t *buf, uint32_t seg,
+                                               CertScratch *cs) {
+  uint32_t x;
+  if (a == mp && b != mp)
+    x = b;
+  else if (b == mp && a != mp)
+    x = a;
+  else
+    return;
+  const uint32_t lane = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % kPushLanes;
+  const uint32_t i = atomicAdd(&cs->push_cnt[lane], 1u);
+  if (i < seg)
+    buf[(uint64_t)lane * seg + i] = x;
+  else
+    cs->push_overflow = 1u;
+}
+
 __global__ void __launch_bounds__(512) k_degree_certify(const uint4 *__restrict__ e4, uint64_t n_quads,
                                                         const uint2 *head, const uint2 *tail, uint32_t n,
-                                                        CertScratch *cs, Ctrl *ctrl, int decide) {
+                                                        CertScratch *cs, Ctrl *ctrl, int decide, uint32_t *push_buf,
+                                                        uint32_t push_seg) {
   extern __shared__ uint32_t csm[];
   if (cert_skipped(ctrl)) {  // no proof possible: the full histogram runs
     if (decide && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -270,6 +291,9 @@ __global__ void __launch_bounds__(512) k_degree_certify(const uint4 *__restrict_
     return;
   }
   uint32_t *key = csm, *own = csm + kCertBuckets, *bk = csm + 2 * kCertBuckets;
+  // the sampled argmax, whose neighbours the push list gathers
+  const uint32_t mp = ~(uint32_t)(*(const volatile unsigned long long *)&ctrl->maxkey);
+  if (push_buf && blockIdx.x == 0 && threadIdx.x == 0) cs->push_m = mp + 1u;
   for (uint32_t i = threadIdx.x; i < kCertBuckets; i += blockDim.x) {
     const unsigned long long o = cs->owner[i];
     key[i] = o ? (uint32_t)~(uint32_t)o + 1u : 0u;
@@ -284,11 +308,13 @@ __global__ void __launch_bounds__(512) k_degree_certify(const uint4 *__restrict_
     const uint2 e = ld_edge(head);
     cert_count(e.x, key, own, bk);
     cert_count(e.y, key, own, bk);
+    if (push_buf) push_neighbour(e.x, e.y, mp, push_buf, push_seg, cs);
   }
   if (t == 1 % T && tail) {
     const uint2 e = ld_edge(tail);
     cert_count(e.x, key, own, bk);
     cert_count(e.y, key, own, bk);
+    if (push_buf) push_neighbour(e.x, e.y, mp, push_buf, push_seg, cs);
   }
   uint64_t q = t;
   for (; q + T < n_quads; q += 2 * T) {  // two loads in flight per thread
@@ -302,6 +328,12 @@ __global__ void __launch_bounds__(512) k_degree_certify(const uint4 *__restrict_
     cert_count(c.y, key, own, bk);
     cert_count(c.z, key, own, bk);
     cert_count(c.w, key, own, bk);
+    if (push_buf) {
+      push_neighbour(a.x, a.y, mp, push_buf, push_seg, cs);
+      push_neighbour(a.z, a.w, mp, push_buf, push_seg, cs);
+      push_neighbour(c.x, c.y, mp, push_buf, push_seg, cs);
+      push_neighbour(c.z, c.w, mp, push_buf, push_seg, cs);
+    }
   }
   if (q < n_quads) {
     const uint4 a = ld_edges(e4 + q, pol);
@@ -309,6 +341,10 @@ __global__ void __launch_bounds__(512) k_degree_certify(const uint4 *__restrict_
     cert_count(a.y, key, own, bk);
     cert_count(a.z, key, own, bk);
     cert_count(a.w, key, own, bk);
+    if (push_buf) {
+      push_neighbour(a.x, a.y, mp, push_buf, push_seg, cs);
+      push_neighbour(a.z, a.w, mp, push_buf, push_seg, cs);
+    }
   }
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < kCertBuckets; i += blockDim.x) {
@@ -324,6 +360,25 @@ __global__ void __launch_bounds__(512) k_degree_certify(const uint4 *__restrict_
   if (!s_last) return;
   __threadfence();
   certify_decide_block(cs, ctrl);
+}
+
+// Initial Push (Algorithm 4): right after init every vertex is a root, so a
+// gathered neighbour x of m gets parent name 0 (m) by a plain store. Only when
+// the planted m is the vertex whose neighbours were gathered, and no segment
+// overflowed. Row y of the grid takes segment y of the push list.
+__global__ void __launch_bounds__(256) k_initial_push(uint32_t *P, uint32_t n, const uint32_t *buf, uint32_t seg,
+                                                      const CertScratch *cs, const Ctrl *ctrl) {
+  const uint32_t pm = *(const volatile uint32_t *)&cs->push_m;
+  if (pm == 0u || *(const volatile uint32_t *)&cs->push_overflow) return;
+  const uint32_t m = *(const volatile uint32_t *)&ctrl->m;
+  if (pm - 1u != m) return;
+  const uint32_t lane = blockIdx.y;
+  const uint32_t cnt = min(*(const volatile uint32_t *)&cs->push_cnt[lane], seg);
+  const uint32_t *b = buf + (uint64_t)lane * seg;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    const uint32_t x = b[i];
+    if (x < n && x != m) P[x] = 0u;
+  }
 }
 
 // Chunked selection: after the first chunk's candidates are known, decide
@@ -379,7 +434,7 @@ cudaError_t launch_argmax_u32(const uint32_t *cnt, uint32_t n, Ctrl *ctrl, cudaS
 
 cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges, const EdgeSpan &e,
                                          void *cnt, bool wide, uint32_t n, CertScratch *cs, Ctrl *ctrl,
-                                         cudaStream_t s) {
+                                         cudaStream_t s, uint32_t *push_buf, uint32_t push_cap) {
   cudaError_t err;
   // 0. reset the sampled counters, the scratch and the control fields
   if ((err = cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(uint32_t), s)) != cudaSuccess) return err;
@@ -403,8 +458,10 @@ cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges
                               (int)kCertSmem, smem_set_certify)) != cudaSuccess)
     return err;
   const unsigned gcert = clamp_grid((e.n_quads + 511) / 512, persistent_cap((const void *)k_degree_certify, 512, kCertSmem));
-  // 4. the proof: taken by the counting pass's last block
-  k_degree_certify<<<gcert, 512, kCertSmem, s>>>(e.quads, e.n_quads, e.head, e.tail, n, cs, ctrl, 1);
+  // 4. the proof: taken by the counting pass's last block (which also
+  // gathers the push list when asked to)
+  k_degree_certify<<<gcert, 512, kCertSmem, s>>>(e.quads, e.n_quads, e.head, e.tail, n, cs, ctrl, 1, push_buf,
+                                                 push_buf ? push_cap / kPushLanes : 0u);
   note_launch();
   // 5. full histogram, skipped when certified
   const uint32_t *skip = &ctrl->cert;
@@ -514,7 +571,8 @@ cudaError_t chunked_select_chunk(const EdgeSpan &chunk, void *cnt, bool wide, ui
     return err;
   const unsigned gcert =
       clamp_grid((chunk.n_quads + 511) / 512, persistent_cap((const void *)k_degree_certify, 512, kCertSmem));
-  k_degree_certify<<<gcert, 512, kCertSmem, s>>>(chunk.quads, chunk.n_quads, chunk.head, chunk.tail, n, cs, ctrl, 0);
+  k_degree_certify<<<gcert, 512, kCertSmem, s>>>(chunk.quads, chunk.n_quads, chunk.head, chunk.tail, n, cs, ctrl, 0,
+                                                 nullptr, 0u);
   note_launch();
   return cudaGetLastError();
 }
@@ -534,6 +592,16 @@ cudaError_t chunked_select_end(const EdgeSpan &all, void *cnt, bool wide, uint32
   if ((err = launch_zero(cnt, wide, n, full, s)) != cudaSuccess) return err;
   if ((err = launch_histogram(all, cnt, wide, n, full, s)) != cudaSuccess) return err;
   return launch_hist_argmax(cnt, wide, n, ctrl, full, s);
+}
+
+cudaError_t launch_initial_push(uint32_t *P, uint32_t n, const uint32_t *push_buf, uint32_t push_cap,
+                                const CertScratch *cs, const Ctrl *ctrl, cudaStream_t s) {
+  if (!push_buf || n == 0) return cudaSuccess;
+  const uint32_t seg = push_cap / kPushLanes;
+  const dim3 grid(clamp_grid(((uint64_t)seg + 255) / 256, 16), kPushLanes);
+  k_initial_push<<<grid, 256, 0, s>>>(P, n, push_buf, seg, cs, ctrl);
+  note_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace cc

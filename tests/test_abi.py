@@ -97,6 +97,11 @@ def test_host_side_errors(lib):
     bad = lib.cc_options_init()
     bad.reserved[2] = 1
     assert L.cc_create(10, 0, ctypes.byref(bad), ctypes.byref(h)) == lib.CC_ERR_INVALID_ARGUMENT
+    bad = lib.cc_options_init(initial_push=3)
+    assert L.cc_create(10, 0, ctypes.byref(bad), ctypes.byref(h)) == lib.CC_ERR_INVALID_ARGUMENT
+    bad = lib.cc_options_init()
+    bad.reserved32 = 1
+    assert L.cc_create(10, 0, ctypes.byref(bad), ctypes.byref(h)) == lib.CC_ERR_INVALID_ARGUMENT
     # the HBM budget refuses before any allocation
     small = lib.cc_options_init(hbm_budget_bytes=1 << 20)
     assert L.cc_create(1 << 20, 0, ctypes.byref(small), ctypes.byref(h)) == lib.CC_ERR_OOM

@@ -434,6 +434,42 @@ def test_root_select_hidden_hub(extra):
     np.testing.assert_array_equal(got, oracle.root_value_labels(n, e, want_m))
 
 
+def _push_case(case):
+    if case == "rmat16":
+        w = graphgen.RMAT16
+        return w.n_vertices, w.host_edges(), False
+    if case == "rmat20":  # several grid waves
+        return 1 << 20, graphgen.rmat(20, 1 << 24, 70, scramble=True), False
+    if case == "grid":  # no dominant hub: no certificate, no push list
+        return 512 * 512, graphgen.grid(512, 512, 3), False
+    if case == "ragged":  # misaligned head and odd tail
+        e = graphgen.rmat(18, 900013, 72, scramble=True)
+        return 1 << 18, e, True
+    extra = 5000 if case == "hidden_other" else -1
+    n, e = _hidden_hub_graph(extra)  # the sampled argmax is (or is not) the exact m
+    return n, e, False
+
+
+@pytest.mark.parametrize("case", ["rmat16", "rmat20", "grid", "ragged", "hidden_same", "hidden_other"])
+def test_initial_push(case):
+    """Initial Push (Algorithm 4) hooks the neighbours of m before the edge
+    pass; labels, m and the component count must not change, and the push
+    must be skipped when the gathered neighbours belong to another vertex."""
+    n, e, misalign = _push_case(case)
+    want = oracle.min_labels(n, e)
+    m_want = oracle.max_degree_vertex(n, e)
+    for label_space in (cc.CC_LABEL_MIN_ID, cc.CC_LABEL_ROOT_VALUE):
+        for _ in range(2):
+            got, ncomp, m = run_labels(n, e, misalign, mode=cc.CC_ROOT_MAXDEG, initial_push=cc.CC_PUSH_ON,
+                                       label_space=label_space)
+            assert m == m_want
+            assert ncomp == oracle.num_components(want)
+            if label_space == cc.CC_LABEL_MIN_ID:
+                np.testing.assert_array_equal(got, want)
+            else:
+                np.testing.assert_array_equal(got, oracle.root_value_labels(n, e, m_want))
+
+
 def test_root_select_many_candidates():
     """Thousands of equally heavy vertices (more than the candidate list
     holds) plus one slightly heavier: still the exact maximum."""
