@@ -208,6 +208,17 @@ def _check(rc: int, what: str) -> None:
         raise RuntimeError(f"{what} failed with CUDA error {rc}")
 
 
+def pack_ids(edges: np.ndarray, id_bytes: int = 3) -> np.ndarray:
+    """The compact host layout of cc_run_host_packed: every id in id_bytes
+    little-endian bytes, u then v, no padding (uint8[2 * id_bytes * E])."""
+    e = np.ascontiguousarray(edges, dtype=np.uint32).reshape(-1)
+    if id_bytes == 4:
+        return e.view(np.uint8).copy()
+    if id_bytes != 3 or (len(e) and int(e.max()) >= 1 << 24):
+        raise ValueError("3-byte ids hold values below 2^24")
+    return e.view(np.uint8).reshape(-1, 4)[:, :3].reshape(-1).copy()
+
+
 def rmat_dev(scale: int, n_edges: int, seed: int, scramble: bool = True, out=None,
              e_begin: int = 0, e_end: int | None = None, stream=None):
     """R-MAT edges generated directly in HBM; returns a (E, 2) uint32-valued

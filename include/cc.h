@@ -171,13 +171,27 @@ CC_API cc_status cc_run(cc_graph *g, const uint32_t *edges_dev, uint64_t n_edges
                  cc_stream_t stream);
 
 /* cc_run on host buffers: copies the n_edges pairs (n_edges <= the handle's
- * n_edges_capacity) to the device in chunks that overlap the root-selection
- * histogram (or, when m is known in advance, the edge pass itself), runs the
- * pass and copies the labels to L_out_host (uint32[n_vertices], may be NULL).
- * Synchronising: returns after the labels are in host memory, with any device
- * error. */
+ * n_edges_capacity) to the device in chunks of 2^24 edges and works on each
+ * chunk as it lands: with m known in advance (identity, or a hint) the edge
+ * pass; with exact selection, hooking under a speculative m' taken from the
+ * first chunk while the certificate's counts accumulate, then one more
+ * init + edge pass only if m' was not the exact m; with sampled selection,
+ * nothing until the last chunk. The labels go to L_out_host
+ * (uint32[n_vertices], may be NULL). Synchronising: returns after the labels
+ * are in host memory, with any device error. */
 CC_API cc_status cc_run_host(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges,
                       uint32_t *L_out_host, cc_stream_t stream);
+
+/* cc_run_host on compactly encoded edges (Section V sends ids in the fewest
+ * whole bytes that hold them): each id takes id_bytes little-endian bytes,
+ * an edge is u then v, 2 * id_bytes bytes per edge, no padding. id_bytes is
+ * 3 (requires n_vertices <= 2^24) or 4 (the layout of cc_run_host). The
+ * packed bytes cross the host link; each chunk is unpacked on the device into
+ * the staging buffer, and the work of cc_run_host follows. The unpacking uses
+ * two device buffers of 2^24 packed edges each, allocated at the first call.
+ * CC_ERR_INVALID_ARGUMENT for another id_bytes or n_vertices > 2^24 with 3. */
+CC_API cc_status cc_run_host_packed(cc_graph *g, const uint8_t *edges_host, uint64_t n_edges, int32_t id_bytes,
+                             uint32_t *L_out_host, cc_stream_t stream);
 
 /* Incremental union: applies n_edges new pairs to the live P without
  * re-initialisation, exactly as the edge pass does (JT processes edges in any

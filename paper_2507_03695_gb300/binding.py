@@ -101,6 +101,7 @@ def lib():
             "cc_create": (_i32, [_u64, _u64, P(cc_options), P(_ptr)]),
             "cc_run": (_i32, [_ptr, _ptr, _u64, _ptr, _ptr]),
             "cc_run_host": (_i32, [_ptr, _ptr, _u64, _ptr, _ptr]),
+            "cc_run_host_packed": (_i32, [_ptr, _ptr, _u64, _i32, _ptr, _ptr]),
             "cc_stream_insert": (_i32, [_ptr, _ptr, _u64, _ptr]),
             "cc_labels": (_i32, [_ptr, _ptr, _ptr]),
             "cc_connected": (_i32, [_ptr, _ptr, _u64, _ptr, _ptr]),
@@ -205,6 +206,12 @@ def cc_create(n_vertices: int, n_edges_capacity: int = 0, opt: cc_options | None
 def cc_run(g: int, edges, n_edges: int | None = None, L_out=None, stream=None) -> None:
     _check(lib().cc_run(g, _addr(edges), _count_pairs(edges, n_edges), _addr(L_out), _stream(stream)),
            "cc_run")
+
+
+def cc_run_host_packed(g: int, edges_host, n_edges: int, id_bytes: int, L_out_host=None, stream=None) -> None:
+    """edges_host: a host buffer of 2 * id_bytes * n_edges bytes (pinned for speed)."""
+    _check(lib().cc_run_host_packed(g, _addr(edges_host), int(n_edges), int(id_bytes), _addr(L_out_host),
+                                    _stream(stream)), "cc_run_host_packed")
 
 
 def cc_run_host(g: int, edges_host, n_edges: int | None = None, L_out_host=None, stream=None) -> None:

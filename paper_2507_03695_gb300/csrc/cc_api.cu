@@ -39,6 +39,9 @@ struct cc_graph {
   bool timed_run = false;
   bool ncomp_fresh = false;
   uint64_t owned = 0;
+  uint8_t *pk[2] = {nullptr, nullptr};  // cc_run_host_packed: packed chunk slots
+  size_t pk_bytes = 0;                   // bytes of each slot
+  cudaEvent_t pk_ev[2] = {nullptr, nullptr};  // a slot's last unpack has run
   uint32_t *push = nullptr;  // Initial Push list (push_cap entries), or null
   uint32_t push_cap = 0;
   uint32_t *z = nullptr;   // zero-tree bitmap (one bit per name), or null
@@ -352,6 +355,10 @@ void cc_destroy(cc_graph *g) {
   dev_free(g, g->label_dev, (size_t)g->n * 4);
   dev_free(g, g->z, g->z_bytes);
   dev_free(g, g->push, (size_t)g->push_cap * 4);
+  for (int i = 0; i < 2; ++i) {
+    dev_free(g, g->pk[i], g->pk_bytes);
+    if (g->pk_ev[i]) cudaEventDestroy(g->pk_ev[i]);
+  }
   if (g->host_ctrl) cudaFreeHost(g->host_ctrl);
   if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
   if (g->copy_ev) cudaEventDestroy(g->copy_ev);
@@ -404,8 +411,10 @@ cc_status cc_run(cc_graph *g, const uint32_t *edges_dev, uint64_t n_edges, uint3
   return CC_OK;
 }
 
-cc_status cc_run_host(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges, uint32_t *L_out_host,
-                      cc_stream_t stream) {
+// The work of cc_run_host; id_bytes 0: edges_host holds uint32 pairs;
+// 3: packed ids, copied into the two slots in turn and unpacked on s.
+static cc_status run_host_impl(cc_graph *g, const void *edges_host, uint64_t n_edges, int id_bytes, uint32_t *L_out_host,
+                        cc_stream_t stream) {
   if (!g) return CC_ERR_INVALID_ARGUMENT;
   if (n_edges && !edges_host) return CC_ERR_INVALID_ARGUMENT;
   if (n_edges > g->capacity) return CC_ERR_TOO_LARGE;
@@ -437,11 +446,24 @@ cc_status cc_run_host(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges,
   const uint32_t *no_spec = &g->ctrl->skip[cc::kSkipSpec];
   for (uint64_t off = 0; off < n_edges; off += kHostChunk) {
     const uint64_t cnt = (n_edges - off) < kHostChunk ? (n_edges - off) : kHostChunk;
-    CC_TRY(cudaMemcpyAsync(g->staging + 2 * off, edges_host + 2 * off, cnt * 8, cudaMemcpyHostToDevice,
-                           g->copy_stream));
-    if (select && !chunked) continue;
-    CC_TRY(cudaEventRecord(g->copy_ev, g->copy_stream));
-    CC_TRY(cudaStreamWaitEvent(s, g->copy_ev, 0));
+    if (id_bytes == 3) {
+      // a slot is refilled only after the unpack of the chunk before last
+      const int slot = (int)((off / kHostChunk) & 1u);
+      if (off >= 2 * kHostChunk) CC_TRY(cudaStreamWaitEvent(g->copy_stream, g->pk_ev[slot], 0));
+      CC_TRY(cudaMemcpyAsync(g->pk[slot], static_cast<const uint8_t *>(edges_host) + 6 * off, cnt * 6,
+                             cudaMemcpyHostToDevice, g->copy_stream));
+      CC_TRY(cudaEventRecord(g->copy_ev, g->copy_stream));
+      CC_TRY(cudaStreamWaitEvent(s, g->copy_ev, 0));
+      CC_TRY(cc::launch_unpack3(g->pk[slot], cnt, g->staging + 2 * off, s));
+      CC_TRY(cudaEventRecord(g->pk_ev[slot], s));
+      if (select && !chunked) continue;
+    } else {
+      CC_TRY(cudaMemcpyAsync(g->staging + 2 * off, static_cast<const uint32_t *>(edges_host) + 2 * off, cnt * 8,
+                             cudaMemcpyHostToDevice, g->copy_stream));
+      if (select && !chunked) continue;
+      CC_TRY(cudaEventRecord(g->copy_ev, g->copy_stream));
+      CC_TRY(cudaStreamWaitEvent(s, g->copy_ev, 0));
+    }
     const cc::EdgeSpan chunk = cc::split_edges(g->staging + 2 * off, cnt);
     if (chunked && off == 0) {
       CC_TRY(cc::chunked_select_begin(g->staging, cnt, g->cnt, wide, n, g->cert, g->ctrl, s));
@@ -464,8 +486,10 @@ cc_status cc_run_host(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges,
     CC_TRY(cc::launch_edge_pass(true, eff_filter(g), eff_ept(g), eff_block(g), all, g->P, n, g->ctrl, held, s,
                                 g->z, Zf ? nullptr : &g->ctrl->cert));
   } else if (select) {
-    CC_TRY(cudaEventRecord(g->copy_ev, g->copy_stream));
-    CC_TRY(cudaStreamWaitEvent(s, g->copy_ev, 0));
+    if (id_bytes != 3) {  // (packed chunks were unpacked on s already)
+      CC_TRY(cudaEventRecord(g->copy_ev, g->copy_stream));
+      CC_TRY(cudaStreamWaitEvent(s, g->copy_ev, 0));
+    }
     int m_src = cc::kMFromHint;
     cc_status st = root_select(g, g->staging, n_edges, all, s, &m_src);
     if (st != CC_OK) return st;
@@ -479,6 +503,29 @@ cc_status cc_run_host(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges,
     CC_TRY(cudaMemcpyAsync(L_out_host, g->label_dev, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
   g->ncomp_fresh = true;
   return fetch_ctrl(g, s);
+}
+
+cc_status cc_run_host(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges, uint32_t *L_out_host,
+                      cc_stream_t stream) {
+  return run_host_impl(g, edges_host, n_edges, 0, L_out_host, stream);
+}
+
+cc_status cc_run_host_packed(cc_graph *g, const uint8_t *edges_host, uint64_t n_edges, int32_t id_bytes,
+                             uint32_t *L_out_host, cc_stream_t stream) {
+  if (!g) return CC_ERR_INVALID_ARGUMENT;
+  if (id_bytes == 4) return run_host_impl(g, edges_host, n_edges, 0, L_out_host, stream);
+  if (id_bytes != 3 || g->n > (1ULL << 24)) return CC_ERR_INVALID_ARGUMENT;
+  if (n_edges && !edges_host) return CC_ERR_INVALID_ARGUMENT;
+  if (n_edges > g->capacity) return CC_ERR_TOO_LARGE;
+  if (!g->pk[0] && n_edges) {
+    DeviceGuard dg(g->device);
+    g->pk_bytes = (size_t)kHostChunk * 6;
+    for (int i = 0; i < 2; ++i) {
+      CC_TRY(dev_alloc(g, (void **)&g->pk[i], g->pk_bytes));
+      CC_TRY(cudaEventCreateWithFlags(&g->pk_ev[i], cudaEventDisableTiming));
+    }
+  }
+  return run_host_impl(g, edges_host, n_edges, 3, L_out_host, stream);
 }
 
 cc_status cc_stream_insert(cc_graph *g, const uint32_t *edges_dev, uint64_t n_edges, cc_stream_t stream) {

@@ -150,6 +150,9 @@ cudaError_t launch_initial_push(uint32_t *P, uint32_t n, const uint32_t *push_bu
                                 const CertScratch *cs, const Ctrl *ctrl, cudaStream_t s);
 
 cudaError_t launch_degree_u32(const EdgeSpan &e, uint32_t *cnt, uint32_t n, cudaStream_t s);
+// Unpacks n_edges edges of 3-byte ids (cc_pack.cu; src 16-byte aligned) into
+// uint32 pairs at dst (16-byte aligned).
+cudaError_t launch_unpack3(const uint8_t *src, uint64_t n_edges, uint32_t *dst, cudaStream_t s);
 cudaError_t launch_degree_sampled_u32(const uint2 *edges, uint64_t n_edges, uint64_t edge_base,
                                       uint32_t stride, uint32_t *cnt, uint32_t n, cudaStream_t s);
 cudaError_t launch_argmax_u32(const uint32_t *cnt, uint32_t n, Ctrl *ctrl, cudaStream_t s);

@@ -394,6 +394,43 @@ def test_zero_tree_bitmap_large(rmat25, flt):
         np.testing.assert_array_equal(L.cpu().numpy().view(np.uint32), r["want_er"])
 
 
+@pytest.mark.parametrize("mode,select", [(cc.CC_ROOT_MAXDEG, cc.CC_ROOT_SELECT_EXACT),
+                                         (cc.CC_ROOT_MAXDEG, cc.CC_ROOT_SELECT_SAMPLED),
+                                         (cc.CC_ROOT_IDENTITY, cc.CC_ROOT_SELECT_EXACT)])
+def test_run_host_packed(mode, select):
+    """Compact 3-byte ids over the host link: several chunks (the two unpack
+    slots are reused) and a tail that is not a whole group of eight edges."""
+    n = 1 << 20
+    E = 3 * (1 << 24) + 77
+    e = graphgen.rmat(20, E, 73, scramble=True)
+    want = oracle.min_labels(n, e)
+    packed = torch.from_numpy(graphgen.pack_ids(e, 3)).pin_memory()
+    plain = torch.from_numpy(graphgen.pack_ids(e, 4)).pin_memory()
+    L = torch.empty(n, dtype=torch.int32).pin_memory()
+    with cc.Graph(n, E, mode=mode, root_select=select) as g:
+        for _ in range(2):
+            L.fill_(-1)
+            cc.cc_run_host_packed(g.h, packed, E, 3, L)
+            np.testing.assert_array_equal(L.numpy().view(np.uint32), want)
+        if mode == cc.CC_ROOT_MAXDEG and select == cc.CC_ROOT_SELECT_EXACT:
+            assert g.root_vertex() == oracle.max_degree_vertex(n, e)
+        L.fill_(-1)
+        cc.cc_run_host_packed(g.h, plain, E, 4, L)  # 4-byte ids: the cc_run_host layout
+        np.testing.assert_array_equal(L.numpy().view(np.uint32), want)
+        for bad in (2, 5):
+            with pytest.raises(cc.CCError):
+                cc.cc_run_host_packed(g.h, packed, E, bad, L)
+    small = graphgen.rmat(10, 1001, 74, scramble=True)  # one chunk, ragged
+    ps = torch.from_numpy(graphgen.pack_ids(small, 3)).pin_memory()
+    Ls = torch.empty(1 << 10, dtype=torch.int32).pin_memory()
+    with cc.Graph(1 << 10, 1001, mode=mode, root_select=select) as g:
+        cc.cc_run_host_packed(g.h, ps, 1001, 3, Ls)
+        np.testing.assert_array_equal(Ls.numpy().view(np.uint32), oracle.min_labels(1 << 10, small))
+    with cc.Graph((1 << 24) + 1, 10) as g:  # 3-byte ids cannot name every vertex
+        with pytest.raises(cc.CCError):
+            cc.cc_run_host_packed(g.h, ps, 10, 3, None)
+
+
 def test_phase_times_and_budget():
     n = 1 << 16
     e = graphgen.rmat(16, 1 << 20, 1, scramble=False)
