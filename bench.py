@@ -64,6 +64,7 @@ def parse_args(argv=None):
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batched-graphs", type=int, default=4096)
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-csr", action="store_true")
     p.add_argument("--serving-requests", type=int, default=2000,
                    help="requests per arrival rate (the full configuration uses 20000)")
     p.add_argument("--cpu-fraction", type=float, default=1 / 8,
@@ -78,6 +79,18 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def device_csr(e, n: int):
+    """CSR of a device edge list for cc_run_csr: rows by source in input order
+    (a stable sort), offsets int64[n + 1], neighbors int32 (uint32 ids)."""
+    import torch
+    u = e[:, 0].long()
+    order = torch.sort(u, stable=True).indices
+    nb = e[:, 1].index_select(0, order).contiguous()
+    off = torch.zeros(n + 1, dtype=torch.int64, device=e.device)
+    off[1:] = torch.cumsum(torch.bincount(u, minlength=n), 0)
+    return off, nb
 
 
 def measured_peaks():
@@ -421,6 +434,7 @@ def run_ours(args):
 
     for h in handles:
         h.close()
+    csr = None if args.no_csr else bench_csr(args, cc, graphs, torch, stream)
     batched = None if args.no_batched else bench_batched(args, cc, graphgen, torch, stream)
     serving = None
     if not args.no_serving:
@@ -457,6 +471,7 @@ def run_ours(args):
             "path_algorithmic_gbs": path_bytes / (ms_per_step * 1e-3) / 1e9,
             "gteps_without_root_select": E_total / (sum(p[4] - p[0] for p in phase_ms) * 1e-3) / 1e9,
             "e2e": e2e,
+            "csr": csr,
             "batched": batched,
             "serving": serving,
             "cpu_baseline": cpu,
@@ -475,6 +490,42 @@ def percentile(xs, q):
         return None
     k = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
     return xs[k]
+
+
+def bench_csr(args, cc, graphs, torch, stream):
+    """The same graphs as CSR (rows sorted by source, built on the device
+    before timing): cc_run_csr, timed like the main step."""
+    csr = [device_csr(e, w.n_vertices) for w, e, _ in graphs]
+    handles = [cc.Graph(w.n_vertices, **BENCH_OPTIONS, timing=1) for w, _, _ in graphs]
+    labels = [torch.empty(w.n_vertices, dtype=torch.int32, device="cuda") for w, _, _ in graphs]
+
+    def step():
+        for h, (off, nb), L in zip(handles, csr, labels):
+            cc.cc_run_csr(h.h, off, nb, nb.shape[0], L, stream)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    for h in handles:
+        h.sync()
+        cc.cc_phase_times_total(h.h)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    phases = {}
+    for (w, _, _), h in zip(graphs, handles):
+        tot, runs = cc.cc_phase_times_total(h.h)
+        p = [x / max(runs, 1) for x in tot]
+        phases[w.name] = {"root_select": p[0], "init": p[1], "edge_pass": p[2], "flatten": p[3], "total": p[4]}
+        h.close()
+    E = sum(E for _, _, E in graphs)
+    return {"gteps": E / (ms * 1e-3) / 1e9, "ms_per_step": ms, "phases_ms": phases,
+            "input": "CSR, rows by source (stable), offsets int64, neighbors uint32; m = longest row",
+            "api": "cc_run_csr"}
 
 
 def bench_batched(args, cc, graphgen, torch, stream):

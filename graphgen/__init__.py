@@ -208,6 +208,17 @@ def _check(rc: int, what: str) -> None:
         raise RuntimeError(f"{what} failed with CUDA error {rc}")
 
 
+def to_csr(n: int, edges: np.ndarray):
+    """CSR layout of a COO edge list for cc_run_csr: offsets (uint64[n + 1])
+    and neighbors (uint32), row u holding the v of every pair (u, v) in input
+    order (a stable sort by u). No symmetrisation."""
+    e = np.ascontiguousarray(edges, dtype=np.uint32).reshape(-1, 2)
+    order = np.argsort(e[:, 0], kind="stable")
+    offsets = np.zeros(n + 1, dtype=np.uint64)
+    np.cumsum(np.bincount(e[:, 0], minlength=n), out=offsets[1:])
+    return offsets, np.ascontiguousarray(e[order, 1])
+
+
 def pack_ids(edges: np.ndarray, id_bytes: int = 3) -> np.ndarray:
     """The compact host layout of cc_run_host_packed: every id in id_bytes
     little-endian bytes, u then v, no padding (uint8[2 * id_bytes * E])."""

@@ -170,6 +170,22 @@ CC_API cc_status cc_create(uint64_t n_vertices, uint64_t n_edges_capacity, const
 CC_API cc_status cc_run(cc_graph *g, const uint32_t *edges_dev, uint64_t n_edges, uint32_t *L_out_dev,
                  cc_stream_t stream);
 
+/* cc_run on CSR input, the layout the paper's implementation keeps in memory
+ * (Section V): offsets_dev[n_vertices + 1] (uint64, offsets_dev[0] = 0,
+ * never decreasing, offsets_dev[n_vertices] = n_entries) and
+ * neighbors_dev[n_entries] (uint32). The edges are (u, neighbors_dev[j]) for
+ * offsets_dev[u] <= j < offsets_dev[u + 1]; the graph need not be symmetric
+ * (Section II). Under f = R with automatic selection, m is the vertex with the
+ * longest row (the degree that Algorithm 4's max_degree() reads from the
+ * offsets), ties to the smaller id. The edge pass walks the neighbor array in
+ * order, so the entries of one row share the parent load of their row.
+ * Stream-ordered; malformed offsets are reported as CC_ERR_INVALID_ARGUMENT
+ * and a neighbor id >= n_vertices as CC_ERR_OUT_OF_RANGE at the next
+ * synchronising call (the labels are then undefined). Allocates 4 bytes per
+ * 1024 entries on the first call of a larger size. */
+CC_API cc_status cc_run_csr(cc_graph *g, const uint64_t *offsets_dev, const uint32_t *neighbors_dev,
+                     uint64_t n_entries, uint32_t *L_out_dev, cc_stream_t stream);
+
 /* cc_run on host buffers: copies the n_edges pairs (n_edges <= the handle's
  * n_edges_capacity) to the device in chunks of 2^24 edges and works on each
  * chunk as it lands: with m known in advance (identity, or a hint) the edge

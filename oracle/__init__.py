@@ -74,6 +74,8 @@ def _L():
         lib.oracle_bfs_labels.restype = _i32
         lib.oracle_max_degree_vertex.argtypes = [_u64, _ptr, _u64, _ptr]
         lib.oracle_max_degree_vertex.restype = _i64
+        lib.oracle_csr_max_row_vertex.argtypes = [_u64, _ptr]
+        lib.oracle_csr_max_row_vertex.restype = _i64
         lib.oracle_degree_add.argtypes = [_u64, _ptr, _u64, _ptr]
         lib.oracle_degree_add.restype = _i32
         lib.oracle_num_components.argtypes = [_u64, _ptr]
@@ -125,6 +127,23 @@ def root_value_labels(n: int, edges, m: int) -> np.ndarray:
     _ok(_L().oracle_root_value_labels(n, e.ctypes.data, len(e), m, L.ctypes.data),
         "root_value_labels")
     return L
+
+
+def csr_max_row_vertex(n: int, offsets) -> int:
+    """CSR input: the vertex with the longest row, smallest id on ties."""
+    off = np.ascontiguousarray(offsets, dtype=np.uint64)
+    if len(off) != n + 1:
+        raise ValueError("offsets must hold n + 1 entries")
+    m = _L().oracle_csr_max_row_vertex(n, off.ctypes.data)
+    _ok(int(m), "csr_max_row_vertex")
+    return int(m)
+
+
+def csr_edges(offsets, neighbors) -> np.ndarray:
+    """The (u, v) pairs a CSR graph stands for, in storage order."""
+    off = np.asarray(offsets, dtype=np.int64)
+    u = np.repeat(np.arange(len(off) - 1, dtype=np.uint32), np.diff(off))
+    return np.stack([u, np.asarray(neighbors, dtype=np.uint32)], axis=1)
 
 
 def max_degree_vertex(n: int, edges, return_degrees: bool = False):

@@ -220,6 +220,24 @@ ORACLE_EXPORT int64_t oracle_max_degree_vertex(uint64_t n, const uint32_t *edges
   return (int64_t)best;
 }
 
+/* CSR input (Section V keeps graphs as offsets + neighbors): the vertex
+ * whose row is longest, the smaller id on ties, as Algorithm 4 reads
+ * max_degree() from the offsets. Returns -1 for malformed offsets (not
+ * starting at 0 or decreasing) and for n == 0. */
+ORACLE_EXPORT int64_t oracle_csr_max_row_vertex(uint64_t n, const uint64_t *offsets) {
+  if (n == 0 || offsets[0] != 0) return -1;
+  uint64_t best = 0, best_len = 0;
+  for (uint64_t v = 0; v < n; ++v) {
+    if (offsets[v + 1] < offsets[v]) return -1;
+    const uint64_t len = offsets[v + 1] - offsets[v];
+    if (len > best_len) { /* strictly longer: an earlier (smaller) id keeps ties */
+      best = v;
+      best_len = len;
+    }
+  }
+  return (int64_t)best;
+}
+
 /* Streaming degree count for inputs that do not fit in memory at once. */
 ORACLE_EXPORT int oracle_degree_add(uint64_t n, const uint32_t *edges, uint64_t n_edges,
                                     uint64_t *deg) {

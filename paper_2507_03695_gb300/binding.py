@@ -102,6 +102,7 @@ def lib():
             "cc_run": (_i32, [_ptr, _ptr, _u64, _ptr, _ptr]),
             "cc_run_host": (_i32, [_ptr, _ptr, _u64, _ptr, _ptr]),
             "cc_run_host_packed": (_i32, [_ptr, _ptr, _u64, _i32, _ptr, _ptr]),
+            "cc_run_csr": (_i32, [_ptr, _ptr, _ptr, _u64, _ptr, _ptr]),
             "cc_stream_insert": (_i32, [_ptr, _ptr, _u64, _ptr]),
             "cc_labels": (_i32, [_ptr, _ptr, _ptr]),
             "cc_connected": (_i32, [_ptr, _ptr, _u64, _ptr, _ptr]),
@@ -206,6 +207,14 @@ def cc_create(n_vertices: int, n_edges_capacity: int = 0, opt: cc_options | None
 def cc_run(g: int, edges, n_edges: int | None = None, L_out=None, stream=None) -> None:
     _check(lib().cc_run(g, _addr(edges), _count_pairs(edges, n_edges), _addr(L_out), _stream(stream)),
            "cc_run")
+
+
+def cc_run_csr(g: int, offsets, neighbors, n_entries: int | None = None, L_out=None, stream=None) -> None:
+    """offsets: uint64[n + 1] on the device (an int64 tensor), neighbors: uint32[n_entries]."""
+    if n_entries is None:
+        n_entries = int(neighbors.numel()) if hasattr(neighbors, "numel") else int(neighbors.size)
+    _check(lib().cc_run_csr(g, _addr(offsets), _addr(neighbors), int(n_entries), _addr(L_out), _stream(stream)),
+           "cc_run_csr")
 
 
 def cc_run_host_packed(g: int, edges_host, n_edges: int, id_bytes: int, L_out_host=None, stream=None) -> None:

@@ -39,6 +39,8 @@ struct cc_graph {
   bool timed_run = false;
   bool ncomp_fresh = false;
   uint64_t owned = 0;
+  uint32_t *csr_rows = nullptr;  // cc_run_csr: the row of each tile's first entry
+  uint64_t csr_rows_cap = 0;
   uint8_t *pk[2] = {nullptr, nullptr};  // cc_run_host_packed: packed chunk slots
   size_t pk_bytes = 0;                   // bytes of each slot
   cudaEvent_t pk_ev[2] = {nullptr, nullptr};  // a slot's last unpack has run
@@ -152,6 +154,7 @@ cc_status fetch_ctrl(cc_graph *g, cudaStream_t s) {
     CC_TRY(cudaMemsetAsync(&g->ctrl->err, 0, sizeof(uint32_t), s));
     CC_TRY(cudaStreamSynchronize(s));
     if (err & cc::kErrInternal) return CC_ERR_INTERNAL;
+    if (err & cc::kErrFormat) return CC_ERR_INVALID_ARGUMENT;
     if (err & cc::kErrTimeout) return CC_ERR_TIMEOUT;
     if (err & cc::kErrRange) return CC_ERR_OUT_OF_RANGE;
   }
@@ -355,6 +358,7 @@ void cc_destroy(cc_graph *g) {
   dev_free(g, g->label_dev, (size_t)g->n * 4);
   dev_free(g, g->z, g->z_bytes);
   dev_free(g, g->push, (size_t)g->push_cap * 4);
+  dev_free(g, g->csr_rows, (size_t)g->csr_rows_cap * 4);
   for (int i = 0; i < 2; ++i) {
     dev_free(g, g->pk[i], g->pk_bytes);
     if (g->pk_ev[i]) cudaEventDestroy(g->pk_ev[i]);
@@ -503,6 +507,50 @@ static cc_status run_host_impl(cc_graph *g, const void *edges_host, uint64_t n_e
     CC_TRY(cudaMemcpyAsync(L_out_host, g->label_dev, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
   g->ncomp_fresh = true;
   return fetch_ctrl(g, s);
+}
+
+cc_status cc_run_csr(cc_graph *g, const uint64_t *offsets_dev, const uint32_t *neighbors_dev, uint64_t n_entries,
+                     uint32_t *L_out_dev, cc_stream_t stream) {
+  if (!g) return CC_ERR_INVALID_ARGUMENT;
+  if (g->n && (!offsets_dev || !aligned(offsets_dev, 8))) return CC_ERR_INVALID_ARGUMENT;
+  if (n_entries && (!neighbors_dev || !aligned(neighbors_dev, 4))) return CC_ERR_INVALID_ARGUMENT;
+  if (L_out_dev && !aligned(L_out_dev, 4)) return CC_ERR_INVALID_ARGUMENT;
+  DeviceGuard dg(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  g->last = s;
+  if (g->n == 0) return CC_OK;
+  const uint32_t n = (uint32_t)g->n;
+  const uint64_t tiles = cc::csr_tiles(n_entries);
+  if (tiles > g->csr_rows_cap) {
+    CC_TRY(cudaStreamSynchronize(s));
+    dev_free(g, g->csr_rows, (size_t)g->csr_rows_cap * 4);
+    g->csr_rows = nullptr;
+    g->csr_rows_cap = 0;
+    CC_TRY(dev_alloc(g, (void **)&g->csr_rows, (size_t)tiles * 4));
+    g->csr_rows_cap = tiles;
+  }
+  begin_timed_run(g);
+  record(g, 0, s);
+  int m_src = cc::kMFromHint;
+  uint32_t hint = 0;
+  if (g->rf && g->opt.root_hint == CC_ROOT_AUTO) {
+    CC_TRY(cc::launch_csr_root_select(offsets_dev, n, n_entries, g->ctrl, s));
+    m_src = cc::kMFromPackedMax;
+  } else {
+    if (g->rf) hint = (uint32_t)g->opt.root_hint;
+    CC_TRY(cc::launch_csr_check(offsets_dev, n, n_entries, g->ctrl, s));
+  }
+  record(g, 1, s);
+  CC_TRY(cc::launch_init(g->rf, g->P, n, g->ctrl, m_src, hint, s));
+  if (g->z) CC_TRY(cudaMemsetAsync(g->z, 0, g->z_bytes, s));
+  g->z_auto_ok = false;
+  record(g, 2, s);
+  CC_TRY(cc::launch_edge_pass_csr(g->rf, offsets_dev, neighbors_dev, n_entries, n, g->csr_rows, g->P, g->ctrl, s));
+  record(g, 3, s);
+  CC_TRY(cc::launch_flatten(g->rf, g->opt.label_space, g->P, n, L_out_dev, g->ctrl, s));
+  record(g, 4, s);
+  g->ncomp_fresh = true;
+  return CC_OK;
 }
 
 cc_status cc_run_host(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges, uint32_t *L_out_host,

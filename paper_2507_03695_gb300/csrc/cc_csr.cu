@@ -1,0 +1,197 @@
+// cc_csr.cu - the edge pass and the root selection on CSR input
+// (cc_run_csr): offsets[n + 1] (64-bit) and neighbors[offsets[n]], the
+// in-memory layout of the paper's implementation (Section V). The edges are
+// (u, neighbors[j]) for offsets[u] <= j < offsets[u + 1]; direction does not
+// matter (Section II).
+//
+// What CSR changes on the GPU: every edge of row u shares the endpoint u, so
+// the lanes of a warp that hold entries of one row load P[u] in one
+// transaction, and a skewed graph pays about one random parent read per edge
+// instead of two. max_degree() of Algorithm 4 is read from the offsets (the
+// row length), as the paper does.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cc_device.cuh"
+#include "cc_internal.h"
+
+namespace cc {
+
+namespace {
+
+// 32-bit streaming load of a neighbour id: non-coherent path, no L1 allocation.
+__device__ __forceinline__ uint32_t ld_nc_u32(const uint32_t *a, uint64_t pol) {
+  uint32_t r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(a), "l"(pol));
+  return r;
+}
+
+// Row length of vertex v (0 when the offsets are not monotone there).
+__device__ __forceinline__ uint64_t row_len(const uint64_t *off, uint32_t v) {
+  const uint64_t a = off[v], b = off[v + 1];
+  return b > a ? b - a : 0u;
+}
+
+// Longest row, and a check of the offsets: off[0] == 0, off[n] == n_entries,
+// never decreasing (violations set kErrFormat).
+__global__ void __launch_bounds__(256) k_csr_maxlen(const uint64_t *__restrict__ off, uint32_t n,
+                                                    uint64_t n_entries, Ctrl *ctrl) {
+  unsigned long long best = 0;
+  bool bad = false;
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+       v += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = off[v], b = off[v + 1];
+    bad |= b < a;
+    const uint64_t len = b > a ? b - a : 0u;
+    best = len > best ? len : best;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) bad |= off[0] != 0u || off[n] != n_entries;
+  if (bad) set_err(ctrl, kErrFormat);
+  best = warp_max_u64(best);
+  if ((threadIdx.x & 31) == 0 && best) atomicMax(&ctrl->maxcnt, best);
+}
+
+// Smallest vertex with the longest row; then m for the init kernel.
+__global__ void __launch_bounds__(256) k_csr_minid(const uint64_t *__restrict__ off, uint32_t n, Ctrl *ctrl) {
+  const unsigned long long mx = *(volatile unsigned long long *)&ctrl->maxcnt;
+  uint32_t best = 0xFFFFFFFFu;
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+       v += (uint64_t)gridDim.x * blockDim.x)
+    if (row_len(off, (uint32_t)v) == mx && (uint32_t)v < best) best = (uint32_t)v;
+  best = __reduce_min_sync(0xFFFFFFFFu, best);
+  if ((threadIdx.x & 31) == 0 && best != 0xFFFFFFFFu) atomicMin(&ctrl->m_sel, best);
+}
+
+__global__ void k_csr_finalize_m(Ctrl *ctrl) { ctrl->maxkey = (unsigned long long)(uint32_t)~ctrl->m_sel; }
+
+// The row that holds entry t * tile: the largest r with off[r] <= t * tile
+// (one binary search per tile, all tiles in parallel).
+__global__ void __launch_bounds__(256) k_csr_tile_rows(const uint64_t *__restrict__ off, uint32_t n,
+                                                       uint64_t n_tiles, uint32_t tile, uint32_t *tile_row) {
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n_tiles;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t j = t * tile;
+    uint32_t lo = 0, hi = n;  // off[lo] <= j (off[0] = 0) ... answer in [lo, hi)
+    while (hi - lo > 1u) {
+      const uint32_t mid = lo + (hi - lo) / 2u;
+      if (off[mid] <= j)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    tile_row[t] = lo;
+  }
+}
+
+// The edge pass over CSR: warp-sized chunks of consecutive entries, the row
+// of each lane found by walking the offsets forward from the warp's current
+// row (bounded by n), the filter and the warp ring as in the COO pass.
+template <class F>
+__global__ void __launch_bounds__(512) k_edge_pass_csr(const uint64_t *__restrict__ off,
+                                                       const uint32_t *__restrict__ nb, uint64_t n_entries,
+                                                       uint32_t n, uint32_t tile, const uint32_t *tile_row,
+                                                       uint32_t *P, Ctrl *ctrl) {
+  extern __shared__ uint32_t ring_smem[];
+  const F fn = F::load(ctrl);
+  uint32_t *const S = slots<F>(P);
+  const uint64_t pol = policy_evict_first();
+  WarpRing ring;
+  ring.init(ring_smem);
+  const uint64_t n_tiles = (n_entries + tile - 1) / tile;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t t = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < n_tiles; t += warps) {
+    uint32_t r = tile_row[t];  // warp-uniform: the row of the tile's first entry
+    const uint64_t end = (t + 1) * tile < n_entries ? (t + 1) * tile : n_entries;
+    for (uint64_t base = t * tile; base < end; base += 32u) {
+      const uint64_t j = base + ring.lane;
+      const bool live = j < end;
+      // The row of entry j: lane k holds the boundary off[r + 1 + k], and each
+      // lane counts, by a binary search over the 32 boundaries in registers,
+      // the rows that end at or before its entry.
+      const uint64_t bnd = r + 1u + ring.lane <= n ? off[r + 1u + ring.lane] : ~0ull;
+      uint32_t lo = 0, hi = 32;  // answer in [0, 32]: six halvings settle it
+      const uint64_t last_j = (end - base < 32u ? end : base + 32u) - 1u;
+      if (__shfl_sync(0xFFFFFFFFu, bnd, 0) <= last_j) {  // else the whole chunk lies in row r
+#pragma unroll
+        for (int step = 0; step < 6; ++step) {
+          const uint32_t mid = (lo + hi) >> 1;
+          const uint64_t b = __shfl_sync(0xFFFFFFFFu, bnd, (int)(mid < 32u ? mid : 31u));
+          if (live && mid < 32u && b <= j)
+            lo = mid + 1u;
+          else
+            hi = mid;
+        }
+      }
+      uint32_t u = r + lo < n ? r + lo : n - 1u;
+      uint32_t v = 0;
+      if (live) {
+        // more than 32 rows (empty ones) end inside this chunk: walk on
+        while (u + 1u < n && off[u + 1] <= j) ++u;
+        v = ld_nc_u32(nb + j, pol);
+        if (v >= n) {
+          set_err(ctrl, kErrRange);
+          v = u;  // a self-loop: no effect
+        }
+      }
+      const uint32_t pu = live ? ldP(P + u) : 0u;
+      const uint32_t pv = live ? ldP(P + v) : 0u;
+      ring.push(S, live && pu != pv, fn.f(u), pu, fn.f(v), pv);
+      // the next chunk starts in the row of this chunk's last entry
+      const int last = (int)((end - base < 32u ? end - base : 32u) - 1u);
+      r = __shfl_sync(0xFFFFFFFFu, u, last);
+    }
+  }
+  ring.drain(S);
+}
+
+}  // namespace
+
+constexpr uint32_t kCsrTile = 1024;
+
+uint64_t csr_tiles(uint64_t n_entries) { return (n_entries + kCsrTile - 1) / kCsrTile; }
+
+cudaError_t launch_csr_root_select(const uint64_t *off, uint32_t n, uint64_t n_entries, Ctrl *ctrl, cudaStream_t s) {
+  cudaError_t err;
+  if ((err = cudaMemsetAsync(&ctrl->maxcnt, 0, sizeof(unsigned long long), s)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(&ctrl->m_sel, 0xFF, sizeof(uint32_t), s)) != cudaSuccess) return err;
+  const unsigned g = clamp_grid(((uint64_t)n + 255) / 256, persistent_cap((const void *)k_csr_maxlen, 256, 0));
+  k_csr_maxlen<<<g, 256, 0, s>>>(off, n, n_entries, ctrl);
+  note_launch();
+  k_csr_minid<<<g, 256, 0, s>>>(off, n, ctrl);
+  note_launch();
+  k_csr_finalize_m<<<1, 1, 0, s>>>(ctrl);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_csr_check(const uint64_t *off, uint32_t n, uint64_t n_entries, Ctrl *ctrl, cudaStream_t s) {
+  // the offsets check alone (the longest row goes to maxcnt, unused)
+  const unsigned g = clamp_grid(((uint64_t)n + 255) / 256, persistent_cap((const void *)k_csr_maxlen, 256, 0));
+  k_csr_maxlen<<<g, 256, 0, s>>>(off, n, n_entries, ctrl);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_edge_pass_csr(bool rf, const uint64_t *off, const uint32_t *nb, uint64_t n_entries, uint32_t n,
+                                 uint32_t *tile_row, uint32_t *P, Ctrl *ctrl, cudaStream_t s) {
+  if (n_entries == 0 || n == 0) return cudaSuccess;
+  const uint64_t n_tiles = csr_tiles(n_entries);
+  const unsigned gt = clamp_grid((n_tiles + 255) / 256, persistent_cap((const void *)k_csr_tile_rows, 256, 0));
+  k_csr_tile_rows<<<gt, 256, 0, s>>>(off, n, n_tiles, kCsrTile, tile_row);
+  note_launch();
+  const int block = 256;
+  const size_t smem = (size_t)(block / 32) * 4 * kRing * sizeof(uint32_t);
+  // at least eight tiles per warp (as the COO pass keeps eight waves)
+  const uint64_t want = (n_tiles + (block / 32) * 8 - 1) / ((block / 32) * 8);
+  if (rf) {
+    const unsigned g = clamp_grid(want, persistent_cap((const void *)k_edge_pass_csr<RootR>, block, smem));
+    k_edge_pass_csr<RootR><<<g, block, smem, s>>>(off, nb, n_entries, n, kCsrTile, tile_row, P, ctrl);
+  } else {
+    const unsigned g = clamp_grid(want, persistent_cap((const void *)k_edge_pass_csr<RootId>, block, smem));
+    k_edge_pass_csr<RootId><<<g, block, smem, s>>>(off, nb, n_entries, n, kCsrTile, tile_row, P, ctrl);
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace cc

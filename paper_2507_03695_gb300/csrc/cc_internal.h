@@ -15,6 +15,7 @@ enum : uint32_t {
   kErrRange = 1u,     // a vertex id >= n reached a kernel
   kErrTimeout = 2u,   // a bounded wait expired
   kErrInternal = 4u,  // an invariant failed (a root search longer than n)
+  kErrFormat = 8u,    // malformed input structure (CSR offsets)
 };
 
 // Where the init kernel takes the planted vertex m from.
@@ -150,6 +151,14 @@ cudaError_t launch_initial_push(uint32_t *P, uint32_t n, const uint32_t *push_bu
                                 const CertScratch *cs, const Ctrl *ctrl, cudaStream_t s);
 
 cudaError_t launch_degree_u32(const EdgeSpan &e, uint32_t *cnt, uint32_t n, cudaStream_t s);
+// CSR input (cc_csr.cu): offsets[n + 1], neighbors[n_entries].
+uint64_t csr_tiles(uint64_t n_entries);  // entries of tile_row needed
+// m = the longest row, smallest id on ties (into ctrl->maxkey); also checks
+// the offsets (kErrFormat).
+cudaError_t launch_csr_root_select(const uint64_t *off, uint32_t n, uint64_t n_entries, Ctrl *ctrl, cudaStream_t s);
+cudaError_t launch_csr_check(const uint64_t *off, uint32_t n, uint64_t n_entries, Ctrl *ctrl, cudaStream_t s);
+cudaError_t launch_edge_pass_csr(bool rf, const uint64_t *off, const uint32_t *nb, uint64_t n_entries, uint32_t n,
+                                 uint32_t *tile_row, uint32_t *P, Ctrl *ctrl, cudaStream_t s);
 // Unpacks n_edges edges of 3-byte ids (cc_pack.cu; src 16-byte aligned) into
 // uint32 pairs at dst (16-byte aligned).
 cudaError_t launch_unpack3(const uint8_t *src, uint64_t n_edges, uint32_t *dst, cudaStream_t s);

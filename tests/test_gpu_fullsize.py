@@ -129,3 +129,25 @@ def test_fullsize_rmat28_against_oracle_values():
         g.run(e, L)
         g.sync()
         assert sha_chunked(L) == gold["labels_root_value_sha256"]
+
+
+def test_fullsize_csr_rmat24_equals_coo_labels():
+    """The CSR of R-MAT scale 24 (rows sorted by source, built on the device)
+    stands for the same edges, so its min-id labels equal the stored COO
+    values, whatever vertex the longest row plants."""
+    with open(os.path.join(GOLDEN, "rmat24_ef16.json")) as f:
+        gold = json.load(f)
+    w = graphgen.WORKLOADS["rmat24_ef16"]
+    n = w.n_vertices
+    e = w.device_edges()
+    off, nb = bench.device_csr(e, n)
+    del e
+    L = torch.empty(n, dtype=torch.int32, device="cuda")
+    with cc.Graph(n, **bench.BENCH_OPTIONS) as g:
+        cc.cc_run_csr(g.h, off, nb, nb.shape[0], L)
+        g.sync()
+        assert sha_tensor(L) == gold["labels_min_id_sha256"]
+        assert g.num_components() == gold["num_components"]
+        lens = (off[1:] - off[:-1])
+        assert g.root_vertex() == int(torch.argmax(lens).item())  # first index of the maximum
+

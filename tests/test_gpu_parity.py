@@ -431,6 +431,76 @@ def test_run_host_packed(mode, select):
             cc.cc_run_host_packed(g.h, ps, 10, 3, None)
 
 
+def _csr_dev(off, nb):
+    return (torch.from_numpy(off.astype(np.int64)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(nb, dtype=np.uint32).view(np.int32)).cuda())
+
+
+def _csr_case(case):
+    if case == "rmat16":
+        w = graphgen.RMAT16
+        return w.n_vertices, w.host_edges()
+    if case == "rmat20":
+        return 1 << 20, graphgen.rmat(20, 1 << 23, 75, scramble=True)
+    if case == "grid":
+        return 512 * 512, graphgen.grid(512, 512, 3)
+    if case == "sparse":  # mostly empty rows, a few long ones
+        rng = np.random.default_rng(76)
+        e = rng.integers(0, 50000, size=(20000, 2)).astype(np.uint32)
+        e[:3000, 0] = 7
+        return 50000, e
+    return 1000, np.zeros((0, 2), np.uint32)  # no edges
+
+
+@pytest.mark.parametrize("case", ["rmat16", "rmat20", "grid", "sparse", "empty"])
+@pytest.mark.parametrize("mode", [cc.CC_ROOT_MAXDEG, cc.CC_ROOT_IDENTITY])
+def test_csr_path(case, mode):
+    n, e = _csr_case(case)
+    off, nb = graphgen.to_csr(n, e)
+    pairs = oracle.csr_edges(off, nb)
+    want = oracle.min_labels(n, pairs)
+    d_off, d_nb = _csr_dev(off, nb)
+    for label_space in (cc.CC_LABEL_MIN_ID, cc.CC_LABEL_ROOT_VALUE):
+        with cc.Graph(n, mode=mode, label_space=label_space) as g:
+            L = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+            for _ in range(2):
+                cc.cc_run_csr(g.h, d_off, d_nb, len(nb), L)
+                g.sync()
+                got = L.cpu().numpy().view(np.uint32)
+                if mode == cc.CC_ROOT_MAXDEG:
+                    m = oracle.csr_max_row_vertex(n, off)
+                    assert g.root_vertex() == m
+                    ref = want if label_space == cc.CC_LABEL_MIN_ID else oracle.root_value_labels(n, pairs, m)
+                else:
+                    ref = want
+                np.testing.assert_array_equal(got, ref)
+                assert g.num_components() == oracle.num_components(want)
+
+
+def test_csr_errors():
+    n = 100
+    off, nb = graphgen.to_csr(n, np.array([[1, 2], [3, 4], [5, 6]], np.uint32))
+    bad_nb = nb.copy()
+    bad_nb[1] = n
+    d_off, d_nb = _csr_dev(off, bad_nb)
+    with cc.Graph(n) as g:
+        cc.cc_run_csr(g.h, d_off, d_nb, len(nb), None)
+        assert cc.cc_sync_status(g.h) == cc.CC_ERR_OUT_OF_RANGE
+    start = off.astype(np.int64).copy()
+    start[0] = 1  # offsets[0] != 0
+    dec = off.astype(np.int64).copy()
+    dec[5] = dec[6] + 1  # decreasing
+    for bad_off in (start, dec):
+        d_off, d_nb = _csr_dev(bad_off.astype(np.uint64), nb)
+        with cc.Graph(n) as g:
+            cc.cc_run_csr(g.h, d_off, d_nb, len(nb), None)
+            assert cc.cc_sync_status(g.h) == cc.CC_ERR_INVALID_ARGUMENT
+    d_off, d_nb = _csr_dev(off, nb)
+    with cc.Graph(n, mode=cc.CC_ROOT_IDENTITY) as g:
+        cc.cc_run_csr(g.h, d_off, d_nb, len(nb) + 1, None)  # n_entries != off[n]
+        assert cc.cc_sync_status(g.h) == cc.CC_ERR_INVALID_ARGUMENT
+
+
 def test_phase_times_and_budget():
     n = 1 << 16
     e = graphgen.rmat(16, 1 << 20, 1, scramble=False)

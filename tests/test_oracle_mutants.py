@@ -28,6 +28,9 @@ MUTANTS = {
                                   "      P[u] = (uint32_t)f_of(use_r, m, v);\n    else\n      P[v] = (uint32_t)f_of(use_r, m, u);"),
     "rfjt_inverse_off_by_one": ("return c == 0 ? m : c - 1; /* Eq. 2 */", "return c == 0 ? m : c; /* Eq. 2 */"),
     "pointer_jump_keeps_parent": ("    P[v] = P[u];\n  }", "    P[v] = P[v];\n  }"),
+    "csr_row_tie_to_larger": ("if (len > best_len) {", "if (len >= best_len) {"),
+    "csr_row_len_dropped_term": ("const uint64_t len = offsets[v + 1] - offsets[v];",
+                                 "const uint64_t len = offsets[v + 1];"),
 }
 
 
@@ -47,6 +50,8 @@ def _load(so):
     lib.oracle_root_value_labels.argtypes = [u64, p, u64, u64, p]
     lib.oracle_max_degree_vertex.argtypes = [u64, p, u64, p]
     lib.oracle_max_degree_vertex.restype = ctypes.c_int64
+    lib.oracle_csr_max_row_vertex.argtypes = [u64, p]
+    lib.oracle_csr_max_row_vertex.restype = ctypes.c_int64
     lib.oracle_rfjt_init.argtypes = [u64, i32, u64, p]
     lib.oracle_rfjt_hook.argtypes = [u64, i32, u64, p, u64, p]
     lib.oracle_rfjt_pointer_jump.argtypes = [u64, i32, u64, p]
@@ -77,6 +82,21 @@ def _pins_pass(lib) -> bool:
     # the tie rule of the degree argmax
     e = np.array([[1, 1], [2, 3], [2, 4], [0, 5]], np.uint32)
     if lib.oracle_max_degree_vertex(6, e.ctypes.data, len(e), None) != 1:
+        return False
+    # CSR rows: on a symmetric graph without self-loops the longest row is
+    # the vertex of largest degree (same tie rule); ties and empty rows
+    for trial in range(20):
+        k = int(rng.integers(1, 12))
+        e = rng.integers(0, 8, size=(k, 2)).astype(np.uint32)
+        e = e[e[:, 0] != e[:, 1]]
+        sym = np.concatenate([e, e[:, ::-1]]).astype(np.uint32)
+        off = np.zeros(9, np.uint64)
+        np.cumsum(np.bincount(sym[:, 0], minlength=8), out=off[1:])
+        want = lib.oracle_max_degree_vertex(8, np.ascontiguousarray(e).ctypes.data, len(e), None) if len(e) else 0
+        if lib.oracle_csr_max_row_vertex(8, off.ctypes.data) != want:
+            return False
+    off = np.array([0, 0, 2, 2, 4, 5], np.uint64)  # rows 1 and 3 tie at 2
+    if lib.oracle_csr_max_row_vertex(5, off.ctypes.data) != 1:
         return False
     # sequential Algorithm 3, both root functions, every order of small cases
     for trial in range(6):

@@ -217,3 +217,30 @@ def test_out_of_range_rejected():
         oracle.min_labels(4, np.array([[0, 4]], np.uint32))
     with pytest.raises(ValueError):
         oracle.bfs_labels(4, np.array([[5, 1]], np.uint32))
+
+
+def test_csr_max_row_vertex_pins():
+    """CSR input reads max_degree() from the offsets (Algorithm 4): on a
+    symmetric graph without self-loops every undirected edge appears in both
+    rows, so the longest row is the COO maximum-degree vertex (ties to the
+    smaller id in both); closed forms for a star, ties and empty rows."""
+    rng = np.random.default_rng(17)
+    for trial in range(200):
+        n = int(rng.integers(1, 40))
+        e = rng.integers(0, n, size=(int(rng.integers(0, 120)), 2)).astype(np.uint32)
+        e = e[e[:, 0] != e[:, 1]]
+        sym = np.concatenate([e, e[:, ::-1]])
+        off, nb = graphgen.to_csr(n, sym)
+        want = oracle.max_degree_vertex(n, e) if len(e) else 0
+        assert oracle.csr_max_row_vertex(n, off) == want
+        # the CSR stands for the same pairs
+        back = oracle.csr_edges(off, nb)
+        assert sorted(map(tuple, back.tolist())) == sorted(map(tuple, sym.tolist()))
+    star = np.array([[5, k] for k in range(10) if k != 5], np.uint32)
+    off, _ = graphgen.to_csr(10, np.concatenate([star, star[:, ::-1]]))
+    assert oracle.csr_max_row_vertex(10, off) == 5
+    assert oracle.csr_max_row_vertex(4, np.array([0, 0, 0, 0, 0], np.uint64)) == 0  # no edges
+    assert oracle.csr_max_row_vertex(5, np.array([0, 0, 3, 3, 6, 7], np.uint64)) == 1  # rows 1 and 3 tie
+    with pytest.raises(Exception):
+        oracle.csr_max_row_vertex(3, np.array([0, 2, 1, 3], np.uint64))  # decreasing
+
