@@ -166,13 +166,21 @@ __device__ __forceinline__ uint32_t root_name(uint32_t *S, uint32_t c, uint32_t 
 // parent, and the search resumes from that root (the current roots, not the
 // original endpoints). Any moment at which both sides show the same parent
 // name proves a common tree and ends the edge, which includes the case of
-// both endpoints already holding 0. Returns true when the edge is known to
-// end in the tree of name 0 (both endpoints then belong to it for good).
+// both endpoints already holding 0. Reports whether the edge is known to end
+// in the tree of name 0 (both endpoints then belong to it for good), and the
+// name of the root this edge's CAS hooked, if any (the pairs SiskinCC sends on
+// a successful CAS, Algorithm 2).
+struct UniteResult {
+  bool zero;        // ended in the tree of name 0
+  uint32_t hooked;  // the root hooked by this edge, or kNoHook
+};
+constexpr uint32_t kNoHook = 0xFFFFFFFFu;
+
 template <bool kCG = false>
-__device__ __forceinline__ bool unite(uint32_t *S, uint32_t cu, uint32_t pu, uint32_t cv, uint32_t pv) {
+__device__ __forceinline__ UniteResult unite(uint32_t *S, uint32_t cu, uint32_t pu, uint32_t cv, uint32_t pv) {
   if (pu != pv) CC_STAT(0);
   while (true) {
-    if (pu == pv) return pu == 0u;
+    if (pu == pv) return {pu == 0u, kNoHook};
     while (pu != cu) {
       if (pu == 0u) {
         cu = 0u;
@@ -183,7 +191,7 @@ __device__ __forceinline__ bool unite(uint32_t *S, uint32_t cu, uint32_t pu, uin
       if (pw != pu) stP(S + cu, pw);
       cu = pu;
       pu = pw;
-      if (pu == pv) return pu == 0u;
+      if (pu == pv) return {pu == 0u, kNoHook};
     }
     while (pv != cv) {
       if (pv == 0u) {
@@ -195,17 +203,17 @@ __device__ __forceinline__ bool unite(uint32_t *S, uint32_t cu, uint32_t pu, uin
       if (pw != pv) stP(S + cv, pw);
       cv = pv;
       pv = pw;
-      if (pu == pv) return pu == 0u;
+      if (pu == pv) return {pu == 0u, kNoHook};
     }
-    if (pu == pv) return pu == 0u;  // same root
+    if (pu == pv) return {pu == 0u, kNoHook};  // same root
     CC_STAT(2);
     if (pu < pv) {
       const uint32_t old = atomicCAS(S + cv, pv, pu);
-      if (old == pv) return pu == 0u;
+      if (old == pv) return {pu == 0u, cv};
       pv = old;  // that root was hooked meanwhile: continue from it
     } else {
       const uint32_t old = atomicCAS(S + cu, pu, pv);
-      if (old == pu) return pv == 0u;
+      if (old == pu) return {pv == 0u, cu};
       pu = old;
     }
     CC_STAT(3);
@@ -238,15 +246,36 @@ __device__ __forceinline__ bool zbit(const uint32_t *Z, uint32_t c) {
 
 __device__ __forceinline__ void zset(uint32_t *Z, uint32_t c) { atomicOr(Z + (c >> 5), 1u << (c & 31u)); }
 
+// A changed-root log: log[0] counts the entries that follow it, the names of
+// the roots hooked since the log was last cleared. Its capacity (one entry
+// per vertex) cannot be exceeded: a root is hooked once.
+__device__ __forceinline__ void log_hook(uint32_t *log, uint32_t hooked) {
+  const uint32_t i = atomicAdd(log, 1u);
+  log[1u + i] = hooked;
+}
+
+// The same for a whole warp (every lane calls it): one atomic per warp.
+__device__ __forceinline__ void log_hooks_warp(uint32_t *log, uint32_t hooked, uint32_t lane, uint32_t lt_mask) {
+  const uint32_t bal = __ballot_sync(0xFFFFFFFFu, hooked != kNoHook);
+  if (!bal) return;
+  uint32_t base = 0;
+  if (lane == 0) base = atomicAdd(log, (uint32_t)__popc(bal));
+  base = __shfl_sync(0xFFFFFFFFu, base, 0);
+  if (hooked != kNoHook) log[1u + base + (uint32_t)__popc(bal & lt_mask)] = hooked;
+}
+
 struct WarpRing {
   uint32_t *cu, *pu, *cv, *pv;
-  uint32_t *Z;  // zero-tree bitmap, or null
+  uint32_t *Z;    // zero-tree bitmap, or null
+  uint32_t *log;  // changed-root log, or null
   uint32_t head, tail;
   uint32_t lane, lt_mask;
 
   // ring storage for this warp out of 4 * kRing words per warp
-  __device__ __forceinline__ void init(uint32_t *smem_words, uint32_t *zero_tree = nullptr) {
+  __device__ __forceinline__ void init(uint32_t *smem_words, uint32_t *zero_tree = nullptr,
+                                       uint32_t *root_log = nullptr) {
     Z = zero_tree;
+    log = root_log;
     const uint32_t wid = threadIdx.x >> 5;
     cu = smem_words + wid * (4 * kRing);
     pu = cu + kRing;
@@ -274,10 +303,12 @@ struct WarpRing {
       const uint32_t slot = (head + lane) & (kRing - 1);
       const uint32_t sa = cu[slot], spa = pu[slot], sb = cv[slot], spb = pv[slot];
       __syncwarp();
-      if (unite<kCG>(S, sa, spa, sb, spb) && Z) {
+      const UniteResult res = unite<kCG>(S, sa, spa, sb, spb);
+      if (res.zero && Z) {
         zset(Z, sa);
         zset(Z, sb);
       }
+      if (log) log_hooks_warp(log, res.hooked, lane, lt_mask);
       head += 32u;
     }
   }
@@ -285,14 +316,18 @@ struct WarpRing {
   template <bool kCG = false>
   __device__ __forceinline__ void drain(uint32_t *S) {
     __syncwarp();
+    uint32_t hooked = kNoHook;
     if (lane < tail - head) {
       const uint32_t slot = (head + lane) & (kRing - 1);
       const uint32_t a = cu[slot], b = cv[slot];
-      if (unite<kCG>(S, a, pu[slot], b, pv[slot]) && Z) {
+      const UniteResult res = unite<kCG>(S, a, pu[slot], b, pv[slot]);
+      if (res.zero && Z) {
         zset(Z, a);
         zset(Z, b);
       }
+      hooked = res.hooked;
     }
+    if (log) log_hooks_warp(log, hooked, lane, lt_mask);
     head = tail;
     __syncwarp();
   }

@@ -170,13 +170,18 @@ cudaError_t launch_argmax_u32(const uint32_t *cnt, uint32_t n, Ctrl *ctrl, cudaS
 // picks the zero-tree instance when *zsel is nonzero, the plain one otherwise.
 // one_shot: short-lived blocks (a few grid iterations each) instead of a
 // persistent grid (for work that shares the GPU with a resident kernel).
+// log: a changed-root log (log[0] = entries, then the hooked root names), or
+// null.
 cudaError_t launch_edge_pass(bool rf, int filter, int ept, int block, const EdgeSpan &e, uint32_t *P,
                              uint32_t n, Ctrl *ctrl, const uint32_t *skip, cudaStream_t s,
-                             uint32_t *Z = nullptr, const uint32_t *zsel = nullptr, bool one_shot = false);
+                             uint32_t *Z = nullptr, const uint32_t *zsel = nullptr, bool one_shot = false,
+                             uint32_t *log = nullptr);
 // Sets *reject (ctrl->reject when null) and the range error bit when an id is >= n.
 cudaError_t launch_validate(const EdgeSpan &e, uint32_t n, Ctrl *ctrl, cudaStream_t s, uint32_t *reject = nullptr);
 cudaError_t launch_flatten(bool rf, int label_space, uint32_t *P, uint32_t n, uint32_t *L, Ctrl *ctrl,
                            cudaStream_t s);
+// Under R: the smallest vertex of m's tree into ctrl->gmin (which must hold m).
+cudaError_t launch_gmin_probe(uint32_t *P, uint32_t n, Ctrl *ctrl, cudaStream_t s);
 cudaError_t launch_count_roots(bool rf, const uint32_t *P, uint32_t n, Ctrl *ctrl, cudaStream_t s);
 cudaError_t launch_connected(bool rf, uint32_t *P, uint32_t n, const uint2 *pairs, uint64_t n_pairs,
                              uint8_t *out, Ctrl *ctrl, cudaStream_t s);

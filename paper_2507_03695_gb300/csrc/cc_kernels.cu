@@ -80,10 +80,11 @@ __device__ __forceinline__ void guard(uint32_t &a, uint32_t &b, uint32_t n, Ctrl
 
 template <class F>
 __device__ __forceinline__ void single_edge(uint32_t *P, const F fn, const uint2 *e, uint32_t n,
-                                            Ctrl *ctrl) {
+                                            Ctrl *ctrl, uint32_t *log = nullptr) {
   uint2 x = ld_edge(e);
   guard(x.x, x.y, n, ctrl);
-  unite(slots<F>(P), fn.f(x.x), ldP(P + x.x), fn.f(x.y), ldP(P + x.y));
+  const UniteResult r = unite(slots<F>(P), fn.f(x.x), ldP(P + x.x), fn.f(x.y), ldP(P + x.y));
+  if (log && r.hooked != kNoHook) log_hook(log, r.hooked);
 }
 
 // Direct form: each thread takes Q 128-bit loads (2Q edges) per iteration,
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(512) k_edge_pass_filtered(const uint4 *__restr
                                                             const uint2 *tail, uint32_t *P,
                                                             uint32_t n, Ctrl *ctrl,
                                                             const uint32_t *skip, uint32_t *Z,
-                                                            const uint32_t *zsel) {
+                                                            const uint32_t *zsel, uint32_t *log) {
   extern __shared__ uint32_t ring_smem[];
   if (skip && ld_volatile_u32(skip)) return;
   if (zsel && ((ld_volatile_u32(zsel) != 0u) != kZ)) return;
@@ -155,11 +156,11 @@ __global__ void __launch_bounds__(512) k_edge_pass_filtered(const uint4 *__restr
   uint32_t *const S = slots<F>(P);
   const uint64_t pol = policy_evict_first();
   WarpRing ring;
-  ring.init(ring_smem, kZ ? Z : nullptr);
+  ring.init(ring_smem, kZ ? Z : nullptr, log);
   const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (t == 0 && head) single_edge(P, fn, head, n, ctrl);
-  if (t == 1 % T && tail) single_edge(P, fn, tail, n, ctrl);
+  if (t == 0 && head) single_edge(P, fn, head, n, ctrl, log);
+  if (t == 1 % T && tail) single_edge(P, fn, tail, n, ctrl, log);
   // the loop trip count must be warp-uniform: iterate on the warp's first lane
   const uint64_t warp_t0 = t - (uint64_t)ring.lane;
   for (uint64_t wbase = warp_t0; wbase < n_quads; wbase += T * Q) {
@@ -525,7 +526,8 @@ constexpr uint64_t kMinWaves = 8;
 
 template <class F, int Q>
 cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, uint32_t n, Ctrl *ctrl,
-                        const uint32_t *skip, uint32_t *Z, const uint32_t *zsel, bool one_shot, cudaStream_t s) {
+                        const uint32_t *skip, uint32_t *Z, const uint32_t *zsel, bool one_shot, uint32_t *log,
+                        cudaStream_t s) {
   const uint64_t per_block = (uint64_t)block * Q;
   // At least kMinWaves grid iterations per thread: when a whole graph fits
   // one wave, every edge reads P before any hooking and duplicate hub edges
@@ -542,12 +544,12 @@ cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, u
     if (Z) {  // the zero-tree instance (alone, or chosen on the device by *zsel)
       const unsigned g = clamp_grid(want, one_shot ? cap_big : persistent_cap((const void *)k_edge_pass_filtered<F, Q, true>, block, smem));
       k_edge_pass_filtered<F, Q, true><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
-                                                              skip, Z, zsel); note_launch();
+                                                              skip, Z, zsel, log); note_launch();
     }
     if (!Z || zsel) {
       const unsigned g = clamp_grid(want, one_shot ? cap_big : persistent_cap((const void *)k_edge_pass_filtered<F, Q, false>, block, smem));
       k_edge_pass_filtered<F, Q, false><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
-                                                               skip, nullptr, Z ? zsel : nullptr); note_launch();
+                                                               skip, nullptr, Z ? zsel : nullptr, log); note_launch();
     }
   } else {
     const void *k = (const void *)k_edge_pass_direct<F, Q>;
@@ -561,28 +563,38 @@ cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, u
 template <class F>
 cudaError_t edge_pass_f(int filter, int ept, int block, const EdgeSpan &e, uint32_t *P, uint32_t n,
                         Ctrl *ctrl, const uint32_t *skip, uint32_t *Z, const uint32_t *zsel, bool one_shot,
-                        cudaStream_t s) {
+                        uint32_t *log, cudaStream_t s) {
   switch (ept) {
-    case 2: return edge_pass_q<F, 1>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, s);
-    case 8: return edge_pass_q<F, 4>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, s);
-    default: return edge_pass_q<F, 2>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, s);
+    case 2: return edge_pass_q<F, 1>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, s);
+    case 8: return edge_pass_q<F, 4>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, s);
+    default: return edge_pass_q<F, 2>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, s);
   }
 }
 }  // namespace
 
 cudaError_t launch_edge_pass(bool rf, int filter, int ept, int block, const EdgeSpan &e, uint32_t *P,
                              uint32_t n, Ctrl *ctrl, const uint32_t *skip, cudaStream_t s, uint32_t *Z,
-                             const uint32_t *zsel, bool one_shot) {
+                             const uint32_t *zsel, bool one_shot, uint32_t *log) {
   if (block != 128 && block != 256 && block != 512) block = 256;
   if (e.n_quads == 0 && !e.head && !e.tail) return cudaSuccess;
-  return rf ? edge_pass_f<RootR>(filter, ept, block, e, P, n, ctrl, skip, Z, zsel, one_shot, s)
-            : edge_pass_f<RootId>(filter, ept, block, e, P, n, ctrl, skip, Z, zsel, one_shot, s);
+  if (log) filter = 1;  // the log is kept by the filtered form
+  return rf ? edge_pass_f<RootR>(filter, ept, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, s)
+            : edge_pass_f<RootId>(filter, ept, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, s);
 }
 
 cudaError_t launch_validate(const EdgeSpan &e, uint32_t n, Ctrl *ctrl, cudaStream_t s, uint32_t *reject) {
   if (e.n_quads == 0 && !e.head && !e.tail) return cudaSuccess;
   const unsigned g = clamp_grid((e.n_quads + 255) / 256, persistent_cap((const void *)k_validate, 256, 0));
   k_validate<<<g, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, n, ctrl, reject ? reject : &ctrl->reject);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gmin_probe(uint32_t *P, uint32_t n, Ctrl *ctrl, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const uint64_t want = ((uint64_t)n + 255) / 256;
+  const unsigned gp = clamp_grid(want / 4 + 1, persistent_cap((const void *)k_gmin_probe, 256, 0));
+  k_gmin_probe<<<gp, 256, 0, s>>>(P, n, ctrl);
   note_launch();
   return cudaGetLastError();
 }

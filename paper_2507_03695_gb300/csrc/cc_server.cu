@@ -61,7 +61,7 @@ struct alignas(16) WorkItem {
   uint32_t kind, slot, seq, n_tiles;  // n_tiles: tiles that count towards completion
   uint32_t rf, m, n, n_gate;          // n_gate: validate tiles an apply tile waits for
   uint64_t P, src, begin, end, out;
-  uint64_t pad2;
+  uint64_t log;  // the graph's changed-root log (inserts append the roots they hook)
 };
 static_assert(sizeof(WorkItem) == 80, "work item layout");
 
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(256) k_executor(HostShared *hs, DevShared *ds)
     __syncthreads();
     if ((it.kind == kItemEdges && !s_bad) || (it.kind == kItemApply && !s_skip)) {
       WarpRing ring;
-      ring.init(ring_smem);
+      ring.init(ring_smem, nullptr, reinterpret_cast<uint32_t *>(it.log));
       // warp-uniform rounds of kEpt edges per thread, all parent loads issued together
       for (uint64_t r0 = it.begin; r0 < it.end; r0 += (uint64_t)blockDim.x * kEpt) {
         uint32_t a[kEpt], b[kEpt], pa[kEpt], pb[kEpt];
@@ -313,6 +313,68 @@ __global__ void k_srv_prep_flatten(Ctrl *ctrl) {
   ctrl->ncomp = 0ULL;
 }
 
+// ------------------------------------------------ incremental snapshots
+//
+// Each resident graph keeps the labels of its last snapshot (Llast) and the
+// changed-root log of the inserts since (SiskinCC's pairs sent on a
+// successful CAS, Algorithm 2, reused as a log). A root hooked since the last
+// snapshot was a root then, so the label its component had is the label of
+// that root; every other component kept its label, except that under R the
+// smallest vertex of m's tree (gmin) may have dropped. The next snapshot
+// therefore maps each changed label to the label of the logged root's
+// current root and rewrites Llast in one streaming pass, with no parent walk
+// per vertex.
+
+// Label of the root named c in the server's label space.
+__device__ __forceinline__ uint32_t root_label(uint32_t c, uint32_t rf, uint32_t min_id, uint32_t gmin) {
+  if (!rf || !min_id) return c;  // identity: names are ids; root-value labels are names
+  return c == 0u ? gmin : c - 1u;
+}
+
+// words[0]: gmin of the last snapshot. chg: one bit per label that changed;
+// rem[l]: the new label of a changed label l.
+__global__ void __launch_bounds__(256) k_srv_inc_remap(uint32_t *P, uint32_t rf, uint32_t min_id,
+                                                       const uint32_t *log, uint32_t *rem, uint32_t *chg,
+                                                       const uint32_t *words, const Ctrl *ctrl) {
+  uint32_t *const S = P - rf;
+  const uint32_t gmin = *(const volatile uint32_t *)&ctrl->gmin;
+  const uint32_t count = *(const volatile uint32_t *)log;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    const uint32_t r = log[1u + i];
+    const uint32_t root = root_name(S, r, ldP_strong(S + r));
+    const uint32_t old = root_label(r, rf, min_id, gmin);
+    rem[old] = root_label(root, rf, min_id, gmin);
+    atomicOr(chg + (old >> 5), 1u << (old & 31u));
+  }
+  if (rf && min_id && blockIdx.x == 0 && threadIdx.x == 0) {
+    const uint32_t g0 = words[0];
+    if (g0 != gmin) {  // m's tree took in a smaller vertex
+      rem[g0] = gmin;
+      atomicOr(chg + (g0 >> 5), 1u << (g0 & 31u));
+    }
+  }
+}
+
+// L[v] = the new label of Llast[v]; Llast takes the changes. After it: the
+// log is emptied, words[0] = gmin (the bitmap is cleared by the host).
+__global__ void __launch_bounds__(256) k_srv_inc_relabel(uint32_t *Llast, uint32_t n, const uint32_t *rem,
+                                                         const uint32_t *chg, uint32_t *L) {
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+       v += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t l = Llast[v];
+    if ((chg[l >> 5] >> (l & 31u)) & 1u) {
+      l = rem[l];
+      Llast[v] = l;
+    }
+    L[v] = l;
+  }
+}
+
+__global__ void k_srv_inc_finish(uint32_t *log, uint32_t *words, const Ctrl *ctrl) {
+  log[0] = 0u;
+  words[0] = *(const volatile uint32_t *)&ctrl->gmin;
+}
+
 }  // namespace srv
 }  // namespace cc
 
@@ -402,6 +464,10 @@ struct GraphState {
   cc::Ctrl *ctrl = nullptr;
   uint32_t *Z = nullptr;  // zero-tree bitmap (large graphs under R), or null
   uint64_t z_bytes = 0;
+  // incremental snapshots: last labels, changed-root log, label remap, bitmap
+  uint32_t *Llast = nullptr, *log = nullptr, *rem = nullptr, *chg = nullptr, *words = nullptr;
+  uint64_t chg_bytes = 0;
+  bool has_last = false;  // Llast holds the labels of a snapshot (or of the admission)
   uint32_t m = 0;
   std::deque<Req *> fifo;
   int group = kIdle;
@@ -456,11 +522,18 @@ namespace {
 bool wants_z(uint64_t n, bool rf) { return rf && n * 4 >= cc::srv::kZMinBytes; }
 uint64_t z_bytes_for(uint64_t n) { return (n + 1 + 31) / 32 * 4; }
 
+// Incremental-snapshot buffers: labels (n), log (count + n), remap (n + 1:
+// root-value labels reach n), changed-label bitmap, a few words.
+uint64_t inc_bytes(uint64_t n) {
+  return align256((size_t)((n + 3) / 4 * 4) * 4) + align256((size_t)(n + 1) * 4) + align256((size_t)(n + 1) * 4) +
+         align256((size_t)((n + 1 + 31) / 32) * 4) + align256(16);
+}
+
 uint64_t graph_bytes(uint64_t n, uint64_t n_edges, bool rf) {
   size_t b = align256((size_t)((n + 3) / 4 * 4) * 4) + align256(sizeof(cc::Ctrl));
   if (rf) b += align256((size_t)n * (n_edges >= (1ULL << 31) ? 8 : 4)) + align256(sizeof(cc::CertScratch));
   if (wants_z(n, rf)) b += align256(z_bytes_for(n));
-  return b;
+  return b + inc_bytes(n);
 }
 
 cudaStream_t side_stream_of(const cc_server *s, uint32_t gid) {
@@ -509,6 +582,7 @@ void write_tiles(cc_server *s, const Req &r, uint32_t kind, uint64_t count, cons
     w.begin = i * tile;
     w.end = w.begin + tile < count ? w.begin + tile : count;
     w.out = (uint64_t)(uintptr_t)r.r.out_dev;
+    w.log = (uint64_t)(uintptr_t)g.log;
   }
   pub += nt;
 }
@@ -591,11 +665,23 @@ bool start_new_graph(cc_server *s, Req *r, GraphState &g) {
   if (wants_z(g.n, rf)) {
     g.Z = reinterpret_cast<uint32_t *>(p);
     g.z_bytes = z_bytes_for(g.n);
+    p += align256(g.z_bytes);
   }
+  g.Llast = reinterpret_cast<uint32_t *>(p);
+  p += align256((size_t)((g.n + 3) / 4 * 4) * 4);
+  g.log = reinterpret_cast<uint32_t *>(p);
+  p += align256((size_t)(g.n + 1) * 4);
+  g.rem = reinterpret_cast<uint32_t *>(p);
+  p += align256((size_t)(g.n + 1) * 4);
+  g.chg = reinterpret_cast<uint32_t *>(p);
+  g.chg_bytes = (size_t)((g.n + 1 + 31) / 32) * 4;
+  p += align256(g.chg_bytes);
+  g.words = reinterpret_cast<uint32_t *>(p);
   r->state.store(kRunning);
   cudaStream_t ss = side_stream_of(s, r->graph);
   cudaError_t e = cudaMemsetAsync(g.ctrl, 0, sizeof(cc::Ctrl), ss);
   if (e == cudaSuccess && g.Z) e = cudaMemsetAsync(g.Z, 0, g.z_bytes, ss);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g.chg, 0, g.chg_bytes, ss);
   const uint32_t n = (uint32_t)g.n;
   const cc::EdgeSpan span = cc::split_edges(r->r.edges_dev, r->r.n_edges);
   int m_src = cc::kMFromHint;
@@ -607,7 +693,18 @@ bool start_new_graph(cc_server *s, Req *r, GraphState &g) {
   if (e == cudaSuccess && n)
     e = cc::launch_edge_pass(rf, 1, 4, 256, span, g.P, n, g.ctrl, nullptr, ss, g.Z, g.Z ? &g.ctrl->cert : nullptr,
                              true);
-  if (e == cudaSuccess && n) e = cc::launch_flatten(rf, s->cfg.label_space, g.P, n, r->r.labels_dev, g.ctrl, ss);
+  // with labels requested they also go to the graph's own copy (the base of
+  // incremental snapshots); otherwise the first snapshot makes that copy
+  g.has_last = r->r.labels_dev != nullptr && n;
+  if (e == cudaSuccess && n)
+    e = cc::launch_flatten(rf, s->cfg.label_space, g.P, n, g.has_last ? g.Llast : nullptr, g.ctrl, ss);
+  if (e == cudaSuccess && g.has_last)
+    e = cudaMemcpyAsync(r->r.labels_dev, g.Llast, (size_t)n * 4, cudaMemcpyDeviceToDevice, ss);
+  if (e == cudaSuccess) {
+    cc::srv::k_srv_inc_finish<<<1, 1, 0, ss>>>(g.log, g.words, g.ctrl);  // empty log, gmin of these labels
+    cc::note_launch();
+    e = cudaGetLastError();
+  }
   const uint32_t gid = r->graph;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&s->side_words[2 * gid], &g.ctrl->m, sizeof(uint32_t), cudaMemcpyDeviceToHost, ss);
@@ -629,11 +726,47 @@ bool start_snapshot(cc_server *s, Req *r, GraphState &g) {
   r->state.store(kRunning);
   cudaStream_t ss = side_stream_of(s, r->graph);
   cudaError_t e = cudaSuccess;
-  if (g.n) {
+  if (g.n && !g.has_last) {
+    // the first snapshot: a full flatten into the graph's copy, then the
+    // caller's buffer; the log starts over
+    const uint32_t n = (uint32_t)g.n;
     cc::srv::k_srv_prep_flatten<<<1, 1, 0, ss>>>(g.ctrl);
     cc::note_launch();
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = cc::launch_flatten(g.rf, s->cfg.label_space, g.P, (uint32_t)g.n, r->r.labels_dev, g.ctrl, ss);
+    if (e == cudaSuccess) e = cc::launch_flatten(g.rf, s->cfg.label_space, g.P, n, g.Llast, g.ctrl, ss);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(r->r.labels_dev, g.Llast, (size_t)n * 4, cudaMemcpyDeviceToDevice, ss);
+    if (e == cudaSuccess) {
+      cc::srv::k_srv_inc_finish<<<1, 1, 0, ss>>>(g.log, g.words, g.ctrl);
+      cc::note_launch();
+      e = cudaGetLastError();
+    }
+    g.has_last = true;
+  } else if (g.n) {
+    // incremental: remap the labels the logged roots led, rewrite Llast
+    const uint32_t n = (uint32_t)g.n;
+    const uint32_t min_id = s->cfg.label_space == cc::kLabelMinId ? 1u : 0u;
+    cc::srv::k_srv_prep_flatten<<<1, 1, 0, ss>>>(g.ctrl);
+    cc::note_launch();
+    e = cudaGetLastError();
+    if (e == cudaSuccess && g.rf && min_id) e = cc::launch_gmin_probe(g.P, n, g.ctrl, ss);
+    if (e == cudaSuccess) {
+      const unsigned gr = cc::clamp_grid(((uint64_t)n + 255) / 256,
+                                         cc::persistent_cap((const void *)cc::srv::k_srv_inc_remap, 256, 0));
+      cc::srv::k_srv_inc_remap<<<gr, 256, 0, ss>>>(g.P, g.rf ? 1u : 0u, min_id, g.log, g.rem, g.chg, g.words, g.ctrl);
+      cc::note_launch();
+      const unsigned gl = cc::clamp_grid(((uint64_t)n + 255) / 256,
+                                         cc::persistent_cap((const void *)cc::srv::k_srv_inc_relabel, 256, 0));
+      cc::srv::k_srv_inc_relabel<<<gl, 256, 0, ss>>>(g.Llast, n, g.rem, g.chg, r->r.labels_dev);
+      cc::note_launch();
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.chg, 0, g.chg_bytes, ss);
+    if (e == cudaSuccess) {
+      cc::srv::k_srv_inc_finish<<<1, 1, 0, ss>>>(g.log, g.words, g.ctrl);
+      cc::note_launch();
+      e = cudaGetLastError();
+    }
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(r->ev, ss);
@@ -665,7 +798,7 @@ bool start_side_insert(cc_server *s, Req *r, GraphState &g) {
   if (e == cudaSuccess) e = cc::launch_validate(span, n, g.ctrl, ss, rej);
   if (e == cudaSuccess)
     e = cc::launch_edge_pass(g.rf, 1, 4, 256, span, g.P, n, g.ctrl, rej, ss, g.Z, g.Z ? &g.ctrl->cert : nullptr,
-                             true);
+                             true, g.log);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&s->side_flags[r->flag], rej, sizeof(uint32_t), cudaMemcpyDeviceToHost, ss);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
@@ -943,13 +1076,14 @@ cudaError_t warm_up(cc_server *s) {
   const bool rf = s->cfg.mode == CC_ROOT_MAXDEG;
   const uint32_t n = 16;
   const uint32_t edges_h[8] = {0, 1, 2, 3, 3, 1, 5, 5};
-  uint32_t *P = nullptr, *edges = nullptr, *labels = nullptr, *Z = nullptr;
+  uint32_t *P = nullptr, *edges = nullptr, *labels = nullptr, *Z = nullptr, *inc = nullptr;
   void *cnt = nullptr;
   cc::CertScratch *cert = nullptr;
   cc::Ctrl *ctrl = nullptr;
   cudaStream_t ss = s->side_stream;
   cudaError_t e = cudaMalloc((void **)&P, 64 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc((void **)&Z, 64 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&inc, 256 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc((void **)&edges, sizeof(edges_h));
   if (e == cudaSuccess) e = cudaMalloc((void **)&labels, 64 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&cnt, 64 * sizeof(unsigned long long));
@@ -973,6 +1107,16 @@ cudaError_t warm_up(cc_server *s) {
     if (e == cudaSuccess) e = cc::launch_edge_pass(rf, 1, 4, 256, span, P, n, ctrl, &ctrl->reject, ss, Z, &ctrl->cert);
     if (e == cudaSuccess) e = cc::launch_flatten(rf, s->cfg.label_space, P, n, labels, ctrl, ss);
     if (e == cudaSuccess) e = cc::launch_flatten(rf, s->cfg.label_space, P, n, nullptr, ctrl, ss);
+    // an incremental snapshot over an empty log (log, remap, bitmap, words
+    // in one zeroed scratch)
+    if (e == cudaSuccess) e = cudaMemsetAsync(inc, 0, 256 * sizeof(uint32_t), ss);
+    if (e == cudaSuccess) e = cc::launch_gmin_probe(P, n, ctrl, ss);
+    if (e == cudaSuccess) {
+      cc::srv::k_srv_inc_remap<<<1, 256, 0, ss>>>(P, rf ? 1u : 0u, 1u, inc, inc + 64, inc + 128, inc + 192, ctrl);
+      cc::srv::k_srv_inc_relabel<<<1, 256, 0, ss>>>(labels, n, inc + 64, inc + 128, labels + 32);
+      cc::srv::k_srv_inc_finish<<<1, 1, 0, ss>>>(inc, inc + 192, ctrl);
+      e = cudaGetLastError();
+    }
     if (e == cudaSuccess) {
       cc::srv::k_srv_prep_flatten<<<1, 1, 0, ss>>>(ctrl);
       e = cudaGetLastError();
@@ -997,6 +1141,7 @@ cudaError_t warm_up(cc_server *s) {
   }
   cudaFree(P);
   cudaFree(Z);
+  cudaFree(inc);
   cudaFree(edges);
   cudaFree(labels);
   cudaFree(cnt);

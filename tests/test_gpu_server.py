@@ -144,9 +144,9 @@ def test_insert_with_bad_id_is_rejected_whole():
 
 
 def test_admission_waits_for_memory_and_drop_frees_it():
-    n = 1 << 20  # ~8.2 MiB per graph under f = R (P + histogram + scratch)
+    n = 1 << 20  # ~20.3 MiB per graph under f = R (P, histogram, scratch, last labels, log, remap)
     e = graphgen.rmat(20, 1 << 21, 5, scramble=True)
-    with cc.Server(12 << 20) as s:
+    with cc.Server(32 << 20) as s:
         ta, ga = s.new_graph(n, dev(e))
         tb, gb = s.new_graph(n, dev(e))  # cannot fit until graph a is dropped
         assert s.wait(ta) == cc.CC_OK
@@ -268,3 +268,41 @@ def test_large_graph_side_inserts_and_zero_tree():
         np.testing.assert_array_equal(out.cpu().numpy(), oracle.connected(want, q))
         assert s.stats()["failed"] == 0
 
+
+
+@pytest.mark.parametrize("mode", [cc.CC_ROOT_MAXDEG, cc.CC_ROOT_IDENTITY])
+@pytest.mark.parametrize("label_space", [cc.CC_LABEL_MIN_ID, cc.CC_LABEL_ROOT_VALUE])
+@pytest.mark.parametrize("admit_labels", [True, False])
+def test_incremental_snapshots(mode, label_space, admit_labels):
+    """Snapshots after inserts come from the last labels and the changed-root
+    log (executor tiles and side-stream inserts both log the roots they
+    hook); every one must equal the oracle on all edges so far, including an
+    insert that gives m's component a smaller vertex (a new gmin)."""
+    n = 1 << 15
+    base = graphgen.rmat(15, 1 << 16, 41, scramble=True)
+    base = base[(base[:, 0] != 3) & (base[:, 1] != 3)]  # vertex 3 starts isolated
+    m = oracle.max_degree_vertex(n, base)
+    batches = [graphgen.pairs(n, k, 42, tag=i) for i, k in enumerate([5, 2000, 300000, 1, 40000])]
+    batches.insert(2, np.array([[3, m]], np.uint32))  # 3 joins m's component
+    seen = [base]
+
+    def want():
+        e = np.concatenate(seen)
+        if label_space == cc.CC_LABEL_MIN_ID:
+            return oracle.min_labels(n, e)
+        return oracle.root_value_labels(n, e, m) if mode == cc.CC_ROOT_MAXDEG else oracle.min_labels(n, e)
+
+    with cc.Server(GB, mode=mode, label_space=label_space) as s:
+        L0 = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        t, g = s.new_graph(n, dev(base), L0 if admit_labels else None)
+        assert s.wait(t) == cc.CC_OK
+        if admit_labels:  # else the first snapshot below makes the graph's copy
+            np.testing.assert_array_equal(L0.cpu().numpy().view(np.uint32), want())
+        for b in batches:
+            assert s.wait(s.insert(g, dev(b))) == cc.CC_OK
+            seen.append(b)
+            for _ in range(2):  # a second snapshot with an empty log
+                L = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+                torch.cuda.synchronize()
+                assert s.wait(s.snapshot(g, L)) == cc.CC_OK
+                np.testing.assert_array_equal(L.cpu().numpy().view(np.uint32), want())
