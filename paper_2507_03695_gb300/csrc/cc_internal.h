@@ -96,13 +96,16 @@ cudaError_t launch_init(bool rf, uint32_t *P, uint32_t n, Ctrl *ctrl, int m_src,
                         cudaStream_t s, const uint32_t *skip = nullptr);
 // Scratch of the certified exact root selection (cc_rootsel.cu).
 constexpr uint32_t kCertCand = 4096;     // more candidates than this: no proof is tried
-constexpr uint32_t kCertBuckets = 8192;  // hash buckets of the degree bound, one owner each
+constexpr uint32_t kCertBuckets = 8192;  // hash buckets of the degree bound
+constexpr uint32_t kCertTop = 4;         // candidates whose degree is counted exactly
 constexpr uint32_t kCertSample = 128;    // the sampled pass keeps 1 group of 1024 edges in this many
 struct CertScratch {
-  unsigned long long owner[kCertBuckets];     // (sampled count << 32) | ~vertex of the owner; 0 = none
-  unsigned long long cand_cnt[kCertBuckets];  // exact degree of the owner
-  unsigned long long bucket[kCertBuckets];    // endpoint occurrences of the other vertices
-  unsigned int blocks_done;                   // counting blocks finished (the last one decides)
+  unsigned long long owner[kCertBuckets];   // per bucket, its best sampled (count << 32) | ~vertex; 0 = none
+  unsigned long long top[kCertTop];         // the best owners, same packing; 0 = empty slot
+  unsigned long long top_cnt[kCertTop];     // their exact degrees
+  unsigned long long bucket[kCertBuckets];  // endpoint occurrences of all vertices of the bucket
+  unsigned int sel_done;                    // candidate-selection blocks finished (the last one ranks)
+  unsigned int blocks_done;                 // counting blocks finished (the last one decides)
   // Initial Push (Algorithm 4): neighbours of the sampled argmax m', appended
   // through kPushLanes counters, each owning a segment of the push buffer
   unsigned int push_cnt[256];

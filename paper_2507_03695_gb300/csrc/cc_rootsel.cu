@@ -8,13 +8,16 @@
 // therefore certified instead:
 //   1. a histogram over 1 group of 1024 edges in 128 (global atomics) gives
 //      candidate hubs: every vertex with at least 1/32 of the largest sampled
-//      count (at most kCertCand of them);
-//   2. one pass over all edges counts, in shared memory only, the exact
-//      degree of every candidate and the total endpoint occurrences of every
-//      hash bucket of vertex ids;
-//   3. if the best candidate's degree D exceeds, in every bucket, the
-//      occurrences that belong to non-candidates, no non-candidate can reach
-//      D, so the best candidate (smaller id on ties) is the exact answer;
+//      count (at most kCertCand of them); the best per hash bucket of vertex
+//      ids competes, and the kCertTop best of those are kept;
+//   2. one pass over all edges counts, in registers, the exact degree of each
+//      kept candidate and, in shared memory, the endpoint occurrences of every
+//      bucket;
+//   3. a bucket's occurrences minus the exact degrees of the kept candidates
+//      in it bound the degree of every other vertex of the bucket; if the
+//      best candidate's degree D (smaller id on ties) exceeds that bound in
+//      every bucket, no other vertex can reach D, and the best candidate is
+//      the exact answer;
 //   4. otherwise (graphs without a dominant hub, such as grids) the full
 //      global histogram runs; its kernels read the certificate flag and
 //      return at once when step 3 succeeded.
@@ -167,16 +170,15 @@ static_assert(kCertBuckets == 8192, "13-bit buckets");
 
 // Candidates: every vertex whose sampled count is at least 1/32 of the largest
 // competes for its bucket; the larger sampled count (then the smaller id)
-// owns it. A vertex that loses stays counted in the bucket total, which then
-// bounds its degree too, so the proof stays sound. Without a dominant hub
-// (largest sampled count below 64) no certificate can succeed and nothing is
-// selected. Scanning stops once more than kCertCand candidates are seen: so
-// many near-maximal vertices leave no room for a proof, and the full
-// histogram runs.
+// owns it. Without a dominant hub (largest sampled count below 64) no
+// certificate can succeed and nothing is selected. Scanning stops once more
+// than kCertCand candidates are seen: so many near-maximal vertices leave no
+// room for a proof, and the full histogram runs. The last block to finish
+// ranks the owners and keeps the kCertTop best for the counting pass.
 __global__ void __launch_bounds__(256) k_select_candidates(const uint32_t *__restrict__ cnt, uint32_t n,
                                                            Ctrl *ctrl, CertScratch *cs) {
   const uint32_t cmax = (uint32_t)(*(volatile unsigned long long *)&ctrl->maxkey >> 32);
-  if (cmax < 64u) return;
+  if (cmax < 64u) return;  // uniform over the grid: no block ranks, top stays empty
   const uint32_t thr = cmax >> 5;
   const int lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
@@ -190,56 +192,75 @@ __global__ void __launch_bounds__(256) k_select_candidates(const uint32_t *__res
     uint32_t seen = 0;
     if (lane == 0) seen = atomicAdd(&ctrl->n_cand, (uint32_t)__popc(bal)) + (uint32_t)__popc(bal);
     seen = __shfl_sync(0xFFFFFFFFu, seen, 0);
-    if (seen > kCertCand) return;  // too many candidates (warp-uniform)
+    if (seen > kCertCand) break;  // too many candidates (warp-uniform)
     if (q)
       atomicMax(&cs->owner[bucket_of((uint32_t)v)], ((unsigned long long)c << 32) | (uint32_t)~(uint32_t)v);
   }
+  __shared__ unsigned s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&cs->sel_done, 1u) == gridDim.x - 1u;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // rank: kCertTop rounds of a block maximum over the owners, each round
+  // excluding the keys already taken (keys are distinct: they hold the id)
+  unsigned long long taken = ~0ULL;  // the previous round's winner; keys below it remain
+  for (uint32_t r = 0; r < kCertTop; ++r) {
+    unsigned long long best = 0;
+    for (uint32_t b = threadIdx.x; b < kCertBuckets; b += blockDim.x) {
+      const unsigned long long o = __ldcg(&cs->owner[b]);
+      if (o < taken && o > best) best = o;
+    }
+    best = block_max_u64(best);
+    if (best == 0ULL) break;  // uniform: fewer owners than kCertTop
+    if (threadIdx.x == 0) cs->top[r] = best;
+    taken = best;
+  }
 }
 
-// One endpoint: the owner's exact count, or the bucket total of the others.
-// Ids >= n are counted too; they only make the bound more conservative (the
-// edge pass reports them).
-__device__ __forceinline__ void cert_count(uint32_t x, const uint32_t *key, uint32_t *own, uint32_t *bk) {
-  const uint32_t b = bucket_of(x);
-  if (key[b] == x + 1u)
-    atomicAdd(&own[b], 1u);
-  else
-    atomicAdd(&bk[b], 1u);
-}
-
-constexpr size_t kCertSmem = 3 * kCertBuckets * sizeof(uint32_t);  // 96 KiB
+constexpr size_t kCertSmem = kCertBuckets * sizeof(uint32_t);  // 32 KiB
 
 __device__ __forceinline__ bool cert_skipped(const Ctrl *ctrl) {
   const uint32_t nc = *(const volatile uint32_t *)&ctrl->n_cand;
   return nc == 0u || nc > kCertCand;
 }
 
-// The proof, by one block: D = best owner degree (ties to the smaller id);
-// bound = the largest bucket total of non-owners. D > bound means every other
-// vertex has degree < D. Reads through L2: other blocks wrote the totals.
+// The proof, by one block: D = best exact candidate degree (ties to the
+// smaller id); bound = the largest bucket total less the exact degrees of the
+// candidates in that bucket. D > bound means every other vertex has degree
+// < D. Reads through L2: other blocks wrote the totals.
 __device__ void certify_decide_block(const CertScratch *cs, Ctrl *ctrl) {
-  unsigned long long best = 0, bound = 0;
-  bool wide = false;
   const bool skip = cert_skipped(ctrl);
-  for (uint32_t b = threadIdx.x; b < kCertBuckets && !skip; b += blockDim.x) {
-    const unsigned long long o = __ldcg(&cs->owner[b]);
-    const unsigned long long t = __ldcg(&cs->bucket[b]);
-    bound = t > bound ? t : bound;
+  uint32_t cv[kCertTop];
+  unsigned long long cc[kCertTop];
+  bool any = false, wide = false;
+  unsigned long long best = 0, bound = 0;
+#pragma unroll
+  for (uint32_t k = 0; k < kCertTop; ++k) {
+    const unsigned long long o = __ldcg(&cs->top[k]);
+    cv[k] = o ? ~(uint32_t)o : 0u;
+    cc[k] = o ? __ldcg(&cs->top_cnt[k]) : 0ULL;
     if (!o) continue;
-    const unsigned long long c = __ldcg(&cs->cand_cnt[b]);
-    if (c >= (1ULL << 32)) {
+    any = true;
+    if (cc[k] >= (1ULL << 32)) {
       wide = true;
       continue;
     }
-    const unsigned long long k = (c << 32) | (uint32_t)o;  // low half: ~vertex
-    best = k > best ? k : best;
+    const unsigned long long key = (cc[k] << 32) | (uint32_t)o;  // low half: ~vertex
+    best = key > best ? key : best;
   }
-  const int any_wide = __syncthreads_or(wide);
-  best = block_max_u64(best);
+  for (uint32_t b = threadIdx.x; b < kCertBuckets && !skip && any; b += blockDim.x) {
+    unsigned long long t = __ldcg(&cs->bucket[b]);
+#pragma unroll
+    for (uint32_t k = 0; k < kCertTop; ++k)
+      if (cc[k] && bucket_of(cv[k]) == b) t -= cc[k];
+    bound = t > bound ? t : bound;
+  }
   bound = block_max_u64(bound);
   if (threadIdx.x == 0) {
     const unsigned long long D = best >> 32;
-    if (!skip && !any_wide && best != 0ULL && D > bound) {
+    if (!skip && any && !wide && best != 0ULL && D > bound) {
       ctrl->maxkey = best;
       ctrl->cert = 1u;
     } else {
@@ -254,8 +275,9 @@ __global__ void __launch_bounds__(256) k_certify_decide(const CertScratch *cs, C
   certify_decide_block(cs, ctrl);
 }
 
-// One pass over all edges: exact owner degrees and bucket totals, counted in
-// shared memory (32-bit per block) and flushed once per block.
+// One pass over all edges: exact candidate degrees (per-thread registers,
+// summed per warp at the end) and bucket totals (shared memory, 32-bit per
+// block, flushed once per block): one shared-memory atomic per endpoint.
 // decide: the last block to finish also takes the decision (one pass over
 // all edges); otherwise k_certify_decide runs after the last chunk.
 // With push_buf, the other endpoint of every edge incident to the sampled
@@ -278,10 +300,24 @@ __device__ __forceinline__ void push_neighbour(uint32_t a, uint32_t b, uint32_t 
     cs->push_overflow = 1u;
 }
 
-__global__ void __launch_bounds__(512) k_degree_certify(const uint4 *__restrict__ e4, uint64_t n_quads,
-                                                        const uint2 *head, const uint2 *tail, uint32_t n,
-                                                        CertScratch *cs, Ctrl *ctrl, int decide, uint32_t *push_buf,
-                                                        uint32_t push_seg) {
+// Counts one endpoint. Ids >= n are counted too; they only make the bound
+// more conservative (the edge pass reports them).
+struct CertCounter {
+  uint32_t key[kCertTop];  // candidate ids (an empty slot matches only id 2^32 - 1, and is ignored)
+  uint32_t c[kCertTop];
+  uint32_t *bk;
+  __device__ __forceinline__ void operator()(uint32_t x) {
+    atomicAdd(&bk[bucket_of(x)], 1u);
+#pragma unroll
+    for (uint32_t k = 0; k < kCertTop; ++k) c[k] += x == key[k] ? 1u : 0u;
+  }
+};
+
+constexpr int kCertBlock = 512;
+
+__global__ void __launch_bounds__(kCertBlock, 2)
+    k_degree_certify(const uint4 *__restrict__ e4, uint64_t n_quads, const uint2 *head, const uint2 *tail, uint32_t n,
+                     CertScratch *cs, Ctrl *ctrl, int decide, uint32_t *push_buf, uint32_t push_seg) {
   extern __shared__ uint32_t csm[];
   if (cert_skipped(ctrl)) {  // no proof possible: the full histogram runs
     if (decide && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -290,67 +326,70 @@ __global__ void __launch_bounds__(512) k_degree_certify(const uint4 *__restrict_
     }
     return;
   }
-  uint32_t *key = csm, *own = csm + kCertBuckets, *bk = csm + 2 * kCertBuckets;
+  CertCounter cnt;
+  cnt.bk = csm;
+#pragma unroll
+  for (uint32_t k = 0; k < kCertTop; ++k) {
+    const unsigned long long o = *(const volatile unsigned long long *)&cs->top[k];
+    cnt.key[k] = o ? ~(uint32_t)o : 0xFFFFFFFFu;
+    cnt.c[k] = 0u;
+  }
   // the sampled argmax, whose neighbours the push list gathers
   const uint32_t mp = ~(uint32_t)(*(const volatile unsigned long long *)&ctrl->maxkey);
   if (push_buf && blockIdx.x == 0 && threadIdx.x == 0) cs->push_m = mp + 1u;
-  for (uint32_t i = threadIdx.x; i < kCertBuckets; i += blockDim.x) {
-    const unsigned long long o = cs->owner[i];
-    key[i] = o ? (uint32_t)~(uint32_t)o + 1u : 0u;
-    own[i] = 0u;
-    bk[i] = 0u;
-  }
+  for (uint32_t i = threadIdx.x; i < kCertBuckets; i += blockDim.x) csm[i] = 0u;
   __syncthreads();
   const uint64_t pol = policy_evict_first();
   const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (t == 0 && head) {
     const uint2 e = ld_edge(head);
-    cert_count(e.x, key, own, bk);
-    cert_count(e.y, key, own, bk);
+    cnt(e.x);
+    cnt(e.y);
     if (push_buf) push_neighbour(e.x, e.y, mp, push_buf, push_seg, cs);
   }
   if (t == 1 % T && tail) {
     const uint2 e = ld_edge(tail);
-    cert_count(e.x, key, own, bk);
-    cert_count(e.y, key, own, bk);
+    cnt(e.x);
+    cnt(e.y);
     if (push_buf) push_neighbour(e.x, e.y, mp, push_buf, push_seg, cs);
   }
   uint64_t q = t;
-  for (; q + T < n_quads; q += 2 * T) {  // two loads in flight per thread
-    const uint4 a = ld_edges(e4 + q, pol);
-    const uint4 c = ld_edges(e4 + q + T, pol);
-    cert_count(a.x, key, own, bk);
-    cert_count(a.y, key, own, bk);
-    cert_count(a.z, key, own, bk);
-    cert_count(a.w, key, own, bk);
-    cert_count(c.x, key, own, bk);
-    cert_count(c.y, key, own, bk);
-    cert_count(c.z, key, own, bk);
-    cert_count(c.w, key, own, bk);
-    if (push_buf) {
-      push_neighbour(a.x, a.y, mp, push_buf, push_seg, cs);
-      push_neighbour(a.z, a.w, mp, push_buf, push_seg, cs);
-      push_neighbour(c.x, c.y, mp, push_buf, push_seg, cs);
-      push_neighbour(c.z, c.w, mp, push_buf, push_seg, cs);
+  for (; q + 3 * T < n_quads; q += 4 * T) {  // four loads in flight per thread
+    uint4 a[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a[j] = ld_edges(e4 + q + j * T, pol);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      cnt(a[j].x);
+      cnt(a[j].y);
+      cnt(a[j].z);
+      cnt(a[j].w);
+      if (push_buf) {
+        push_neighbour(a[j].x, a[j].y, mp, push_buf, push_seg, cs);
+        push_neighbour(a[j].z, a[j].w, mp, push_buf, push_seg, cs);
+      }
     }
   }
-  if (q < n_quads) {
+  for (; q < n_quads; q += T) {
     const uint4 a = ld_edges(e4 + q, pol);
-    cert_count(a.x, key, own, bk);
-    cert_count(a.y, key, own, bk);
-    cert_count(a.z, key, own, bk);
-    cert_count(a.w, key, own, bk);
+    cnt(a.x);
+    cnt(a.y);
+    cnt(a.z);
+    cnt(a.w);
     if (push_buf) {
       push_neighbour(a.x, a.y, mp, push_buf, push_seg, cs);
       push_neighbour(a.z, a.w, mp, push_buf, push_seg, cs);
     }
+  }
+#pragma unroll
+  for (uint32_t k = 0; k < kCertTop; ++k) {
+    const uint32_t w = __reduce_add_sync(0xFFFFFFFFu, cnt.c[k]);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(&cs->top_cnt[k], (unsigned long long)w);
   }
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < kCertBuckets; i += blockDim.x) {
-    if (own[i]) atomicAdd(&cs->cand_cnt[i], (unsigned long long)own[i]);
-    if (bk[i]) atomicAdd(&cs->bucket[i], (unsigned long long)bk[i]);
-  }
+  for (uint32_t i = threadIdx.x; i < kCertBuckets; i += blockDim.x)
+    if (csm[i]) atomicAdd(&cs->bucket[i], (unsigned long long)csm[i]);
   if (!decide) return;
   __shared__ unsigned s_last;
   __threadfence();
@@ -457,10 +496,11 @@ cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges
   if ((err = ensure_func_attr((const void *)k_degree_certify, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)kCertSmem, smem_set_certify)) != cudaSuccess)
     return err;
-  const unsigned gcert = clamp_grid((e.n_quads + 511) / 512, persistent_cap((const void *)k_degree_certify, 512, kCertSmem));
+  const unsigned gcert = clamp_grid((e.n_quads + kCertBlock - 1) / kCertBlock,
+                                    persistent_cap((const void *)k_degree_certify, kCertBlock, kCertSmem));
   // 4. the proof: taken by the counting pass's last block (which also
   // gathers the push list when asked to)
-  k_degree_certify<<<gcert, 512, kCertSmem, s>>>(e.quads, e.n_quads, e.head, e.tail, n, cs, ctrl, 1, push_buf,
+  k_degree_certify<<<gcert, kCertBlock, kCertSmem, s>>>(e.quads, e.n_quads, e.head, e.tail, n, cs, ctrl, 1, push_buf,
                                                  push_buf ? push_cap / kPushLanes : 0u);
   note_launch();
   // 5. full histogram, skipped when certified
@@ -570,8 +610,9 @@ cudaError_t chunked_select_chunk(const EdgeSpan &chunk, void *cnt, bool wide, ui
                               (int)kCertSmem, smem_set_certify)) != cudaSuccess)
     return err;
   const unsigned gcert =
-      clamp_grid((chunk.n_quads + 511) / 512, persistent_cap((const void *)k_degree_certify, 512, kCertSmem));
-  k_degree_certify<<<gcert, 512, kCertSmem, s>>>(chunk.quads, chunk.n_quads, chunk.head, chunk.tail, n, cs, ctrl, 0,
+      clamp_grid((chunk.n_quads + kCertBlock - 1) / kCertBlock,
+                 persistent_cap((const void *)k_degree_certify, kCertBlock, kCertSmem));
+  k_degree_certify<<<gcert, kCertBlock, kCertSmem, s>>>(chunk.quads, chunk.n_quads, chunk.head, chunk.tail, n, cs, ctrl, 0,
                                                  nullptr, 0u);
   note_launch();
   return cudaGetLastError();
