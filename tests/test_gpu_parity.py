@@ -436,6 +436,40 @@ def _csr_dev(off, nb):
             torch.from_numpy(np.ascontiguousarray(nb, dtype=np.uint32).view(np.int32)).cuda())
 
 
+@pytest.mark.parametrize("hub,deg", [(1001, 255), (1001, 256), (1003, 300), (4, 70000), (65535, 511)])
+def test_hub_outside_sample(hub, deg):
+    """A hub whose edges all sit in groups the sampled pass skips: no
+    candidate, no certificate, so the exact selection falls back to the full
+    histogram (the sampled counts plus every other edge). Degrees around 2^8
+    and 2^16 and ids at both ends of the range. m and the labels equal the
+    oracle's."""
+    n = 1 << 16
+    e = graphgen.er(n, 1 << 20, 90)  # background degree about 32
+    rng = np.random.default_rng(91)
+    e[e == hub] = (hub + 7) % n  # the hub's degree is exactly the planted edges
+    idx = 1024 + np.arange(deg)  # groups 1 .. 127 of 1024 edges: never sampled
+    assert idx[-1] < 128 * 1024
+    e[idx, 0] = hub
+    other = rng.integers(0, n - 1, size=deg, dtype=np.uint32)
+    e[idx, 1] = other + (other >= hub)
+    m = oracle.max_degree_vertex(n, e)
+    assert m == hub
+    want = oracle.min_labels(n, e)
+    for label_space in (cc.CC_LABEL_MIN_ID, cc.CC_LABEL_ROOT_VALUE):
+        with cc.Graph(n, label_space=label_space) as g:
+            L = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+            d = dev_edges(e)
+            for _ in range(2):  # the second run starts from a used parent array
+                g.run(d, L)
+                g.sync()
+                assert g.root_vertex() == m
+                got = L.cpu().numpy().view(np.uint32)
+                if label_space == cc.CC_LABEL_MIN_ID:
+                    np.testing.assert_array_equal(got, want)
+                else:
+                    np.testing.assert_array_equal(got, oracle.root_value_labels(n, e, m))
+
+
 def _csr_case(case):
     if case == "rmat16":
         w = graphgen.RMAT16
