@@ -190,9 +190,10 @@ CC_API cc_status cc_run_csr(cc_graph *g, const uint64_t *offsets_dev, const uint
  * n_edges_capacity) to the device in chunks of 2^24 edges and works on each
  * chunk as it lands: with m known in advance (identity, or a hint) the edge
  * pass; with exact selection, hooking under a speculative m' taken from the
- * first chunk while the certificate's counts accumulate, then one more
- * init + edge pass only if m' was not the exact m; with sampled selection,
- * nothing until the last chunk. The labels go to L_out_host
+ * first chunk (the sampled leader when a hub shows, else the first chunk's
+ * argmax) while the certificate's or the histogram's counts accumulate, then
+ * one more init + edge pass only if m' was not the exact m; with sampled
+ * selection, nothing until the last chunk. The labels go to L_out_host
  * (uint32[n_vertices], may be NULL). Synchronising: returns after the labels
  * are in host memory, with any device error. */
 CC_API cc_status cc_run_host(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges,

@@ -447,7 +447,6 @@ static cc_status run_host_impl(cc_graph *g, const void *edges_host, uint64_t n_e
   // the copy stream starts after everything already enqueued on s
   CC_TRY(cudaEventRecord(g->copy_ev, s));
   CC_TRY(cudaStreamWaitEvent(g->copy_stream, g->copy_ev, 0));
-  const uint32_t *no_spec = &g->ctrl->skip[cc::kSkipSpec];
   for (uint64_t off = 0; off < n_edges; off += kHostChunk) {
     const uint64_t cnt = (n_edges - off) < kHostChunk ? (n_edges - off) : kHostChunk;
     if (id_bytes == 3) {
@@ -469,13 +468,12 @@ static cc_status run_host_impl(cc_graph *g, const void *edges_host, uint64_t n_e
       CC_TRY(cudaStreamWaitEvent(s, g->copy_ev, 0));
     }
     const cc::EdgeSpan chunk = cc::split_edges(g->staging + 2 * off, cnt);
-    if (chunked && off == 0) {
-      CC_TRY(cc::chunked_select_begin(g->staging, cnt, g->cnt, wide, n, g->cert, g->ctrl, s));
-      CC_TRY(cc::launch_init(true, g->P, n, g->ctrl, cc::kMFromPackedMax, 0u, s, no_spec));
-    }
-    if (chunked) CC_TRY(cc::chunked_select_chunk(chunk, g->cnt, wide, n, g->cert, g->ctrl, s));
-    CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), chunk, g->P, n, g->ctrl,
-                                chunked ? no_spec : nullptr, s, Zf));
+    if (chunked && off == 0) CC_TRY(cc::chunked_select_begin(g->staging, cnt, g->cnt, wide, n, g->cert, g->ctrl, s));
+    if (chunked) CC_TRY(cc::chunked_select_chunk(chunk, off == 0, g->cnt, wide, n, g->cert, g->ctrl, s));
+    // every chunk is hooked as it lands, under m' when m is still unknown
+    if (chunked && off == 0) CC_TRY(cc::launch_init(true, g->P, n, g->ctrl, cc::kMFromPackedMax, 0u, s));
+    CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), chunk, g->P, n, g->ctrl, nullptr,
+                                s, Zf));
   }
   const cc::EdgeSpan all = cc::split_edges(g->staging, n_edges);
   if (chunked) {

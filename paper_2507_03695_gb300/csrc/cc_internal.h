@@ -36,7 +36,7 @@ struct alignas(128) Ctrl {
   uint32_t reject;            // the insert batch being applied failed validation
   uint32_t n_cand;            // root select: candidates found by the sampled pass
   uint32_t cert;              // root select: 1 when the candidate pass proved the argmax
-  uint32_t skip[4];           // chunked root select: skip words (kSkip*), set on the device
+  uint32_t skip[3];           // chunked root select: skip words (kSkip*), set on the device
   unsigned long long stats[4];  // optional edge-pass counters
 };
 static_assert(offsetof(Ctrl, q_u) % 8 == 0, "the query pair is loaded with an 8-byte access");
@@ -115,23 +115,25 @@ struct CertScratch {
 constexpr uint32_t kPushLanes = 256;
 
 // Chunked exact root selection, for edges that arrive in chunks (host input):
-// a dense sample of the first chunk picks candidates and a speculative m'.
-// With a plausible hub, every chunk is hooked under m' as it lands while the
-// certificate's counts accumulate; without one, every chunk adds to the full
-// histogram instead. After the last chunk the device decides: m' proved exact
-// (keep the hooking), or the exact m is known (certificate or histogram) and
-// init plus one edge pass over all edges run again. Kernels read the Ctrl
-// skip words, so the host enqueues every alternative without waiting.
+// a dense sample of the first chunk picks candidates, and every chunk is
+// hooked under a speculative m' as it lands. With a plausible hub, m' is the
+// sampled leader and the certificate's counts accumulate per chunk; without
+// one, every chunk adds to the full histogram and m' is the first chunk's
+// argmax (exact on graphs whose largest degree is reached in their first
+// chunk, such as grids stored row by row). After the last chunk the device
+// knows the exact m (certificate or histogram): m' == m keeps the hooking,
+// otherwise init plus one edge pass over all edges run again. Kernels read
+// the Ctrl skip words, so the host enqueues every alternative without waiting.
 enum : int {
-  kSkipSpec = 0,      // nonzero: no speculation (init under m' and the per-chunk edge passes skip)
-  kSkipHist = 1,      // nonzero: speculating (the per-chunk histogram and its argmax skip)
-  kSkipRerun = 2,     // nonzero: m' was exact (the final init and edge pass skip)
-  kSkipFullHist = 3,  // nonzero unless speculation failed without a certificate
+  kSkipHist = 0,      // nonzero: hub mode (the per-chunk histogram and its argmaxes skip)
+  kSkipRerun = 1,     // nonzero: m' was exact (the final init and edge pass skip)
+  kSkipFullHist = 2,  // nonzero unless the hub's certificate failed (a full histogram then runs)
 };
 cudaError_t chunked_select_begin(const uint32_t *chunk0, uint64_t n0, void *cnt, bool wide, uint32_t n,
                                  CertScratch *cs, Ctrl *ctrl, cudaStream_t s);
-cudaError_t chunked_select_chunk(const EdgeSpan &chunk, void *cnt, bool wide, uint32_t n, CertScratch *cs,
-                                 Ctrl *ctrl, cudaStream_t s);
+// first: the chunk given to chunked_select_begin (its argmax is m' without a hub)
+cudaError_t chunked_select_chunk(const EdgeSpan &chunk, bool first, void *cnt, bool wide, uint32_t n,
+                                 CertScratch *cs, Ctrl *ctrl, cudaStream_t s);
 cudaError_t chunked_select_end(const EdgeSpan &all, void *cnt, bool wide, uint32_t n, CertScratch *cs,
                                Ctrl *ctrl, cudaStream_t s);
 

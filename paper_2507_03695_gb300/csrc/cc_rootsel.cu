@@ -420,26 +420,40 @@ __global__ void __launch_bounds__(256) k_initial_push(uint32_t *P, uint32_t n, c
   }
 }
 
-// Chunked selection: after the first chunk's candidates are known, decide
-// whether to speculate (a hub that a certificate can prove).
+// Chunked selection: after the first chunk's sample, hub mode (candidates
+// that a certificate can prove) or histogram mode. Histogram mode restarts
+// the argmax, which the first chunk's full histogram then sets to m'.
 __global__ void k_spec_begin(Ctrl *ctrl) {
   const uint32_t nc = *(volatile uint32_t *)&ctrl->n_cand;
-  const bool spec = nc != 0u && nc <= kCertCand;
-  ctrl->skip[kSkipSpec] = spec ? 0u : 1u;
-  ctrl->skip[kSkipHist] = spec ? 1u : 0u;
+  const bool hub = nc != 0u && nc <= kCertCand;
+  ctrl->skip[kSkipHist] = hub ? 1u : 0u;
   ctrl->skip[kSkipRerun] = 0u;
   ctrl->skip[kSkipFullHist] = 1u;
+  if (!hub) {
+    ctrl->maxkey = 0ULL;
+    ctrl->maxcnt = 0ULL;
+    ctrl->m_sel = 0xFFFFFFFFu;
+  }
 }
 
-// After the certificate's decision: did the speculative m' (planted by the
-// first init, ctrl->m) turn out to be the exact maximum-degree vertex?
+// After the certificate's decision: a hub whose certificate failed needs the
+// full histogram; histogram mode restarts the argmax for the final counts.
 __global__ void k_spec_end(Ctrl *ctrl) {
-  const bool spec = *(volatile uint32_t *)&ctrl->skip[kSkipSpec] == 0u;
+  const bool hub = *(volatile uint32_t *)&ctrl->skip[kSkipHist] != 0u;
   const bool cert = *(volatile uint32_t *)&ctrl->cert != 0u;
-  const uint32_t best = ~(uint32_t)(*(volatile unsigned long long *)&ctrl->maxkey);
-  const bool held = spec && cert && best == *(volatile uint32_t *)&ctrl->m;
-  ctrl->skip[kSkipRerun] = held ? 1u : 0u;
-  ctrl->skip[kSkipFullHist] = (spec && !cert) ? 0u : 1u;
+  ctrl->skip[kSkipFullHist] = (hub && !cert) ? 0u : 1u;
+  if (!hub) {
+    ctrl->maxkey = 0ULL;
+    ctrl->maxcnt = 0ULL;
+    ctrl->m_sel = 0xFFFFFFFFu;
+  }
+}
+
+// The exact m is in ctrl->maxkey: keep the speculative hooking when it was
+// planted under that vertex (ctrl->m, written by the first init).
+__global__ void k_spec_check(Ctrl *ctrl) {
+  const uint32_t m = ~(uint32_t)(*(volatile unsigned long long *)&ctrl->maxkey);
+  ctrl->skip[kSkipRerun] = m == *(volatile uint32_t *)&ctrl->m ? 1u : 0u;
 }
 
 }  // namespace
@@ -585,6 +599,8 @@ cudaError_t chunked_select_begin(const uint32_t *chunk0, uint64_t n0, void *cnt,
   if ((err = cudaMemsetAsync(cs, 0, sizeof(CertScratch), s)) != cudaSuccess) return err;
   if ((err = cudaMemsetAsync(&ctrl->maxkey, 0, 2 * sizeof(unsigned long long), s)) != cudaSuccess) return err;
   if ((err = cudaMemsetAsync(&ctrl->m_sel, 0xFF, sizeof(uint32_t), s)) != cudaSuccess) return err;
+  // no vertex is planted yet: m' == m cannot hold before the first init
+  if ((err = cudaMemsetAsync(&ctrl->m, 0xFF, sizeof(uint32_t), s)) != cudaSuccess) return err;
   if ((err = cudaMemsetAsync(&ctrl->n_cand, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) return err;
   uint32_t *c32 = static_cast<uint32_t *>(cnt);
   if ((err = launch_degree_sampled_u32(reinterpret_cast<const uint2 *>(chunk0), n0, 0, kChunk0Sample, c32, n, s)) !=
@@ -597,14 +613,17 @@ cudaError_t chunked_select_begin(const uint32_t *chunk0, uint64_t n0, void *cnt,
   k_spec_begin<<<1, 1, 0, s>>>(ctrl);
   note_launch();
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  // without speculation the chunks build the full histogram: start it at zero
+  // histogram mode: the chunks build the full histogram from zero
   return launch_zero(cnt, wide, n, &ctrl->skip[kSkipHist], s);
 }
 
-cudaError_t chunked_select_chunk(const EdgeSpan &chunk, void *cnt, bool wide, uint32_t n, CertScratch *cs,
-                                 Ctrl *ctrl, cudaStream_t s) {
+cudaError_t chunked_select_chunk(const EdgeSpan &chunk, bool first, void *cnt, bool wide, uint32_t n,
+                                 CertScratch *cs, Ctrl *ctrl, cudaStream_t s) {
   cudaError_t err;
-  if ((err = launch_histogram(chunk, cnt, wide, n, &ctrl->skip[kSkipHist], s)) != cudaSuccess) return err;
+  const uint32_t *hub = &ctrl->skip[kSkipHist];
+  if ((err = launch_histogram(chunk, cnt, wide, n, hub, s)) != cudaSuccess) return err;
+  // histogram mode: the first chunk's argmax is m'
+  if (first && (err = launch_hist_argmax(cnt, wide, n, ctrl, hub, s)) != cudaSuccess) return err;
   static std::atomic<unsigned long long> smem_set_certify{0};
   if ((err = ensure_func_attr((const void *)k_degree_certify, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)kCertSmem, smem_set_certify)) != cudaSuccess)
@@ -612,8 +631,8 @@ cudaError_t chunked_select_chunk(const EdgeSpan &chunk, void *cnt, bool wide, ui
   const unsigned gcert =
       clamp_grid((chunk.n_quads + kCertBlock - 1) / kCertBlock,
                  persistent_cap((const void *)k_degree_certify, kCertBlock, kCertSmem));
-  k_degree_certify<<<gcert, kCertBlock, kCertSmem, s>>>(chunk.quads, chunk.n_quads, chunk.head, chunk.tail, n, cs, ctrl, 0,
-                                                 nullptr, 0u);
+  k_degree_certify<<<gcert, kCertBlock, kCertSmem, s>>>(chunk.quads, chunk.n_quads, chunk.head, chunk.tail, n, cs,
+                                                        ctrl, 0, nullptr, 0u);
   note_launch();
   return cudaGetLastError();
 }
@@ -626,13 +645,16 @@ cudaError_t chunked_select_end(const EdgeSpan &all, void *cnt, bool wide, uint32
   k_spec_end<<<1, 1, 0, s>>>(ctrl);
   note_launch();
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  // no speculation: the chunks built the full histogram
+  // histogram mode: the chunks built the full histogram
   if ((err = launch_hist_argmax(cnt, wide, n, ctrl, &ctrl->skip[kSkipHist], s)) != cudaSuccess) return err;
-  // speculation without a certificate: the full histogram over all edges now
+  // hub mode without a certificate: the full histogram over all edges now
   const uint32_t *full = &ctrl->skip[kSkipFullHist];
   if ((err = launch_zero(cnt, wide, n, full, s)) != cudaSuccess) return err;
   if ((err = launch_histogram(all, cnt, wide, n, full, s)) != cudaSuccess) return err;
-  return launch_hist_argmax(cnt, wide, n, ctrl, full, s);
+  if ((err = launch_hist_argmax(cnt, wide, n, ctrl, full, s)) != cudaSuccess) return err;
+  k_spec_check<<<1, 1, 0, s>>>(ctrl);
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_initial_push(uint32_t *P, uint32_t n, const uint32_t *push_buf, uint32_t push_cap,

@@ -289,8 +289,10 @@ def _chunked_case(kind):
     C = 1 << 24
     if kind == "rmat":  # dominant hub, certified from the first chunk: the speculation holds
         return 1 << 20, graphgen.rmat(20, 3 * C + 77, 61, scramble=True)
-    if kind == "er":  # no hub: every chunk feeds the full histogram
+    if kind == "er":  # no hub: histogram mode, the first chunk's argmax is not m (rerun)
         return 1 << 22, graphgen.er(1 << 22, 2 * C + 5, 62)
+    if kind == "grid":  # no hub: histogram mode, the first chunk's argmax is m (the hooking holds)
+        return 4096 * 2560, graphgen.grid(4096, 2560, 64)
     n = 1 << 20
     e = graphgen.er(n, 2 * C + 123, 63)  # background: degree about 64
     rng = np.random.default_rng(64)
@@ -312,7 +314,7 @@ def _chunked_case(kind):
     return n, e
 
 
-@pytest.mark.parametrize("kind", ["rmat", "er", "late_hub", "two_hubs"])
+@pytest.mark.parametrize("kind", ["rmat", "er", "grid", "late_hub", "two_hubs"])
 @pytest.mark.parametrize("flt", [cc.CC_FILTER_AUTO, cc.CC_FILTER_BITMAP])
 def test_run_host_chunked_selection(kind, flt):
     n, e = _chunked_case(kind)
