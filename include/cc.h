@@ -199,6 +199,15 @@ CC_API cc_status cc_run_csr(cc_graph *g, const uint64_t *offsets_dev, const uint
 CC_API cc_status cc_run_host(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges,
                       uint32_t *L_out_host, cc_stream_t stream);
 
+/* cc_run_host without the final wait: returns once every copy and kernel is
+ * enqueued on `stream` (argument errors are still returned at once). The
+ * caller keeps edges_host unchanged and does not read L_out_host until a
+ * synchronising call on the handle (cc_sync) has returned; that call
+ * reports any device error. Several handles, each on its own stream, then
+ * overlap one graph's copies with another's kernels and label read-back. */
+CC_API cc_status cc_run_host_async(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges,
+                            uint32_t *L_out_host, cc_stream_t stream);
+
 /* cc_run_host on compactly encoded edges (Section V sends ids in the fewest
  * whole bytes that hold them): each id takes id_bytes little-endian bytes,
  * an edge is u then v, 2 * id_bytes bytes per edge, no padding. id_bytes is
@@ -209,6 +218,10 @@ CC_API cc_status cc_run_host(cc_graph *g, const uint32_t *edges_host, uint64_t n
  * CC_ERR_INVALID_ARGUMENT for another id_bytes or n_vertices > 2^24 with 3. */
 CC_API cc_status cc_run_host_packed(cc_graph *g, const uint8_t *edges_host, uint64_t n_edges, int32_t id_bytes,
                              uint32_t *L_out_host, cc_stream_t stream);
+
+/* cc_run_host_packed without the final wait, as cc_run_host_async. */
+CC_API cc_status cc_run_host_packed_async(cc_graph *g, const uint8_t *edges_host, uint64_t n_edges,
+                                   int32_t id_bytes, uint32_t *L_out_host, cc_stream_t stream);
 
 /* Incremental union: applies n_edges new pairs to the live P without
  * re-initialisation, exactly as the edge pass does (JT processes edges in any

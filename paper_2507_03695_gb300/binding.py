@@ -102,6 +102,8 @@ def lib():
             "cc_run": (_i32, [_ptr, _ptr, _u64, _ptr, _ptr]),
             "cc_run_host": (_i32, [_ptr, _ptr, _u64, _ptr, _ptr]),
             "cc_run_host_packed": (_i32, [_ptr, _ptr, _u64, _i32, _ptr, _ptr]),
+            "cc_run_host_async": (_i32, [_ptr, _ptr, _u64, _ptr, _ptr]),
+            "cc_run_host_packed_async": (_i32, [_ptr, _ptr, _u64, _i32, _ptr, _ptr]),
             "cc_run_csr": (_i32, [_ptr, _ptr, _ptr, _u64, _ptr, _ptr]),
             "cc_stream_insert": (_i32, [_ptr, _ptr, _u64, _ptr]),
             "cc_labels": (_i32, [_ptr, _ptr, _ptr]),
@@ -226,6 +228,19 @@ def cc_run_host_packed(g: int, edges_host, n_edges: int, id_bytes: int, L_out_ho
 def cc_run_host(g: int, edges_host, n_edges: int | None = None, L_out_host=None, stream=None) -> None:
     _check(lib().cc_run_host(g, _addr(edges_host), _count_pairs(edges_host, n_edges), _addr(L_out_host),
                              _stream(stream)), "cc_run_host")
+
+
+def cc_run_host_async(g: int, edges_host, n_edges: int | None = None, L_out_host=None, stream=None) -> None:
+    """As cc_run_host without the final wait: keep edges_host and L_out_host
+    untouched until cc_sync(g) has returned."""
+    _check(lib().cc_run_host_async(g, _addr(edges_host), _count_pairs(edges_host, n_edges), _addr(L_out_host),
+                                   _stream(stream)), "cc_run_host_async")
+
+
+def cc_run_host_packed_async(g: int, edges_host, n_edges: int, id_bytes: int, L_out_host=None,
+                             stream=None) -> None:
+    _check(lib().cc_run_host_packed_async(g, _addr(edges_host), int(n_edges), int(id_bytes), _addr(L_out_host),
+                                          _stream(stream)), "cc_run_host_packed_async")
 
 
 def cc_stream_insert(g: int, edges, n_edges: int | None = None, stream=None) -> None:

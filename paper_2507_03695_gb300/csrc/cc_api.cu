@@ -417,8 +417,10 @@ cc_status cc_run(cc_graph *g, const uint32_t *edges_dev, uint64_t n_edges, uint3
 
 // The work of cc_run_host; id_bytes 0: edges_host holds uint32 pairs;
 // 3: packed ids, copied into the two slots in turn and unpacked on s.
+// wait: synchronise at the end and report device errors (cc_run_host);
+// otherwise return once everything is enqueued (cc_run_host_async).
 static cc_status run_host_impl(cc_graph *g, const void *edges_host, uint64_t n_edges, int id_bytes, uint32_t *L_out_host,
-                        cc_stream_t stream) {
+                        cc_stream_t stream, bool wait) {
   if (!g) return CC_ERR_INVALID_ARGUMENT;
   if (n_edges && !edges_host) return CC_ERR_INVALID_ARGUMENT;
   if (n_edges > g->capacity) return CC_ERR_TOO_LARGE;
@@ -504,7 +506,7 @@ static cc_status run_host_impl(cc_graph *g, const void *edges_host, uint64_t n_e
   if (L_out_host)
     CC_TRY(cudaMemcpyAsync(L_out_host, g->label_dev, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
   g->ncomp_fresh = true;
-  return fetch_ctrl(g, s);
+  return wait ? fetch_ctrl(g, s) : CC_OK;
 }
 
 cc_status cc_run_csr(cc_graph *g, const uint64_t *offsets_dev, const uint32_t *neighbors_dev, uint64_t n_entries,
@@ -553,13 +555,18 @@ cc_status cc_run_csr(cc_graph *g, const uint64_t *offsets_dev, const uint32_t *n
 
 cc_status cc_run_host(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges, uint32_t *L_out_host,
                       cc_stream_t stream) {
-  return run_host_impl(g, edges_host, n_edges, 0, L_out_host, stream);
+  return run_host_impl(g, edges_host, n_edges, 0, L_out_host, stream, true);
 }
 
-cc_status cc_run_host_packed(cc_graph *g, const uint8_t *edges_host, uint64_t n_edges, int32_t id_bytes,
-                             uint32_t *L_out_host, cc_stream_t stream) {
+cc_status cc_run_host_async(cc_graph *g, const uint32_t *edges_host, uint64_t n_edges, uint32_t *L_out_host,
+                            cc_stream_t stream) {
+  return run_host_impl(g, edges_host, n_edges, 0, L_out_host, stream, false);
+}
+
+static cc_status run_host_packed_impl(cc_graph *g, const uint8_t *edges_host, uint64_t n_edges, int32_t id_bytes,
+                                      uint32_t *L_out_host, cc_stream_t stream, bool wait) {
   if (!g) return CC_ERR_INVALID_ARGUMENT;
-  if (id_bytes == 4) return run_host_impl(g, edges_host, n_edges, 0, L_out_host, stream);
+  if (id_bytes == 4) return run_host_impl(g, edges_host, n_edges, 0, L_out_host, stream, wait);
   if (id_bytes != 3 || g->n > (1ULL << 24)) return CC_ERR_INVALID_ARGUMENT;
   if (n_edges && !edges_host) return CC_ERR_INVALID_ARGUMENT;
   if (n_edges > g->capacity) return CC_ERR_TOO_LARGE;
@@ -571,7 +578,17 @@ cc_status cc_run_host_packed(cc_graph *g, const uint8_t *edges_host, uint64_t n_
       CC_TRY(cudaEventCreateWithFlags(&g->pk_ev[i], cudaEventDisableTiming));
     }
   }
-  return run_host_impl(g, edges_host, n_edges, 3, L_out_host, stream);
+  return run_host_impl(g, edges_host, n_edges, 3, L_out_host, stream, wait);
+}
+
+cc_status cc_run_host_packed(cc_graph *g, const uint8_t *edges_host, uint64_t n_edges, int32_t id_bytes,
+                             uint32_t *L_out_host, cc_stream_t stream) {
+  return run_host_packed_impl(g, edges_host, n_edges, id_bytes, L_out_host, stream, true);
+}
+
+cc_status cc_run_host_packed_async(cc_graph *g, const uint8_t *edges_host, uint64_t n_edges, int32_t id_bytes,
+                                   uint32_t *L_out_host, cc_stream_t stream) {
+  return run_host_packed_impl(g, edges_host, n_edges, id_bytes, L_out_host, stream, false);
 }
 
 cc_status cc_stream_insert(cc_graph *g, const uint32_t *edges_dev, uint64_t n_edges, cc_stream_t stream) {

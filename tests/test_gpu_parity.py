@@ -283,6 +283,49 @@ def test_run_host_buffers(mode, select):
             cc.cc_run_host(g.h, host, E + 1, L)
 
 
+def test_run_host_async():
+    """Two handles on two streams: both host runs are enqueued before either
+    is waited for (one of them packed on the second round). Labels and m
+    equal the oracle's; an out-of-range id is reported by cc_sync, not by the
+    enqueueing call."""
+    n1, e1 = 1 << 20, graphgen.rmat(20, (1 << 24) + 12345, 92, scramble=True)
+    n2, e2 = 512 * 512, graphgen.grid(512, 512, 93)
+    h1 = torch.from_numpy(e1.view(np.int32)).pin_memory()
+    p1 = torch.from_numpy(graphgen.pack_ids(e1, 3)).pin_memory()
+    h2 = torch.from_numpy(e2.view(np.int32)).pin_memory()
+    L1 = torch.empty(n1, dtype=torch.int32).pin_memory()
+    L2 = torch.empty(n2, dtype=torch.int32).pin_memory()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    want1, want2 = oracle.min_labels(n1, e1), oracle.min_labels(n2, e2)
+    with cc.Graph(n1, len(e1)) as g1, cc.Graph(n2, len(e2)) as g2:
+        for rnd in range(2):
+            L1.fill_(-1)
+            L2.fill_(-1)
+            if rnd == 0:
+                cc.cc_run_host_async(g1.h, h1, None, L1, s1)
+            else:
+                cc.cc_run_host_packed_async(g1.h, p1, len(e1), 3, L1, s1)
+            cc.cc_run_host_async(g2.h, h2, None, L2, s2)
+            cc.cc_sync(g1.h)
+            cc.cc_sync(g2.h)
+            np.testing.assert_array_equal(L1.numpy().view(np.uint32), want1)
+            np.testing.assert_array_equal(L2.numpy().view(np.uint32), want2)
+            assert g1.root_vertex() == oracle.max_degree_vertex(n1, e1)
+            assert g2.root_vertex() == oracle.max_degree_vertex(n2, e2)
+        bad = e2.copy()
+        bad[1000, 1] = n2 + 5
+        hb = torch.from_numpy(bad.view(np.int32)).pin_memory()
+        cc.cc_run_host_async(g2.h, hb, None, L2, s2)
+        with pytest.raises(cc.CCError) as ei:
+            cc.cc_sync(g2.h)
+        assert ei.value.status == cc.CC_ERR_OUT_OF_RANGE
+        cc.cc_run_host_async(g2.h, h2, None, L2, s2)  # the handle is usable again
+        cc.cc_sync(g2.h)
+        np.testing.assert_array_equal(L2.numpy().view(np.uint32), want2)
+        with pytest.raises(cc.CCError):
+            cc.cc_run_host_async(g2.h, h2, len(e2) + 1, L2, s2)  # over capacity: at once
+
+
 def _chunked_case(kind):
     """Host inputs of several 2^24-edge copy chunks, built so that each route
     of the chunked exact root selection in cc_run_host is taken."""
