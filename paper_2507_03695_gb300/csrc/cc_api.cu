@@ -407,7 +407,7 @@ cc_status cc_run(cc_graph *g, const uint32_t *edges_dev, uint64_t n_edges, uint3
   const uint32_t *zsel = (Z && !g->z_forced) ? &g->ctrl->cert : nullptr;
   record(g, 2, s);
   CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), span, g->P, n, g->ctrl,
-                              nullptr, s, Z, zsel));
+                              nullptr, s, Z, zsel, false, nullptr, exact ? &g->ctrl->cert : nullptr));
   record(g, 3, s);
   CC_TRY(cc::launch_flatten(g->rf, g->opt.label_space, g->P, n, L_out_dev, g->ctrl, s));
   record(g, 4, s);

@@ -232,6 +232,14 @@ __device__ __forceinline__ UniteResult unite(uint32_t *S, uint32_t cu, uint32_t 
 // push() and drain() together. With a zero-tree bitmap Z (below), an edge that
 // ends in the tree of name 0 marks both endpoint names in it.
 constexpr int kRing = 64;
+// When at least this many lanes keep their edge, the warp resolves them in
+// place: the queue would only add its shared-memory round trip. This pays
+// where most edges reach a search for most of the pass (graphs without a
+// hub, and parent arrays beyond L2 behind the zero-tree bitmap); on a
+// certified hub graph whose P fits L2 it cost a few percent, so the plain
+// edge pass keeps the queue there (kNeverDirect).
+constexpr uint32_t kDirectMin = 28;
+constexpr uint32_t kNeverDirect = 33;
 
 // The zero-tree bitmap: bit c set means the vertex named c belongs to the
 // tree of name 0 (the planted vertex m under R). Bits are only ever set, and
@@ -270,12 +278,14 @@ struct WarpRing {
   uint32_t *log;  // changed-root log, or null
   uint32_t head, tail;
   uint32_t lane, lt_mask;
+  uint32_t direct_min;  // kDirectMin, or kNeverDirect for the queue only
 
   // ring storage for this warp out of 4 * kRing words per warp
   __device__ __forceinline__ void init(uint32_t *smem_words, uint32_t *zero_tree = nullptr,
-                                       uint32_t *root_log = nullptr) {
+                                       uint32_t *root_log = nullptr, uint32_t direct = kDirectMin) {
     Z = zero_tree;
     log = root_log;
+    direct_min = direct;
     const uint32_t wid = threadIdx.x >> 5;
     cu = smem_words + wid * (4 * kRing);
     pu = cu + kRing;
@@ -290,27 +300,41 @@ struct WarpRing {
   __device__ __forceinline__ void push(uint32_t *S, bool keep, uint32_t a, uint32_t pa, uint32_t b,
                                        uint32_t pb) {
     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
-    if (keep) {
-      const uint32_t slot = (tail + __popc(bal & lt_mask)) & (kRing - 1);
-      cu[slot] = a;
-      pu[slot] = pa;
-      cv[slot] = b;
-      pv[slot] = pb;
-    }
-    tail += __popc(bal);
-    if (tail - head >= 32u) {
-      __syncwarp();
-      const uint32_t slot = (head + lane) & (kRing - 1);
-      const uint32_t sa = cu[slot], spa = pu[slot], sb = cv[slot], spb = pv[slot];
-      __syncwarp();
-      const UniteResult res = unite<kCG>(S, sa, spa, sb, spb);
-      if (res.zero && Z) {
-        zset(Z, sa);
-        zset(Z, sb);
+    // one call of unite() serves both routes: a second inlined copy cost
+    // the plain pass a register spill
+    const bool direct = (uint32_t)__popc(bal) >= direct_min;  // warp-uniform
+    bool run = direct;
+    bool mine = keep;
+    if (!direct) {
+      if (keep) {
+        const uint32_t slot = (tail + __popc(bal & lt_mask)) & (kRing - 1);
+        cu[slot] = a;
+        pu[slot] = pa;
+        cv[slot] = b;
+        pv[slot] = pb;
       }
-      if (log) log_hooks_warp(log, res.hooked, lane, lt_mask);
-      head += 32u;
+      tail += __popc(bal);
+      if (tail - head >= 32u) {
+        __syncwarp();
+        const uint32_t slot = (head + lane) & (kRing - 1);
+        a = cu[slot];
+        pa = pu[slot];
+        b = cv[slot];
+        pb = pv[slot];
+        __syncwarp();
+        head += 32u;
+        run = true;
+        mine = true;
+      }
     }
+    if (!run) return;
+    UniteResult res{false, kNoHook};
+    if (mine) res = unite<kCG>(S, a, pa, b, pb);
+    if (res.zero && Z) {
+      zset(Z, a);
+      zset(Z, b);
+    }
+    if (log) log_hooks_warp(log, res.hooked, lane, lt_mask);
   }
 
   template <bool kCG = false>

@@ -180,7 +180,7 @@ cudaError_t launch_argmax_u32(const uint32_t *cnt, uint32_t n, Ctrl *ctrl, cudaS
 cudaError_t launch_edge_pass(bool rf, int filter, int ept, int block, const EdgeSpan &e, uint32_t *P,
                              uint32_t n, Ctrl *ctrl, const uint32_t *skip, cudaStream_t s,
                              uint32_t *Z = nullptr, const uint32_t *zsel = nullptr, bool one_shot = false,
-                             uint32_t *log = nullptr);
+                             uint32_t *log = nullptr, const uint32_t *hub = nullptr);
 // Sets *reject (ctrl->reject when null) and the range error bit when an id is >= n.
 cudaError_t launch_validate(const EdgeSpan &e, uint32_t n, Ctrl *ctrl, cudaStream_t s, uint32_t *reject = nullptr);
 cudaError_t launch_flatten(bool rf, int label_space, uint32_t *P, uint32_t n, uint32_t *L, Ctrl *ctrl,

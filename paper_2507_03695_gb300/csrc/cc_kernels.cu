@@ -148,7 +148,8 @@ __global__ void __launch_bounds__(512) k_edge_pass_filtered(const uint4 *__restr
                                                             const uint2 *tail, uint32_t *P,
                                                             uint32_t n, Ctrl *ctrl,
                                                             const uint32_t *skip, uint32_t *Z,
-                                                            const uint32_t *zsel, uint32_t *log) {
+                                                            const uint32_t *zsel, uint32_t *log,
+                                                            const uint32_t *hub) {
   extern __shared__ uint32_t ring_smem[];
   if (skip && ld_volatile_u32(skip)) return;
   if (zsel && ((ld_volatile_u32(zsel) != 0u) != kZ)) return;
@@ -156,7 +157,10 @@ __global__ void __launch_bounds__(512) k_edge_pass_filtered(const uint4 *__restr
   uint32_t *const S = slots<F>(P);
   const uint64_t pol = policy_evict_first();
   WarpRing ring;
-  ring.init(ring_smem, kZ ? Z : nullptr, log);
+  // hub: nonzero when this run's selection certified a hub (the plain
+  // instance then always queues; see kDirectMin)
+  const bool queue_only = !kZ && hub && ld_volatile_u32(hub) != 0u;
+  ring.init(ring_smem, kZ ? Z : nullptr, log, queue_only ? kNeverDirect : kDirectMin);
   const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (t == 0 && head) single_edge(P, fn, head, n, ctrl, log);
@@ -527,7 +531,7 @@ constexpr uint64_t kMinWaves = 8;
 template <class F, int Q>
 cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, uint32_t n, Ctrl *ctrl,
                         const uint32_t *skip, uint32_t *Z, const uint32_t *zsel, bool one_shot, uint32_t *log,
-                        cudaStream_t s) {
+                        const uint32_t *hub, cudaStream_t s) {
   const uint64_t per_block = (uint64_t)block * Q;
   // At least kMinWaves grid iterations per thread: when a whole graph fits
   // one wave, every edge reads P before any hooking and duplicate hub edges
@@ -544,12 +548,13 @@ cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, u
     if (Z) {  // the zero-tree instance (alone, or chosen on the device by *zsel)
       const unsigned g = clamp_grid(want, one_shot ? cap_big : persistent_cap((const void *)k_edge_pass_filtered<F, Q, true>, block, smem));
       k_edge_pass_filtered<F, Q, true><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
-                                                              skip, Z, zsel, log); note_launch();
+                                                              skip, Z, zsel, log, hub); note_launch();
     }
     if (!Z || zsel) {
       const unsigned g = clamp_grid(want, one_shot ? cap_big : persistent_cap((const void *)k_edge_pass_filtered<F, Q, false>, block, smem));
       k_edge_pass_filtered<F, Q, false><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
-                                                               skip, nullptr, Z ? zsel : nullptr, log); note_launch();
+                                                               skip, nullptr, Z ? zsel : nullptr, log, hub);
+      note_launch();
     }
   } else {
     const void *k = (const void *)k_edge_pass_direct<F, Q>;
@@ -563,23 +568,23 @@ cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, u
 template <class F>
 cudaError_t edge_pass_f(int filter, int ept, int block, const EdgeSpan &e, uint32_t *P, uint32_t n,
                         Ctrl *ctrl, const uint32_t *skip, uint32_t *Z, const uint32_t *zsel, bool one_shot,
-                        uint32_t *log, cudaStream_t s) {
+                        uint32_t *log, const uint32_t *hub, cudaStream_t s) {
   switch (ept) {
-    case 2: return edge_pass_q<F, 1>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, s);
-    case 8: return edge_pass_q<F, 4>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, s);
-    default: return edge_pass_q<F, 2>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, s);
+    case 2: return edge_pass_q<F, 1>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, hub, s);
+    case 8: return edge_pass_q<F, 4>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, hub, s);
+    default: return edge_pass_q<F, 2>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, hub, s);
   }
 }
 }  // namespace
 
 cudaError_t launch_edge_pass(bool rf, int filter, int ept, int block, const EdgeSpan &e, uint32_t *P,
                              uint32_t n, Ctrl *ctrl, const uint32_t *skip, cudaStream_t s, uint32_t *Z,
-                             const uint32_t *zsel, bool one_shot, uint32_t *log) {
+                             const uint32_t *zsel, bool one_shot, uint32_t *log, const uint32_t *hub) {
   if (block != 128 && block != 256 && block != 512) block = 256;
   if (e.n_quads == 0 && !e.head && !e.tail) return cudaSuccess;
   if (log) filter = 1;  // the log is kept by the filtered form
-  return rf ? edge_pass_f<RootR>(filter, ept, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, s)
-            : edge_pass_f<RootId>(filter, ept, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, s);
+  return rf ? edge_pass_f<RootR>(filter, ept, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, hub, s)
+            : edge_pass_f<RootId>(filter, ept, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, hub, s);
 }
 
 cudaError_t launch_validate(const EdgeSpan &e, uint32_t n, Ctrl *ctrl, cudaStream_t s, uint32_t *reject) {
