@@ -10,6 +10,7 @@
 // instead of two. max_degree() of Algorithm 4 is read from the offsets (the
 // row length), as the paper does.
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "cc_device.cuh"
@@ -33,10 +34,12 @@ __device__ __forceinline__ uint64_t row_len(const uint64_t *off, uint32_t v) {
 }
 
 // Longest row, and a check of the offsets: off[0] == 0, off[n] == n_entries,
-// never decreasing (violations set kErrFormat).
+// never decreasing (violations set kErrFormat). One pass also keeps the
+// argmax key (min(length, 2^32 - 1) << 32) | ~v, which is exact unless a row
+// reaches 2^32 - 1 entries (then k_csr_minid settles the smallest id).
 __global__ void __launch_bounds__(256) k_csr_maxlen(const uint64_t *__restrict__ off, uint32_t n,
                                                     uint64_t n_entries, Ctrl *ctrl) {
-  unsigned long long best = 0;
+  unsigned long long best = 0, key = 0;
   bool bad = false;
   for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
        v += (uint64_t)gridDim.x * blockDim.x) {
@@ -44,16 +47,25 @@ __global__ void __launch_bounds__(256) k_csr_maxlen(const uint64_t *__restrict__
     bad |= b < a;
     const uint64_t len = b > a ? b - a : 0u;
     best = len > best ? len : best;
+    const uint64_t l32 = len < 0xFFFFFFFFull ? len : 0xFFFFFFFFull;
+    const unsigned long long k = (l32 << 32) | (uint32_t)~(uint32_t)v;
+    key = k > key ? k : key;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) bad |= off[0] != 0u || off[n] != n_entries;
   if (bad) set_err(ctrl, kErrFormat);
   best = warp_max_u64(best);
-  if ((threadIdx.x & 31) == 0 && best) atomicMax(&ctrl->maxcnt, best);
+  key = warp_max_u64(key);
+  if ((threadIdx.x & 31) == 0) {
+    if (best) atomicMax(&ctrl->maxcnt, best);
+    if (key) atomicMax(&ctrl->maxkey, key);
+  }
 }
 
-// Smallest vertex with the longest row; then m for the init kernel.
+// Smallest vertex with the longest row, when that row has 2^32 - 1 entries
+// or more (the packed key cannot order such lengths); otherwise nothing.
 __global__ void __launch_bounds__(256) k_csr_minid(const uint64_t *__restrict__ off, uint32_t n, Ctrl *ctrl) {
   const unsigned long long mx = *(volatile unsigned long long *)&ctrl->maxcnt;
+  if (mx < 0xFFFFFFFFull) return;
   uint32_t best = 0xFFFFFFFFu;
   for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
        v += (uint64_t)gridDim.x * blockDim.x)
@@ -62,7 +74,9 @@ __global__ void __launch_bounds__(256) k_csr_minid(const uint64_t *__restrict__ 
   if ((threadIdx.x & 31) == 0 && best != 0xFFFFFFFFu) atomicMin(&ctrl->m_sel, best);
 }
 
-__global__ void k_csr_finalize_m(Ctrl *ctrl) { ctrl->maxkey = (unsigned long long)(uint32_t)~ctrl->m_sel; }
+__global__ void k_csr_finalize_m(Ctrl *ctrl) {
+  if (ctrl->maxcnt >= 0xFFFFFFFFull) ctrl->maxkey = (unsigned long long)(uint32_t)~ctrl->m_sel;
+}
 
 // The row that holds entry t * tile: the largest r with off[r] <= t * tile
 // (one binary search per tile, all tiles in parallel).
@@ -152,7 +166,8 @@ uint64_t csr_tiles(uint64_t n_entries) { return (n_entries + kCsrTile - 1) / kCs
 
 cudaError_t launch_csr_root_select(const uint64_t *off, uint32_t n, uint64_t n_entries, Ctrl *ctrl, cudaStream_t s) {
   cudaError_t err;
-  if ((err = cudaMemsetAsync(&ctrl->maxcnt, 0, sizeof(unsigned long long), s)) != cudaSuccess) return err;
+  static_assert(offsetof(Ctrl, maxcnt) == offsetof(Ctrl, maxkey) + sizeof(unsigned long long), "reset together");
+  if ((err = cudaMemsetAsync(&ctrl->maxkey, 0, 2 * sizeof(unsigned long long), s)) != cudaSuccess) return err;
   if ((err = cudaMemsetAsync(&ctrl->m_sel, 0xFF, sizeof(uint32_t), s)) != cudaSuccess) return err;
   const unsigned g = clamp_grid(((uint64_t)n + 255) / 256, persistent_cap((const void *)k_csr_maxlen, 256, 0));
   k_csr_maxlen<<<g, 256, 0, s>>>(off, n, n_entries, ctrl);
@@ -165,7 +180,7 @@ cudaError_t launch_csr_root_select(const uint64_t *off, uint32_t n, uint64_t n_e
 }
 
 cudaError_t launch_csr_check(const uint64_t *off, uint32_t n, uint64_t n_entries, Ctrl *ctrl, cudaStream_t s) {
-  // the offsets check alone (the longest row goes to maxcnt, unused)
+  // the offsets check alone (the longest row goes to maxcnt and maxkey, unused)
   const unsigned g = clamp_grid(((uint64_t)n + 255) / 256, persistent_cap((const void *)k_csr_maxlen, 256, 0));
   k_csr_maxlen<<<g, 256, 0, s>>>(off, n, n_entries, ctrl);
   note_launch();

@@ -203,19 +203,31 @@ __global__ void __launch_bounds__(256) k_select_candidates(const uint32_t *__res
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  // rank: kCertTop rounds of a block maximum over the owners, each round
-  // excluding the keys already taken (keys are distinct: they hold the id)
-  unsigned long long taken = ~0ULL;  // the previous round's winner; keys below it remain
-  for (uint32_t r = 0; r < kCertTop; ++r) {
-    unsigned long long best = 0;
-    for (uint32_t b = threadIdx.x; b < kCertBuckets; b += blockDim.x) {
-      const unsigned long long o = __ldcg(&cs->owner[b]);
-      if (o < taken && o > best) best = o;
+  // rank: each thread keeps the kCertTop best owners of its buckets (one pass
+  // over them), then kCertTop rounds of a block maximum over the threads'
+  // best untaken keys (keys are distinct: they hold the id)
+  unsigned long long loc[kCertTop];
+#pragma unroll
+  for (uint32_t k = 0; k < kCertTop; ++k) loc[k] = 0ULL;
+  for (uint32_t b = threadIdx.x; b < kCertBuckets; b += blockDim.x) {
+    unsigned long long o = __ldcg(&cs->owner[b]);
+#pragma unroll
+    for (uint32_t k = 0; k < kCertTop; ++k) {  // insertion into the sorted list
+      const unsigned long long hi = o > loc[k] ? o : loc[k];
+      o = o > loc[k] ? loc[k] : o;
+      loc[k] = hi;
     }
-    best = block_max_u64(best);
+  }
+  uint32_t next = 0;  // loc[next] is this thread's best untaken key
+  for (uint32_t r = 0; r < kCertTop; ++r) {
+    unsigned long long mine = 0ULL;
+#pragma unroll
+    for (uint32_t k = 0; k < kCertTop; ++k)
+      if (k == next) mine = loc[k];
+    const unsigned long long best = block_max_u64(mine);
     if (best == 0ULL) break;  // uniform: fewer owners than kCertTop
     if (threadIdx.x == 0) cs->top[r] = best;
-    taken = best;
+    if (mine == best) ++next;
   }
 }
 
