@@ -114,8 +114,10 @@ def kernel_source_sha() -> str:
         h.update(f.read())
     with open(os.path.join(csrc, "cc_kernels.cu")) as f:
         text = f.read()
-    start = text.index("__global__ void __launch_bounds__(512) k_edge_pass_filtered(")
+    start = text.index("k_edge_pass_filtered(const uint4")  # the definition, not a launch
     start = text.rindex("template", 0, start)
+    grab = text.index("constexpr uint64_t kGrab")  # the dynamic schedule's claim size
+    h.update(text[grab:text.index("\n", grab)].encode())
     depth, i = 0, text.index("{", start)
     while True:
         if text[i] == "{":

@@ -407,7 +407,7 @@ cc_status cc_run(cc_graph *g, const uint32_t *edges_dev, uint64_t n_edges, uint3
   const uint32_t *zsel = (Z && !g->z_forced) ? &g->ctrl->cert : nullptr;
   record(g, 2, s);
   CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), span, g->P, n, g->ctrl,
-                              nullptr, s, Z, zsel, false, nullptr, exact ? &g->ctrl->cert : nullptr));
+                              nullptr, s, Z, zsel, false, nullptr, exact ? &g->ctrl->cert : nullptr, true));
   record(g, 3, s);
   CC_TRY(cc::launch_flatten(g->rf, g->opt.label_space, g->P, n, L_out_dev, g->ctrl, s));
   record(g, 4, s);
@@ -475,7 +475,7 @@ static cc_status run_host_impl(cc_graph *g, const void *edges_host, uint64_t n_e
     // every chunk is hooked as it lands, under m' when m is still unknown
     if (chunked && off == 0) CC_TRY(cc::launch_init(true, g->P, n, g->ctrl, cc::kMFromPackedMax, 0u, s));
     CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), chunk, g->P, n, g->ctrl, nullptr,
-                                s, Zf));
+                                s, Zf, nullptr, false, nullptr, nullptr, true));
   }
   const cc::EdgeSpan all = cc::split_edges(g->staging, n_edges);
   if (chunked) {
@@ -488,7 +488,7 @@ static cc_status run_host_impl(cc_graph *g, const void *edges_host, uint64_t n_e
     // forgets bits: an empty bitmap is always valid)
     if (Zf) CC_TRY(cudaMemsetAsync(Zf, 0, g->z_bytes, s));
     CC_TRY(cc::launch_edge_pass(true, eff_filter(g), eff_ept(g), eff_block(g), all, g->P, n, g->ctrl, held, s,
-                                g->z, Zf ? nullptr : &g->ctrl->cert));
+                                g->z, Zf ? nullptr : &g->ctrl->cert, false, nullptr, nullptr, true));
   } else if (select) {
     if (id_bytes != 3) {  // (packed chunks were unpacked on s already)
       CC_TRY(cudaEventRecord(g->copy_ev, g->copy_stream));
@@ -499,7 +499,7 @@ static cc_status run_host_impl(cc_graph *g, const void *edges_host, uint64_t n_e
     if (st != CC_OK) return st;
     CC_TRY(cc::launch_init(g->rf, g->P, n, g->ctrl, m_src, hint, s));
     CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), all, g->P, n, g->ctrl,
-                                nullptr, s, Zf));
+                                nullptr, s, Zf, nullptr, false, nullptr, nullptr, true));
   }
   CC_TRY(cc::launch_flatten(g->rf, g->opt.label_space, g->P, n, L_out_host ? g->label_dev : nullptr,
                             g->ctrl, s));
@@ -603,8 +603,10 @@ cc_status cc_stream_insert(cc_graph *g, const uint32_t *edges_dev, uint64_t n_ed
   CC_TRY(cc::launch_validate(span, (uint32_t)g->n, g->ctrl, s));
   uint32_t *Z = (g->z && (g->z_forced || g->z_auto_ok)) ? g->z : nullptr;
   const uint32_t *zsel = (Z && !g->z_forced) ? &g->ctrl->cert : nullptr;
+  // the last run's certificate (when its exact selection ran) picks the form
+  const uint32_t *hub = g->z_auto_ok ? &g->ctrl->cert : nullptr;
   CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), span, g->P,
-                              (uint32_t)g->n, g->ctrl, &g->ctrl->reject, s, Z, zsel));
+                              (uint32_t)g->n, g->ctrl, &g->ctrl->reject, s, Z, zsel, false, nullptr, hub, true));
   g->ncomp_fresh = false;
   return CC_OK;
 }

@@ -38,6 +38,7 @@ struct alignas(128) Ctrl {
   uint32_t cert;              // root select: 1 when the candidate pass proved the argmax
   uint32_t skip[3];           // chunked root select: skip words (kSkip*), set on the device
   unsigned long long stats[4];  // optional edge-pass counters
+  unsigned long long work;      // edge pass, dynamic schedule: steps claimed so far
 };
 static_assert(offsetof(Ctrl, q_u) % 8 == 0, "the query pair is loaded with an 8-byte access");
 static_assert(offsetof(Ctrl, maxkey) % 8 == 0 && offsetof(Ctrl, ncomp) % 8 == 0, "64-bit atomics");
@@ -180,7 +181,9 @@ cudaError_t launch_argmax_u32(const uint32_t *cnt, uint32_t n, Ctrl *ctrl, cudaS
 cudaError_t launch_edge_pass(bool rf, int filter, int ept, int block, const EdgeSpan &e, uint32_t *P,
                              uint32_t n, Ctrl *ctrl, const uint32_t *skip, cudaStream_t s,
                              uint32_t *Z = nullptr, const uint32_t *zsel = nullptr, bool one_shot = false,
-                             uint32_t *log = nullptr, const uint32_t *hub = nullptr);
+                             uint32_t *log = nullptr, const uint32_t *hub = nullptr, bool dyn = false);
+// dyn: warps claim their edges from a counter in ctrl (reset on s before the
+// launch), so at most one dynamic edge pass per Ctrl may be in flight.
 // Sets *reject (ctrl->reject when null) and the range error bit when an id is >= n.
 cudaError_t launch_validate(const EdgeSpan &e, uint32_t n, Ctrl *ctrl, cudaStream_t s, uint32_t *reject = nullptr);
 cudaError_t launch_flatten(bool rf, int label_space, uint32_t *P, uint32_t n, uint32_t *L, Ctrl *ctrl,

@@ -139,40 +139,48 @@ __global__ void __launch_bounds__(512) k_edge_pass_direct(const uint4 *__restric
 // P into L2 hits on Z. Bits are set when a parent value of 0 is read and when
 // an edge ends in the tree of name 0.
 //
-// zsel chooses between the two instances at run time: with zsel null both
-// run as launched; otherwise the kZ instance runs only when *zsel is nonzero
-// and the plain one only when it is zero (the host launches both).
-template <class F, int Q, bool kZ>
-__global__ void __launch_bounds__(512) k_edge_pass_filtered(const uint4 *__restrict__ e4,
-                                                            uint64_t n_quads, const uint2 *head,
-                                                            const uint2 *tail, uint32_t *P,
-                                                            uint32_t n, Ctrl *ctrl,
-                                                            const uint32_t *skip, uint32_t *Z,
-                                                            const uint32_t *zsel, uint32_t *log,
-                                                            const uint32_t *hub) {
+// Instances, chosen at run time by the word *sel (the certificate flag):
+//   kZ (with kDirect): the zero-tree form, for a certified hub when Z exists;
+//   !kZ, !kDirect: the plain form that always queues, for a certified hub
+//     whose P fits L2 (resolving in place cost a few percent there);
+//   !kZ, kDirect: the plain form that resolves nearly full warps in place,
+//     for graphs without a certified hub; capped at 32 registers, because
+//     that search-bound pass gains more from resident warps than it loses
+//     to a few spilled registers.
+// The register caps (the launch bounds' minimum blocks) were measured.
+// The hub-serving instances run only when *sel is nonzero, the other only
+// when it is zero; with sel null the launched instance runs.
+//
+// work: the dynamic schedule. Warps claim kGrab steps of 32 * Q consecutive
+// quads at a time from *work, so warps whose edges need long searches do not
+// set the end of the kernel; null: each warp takes a fixed stride of steps.
+constexpr uint64_t kGrab = 8;
+
+template <class F, int Q, bool kZ, bool kDirect>
+__global__ void __launch_bounds__(512, Q >= 4 ? (kZ ? 1 : 2) : (kZ ? 2 : (kDirect ? 4 : 3)))
+    k_edge_pass_filtered(const uint4 *__restrict__ e4, uint64_t n_quads, const uint2 *head, const uint2 *tail,
+                         uint32_t *P, uint32_t n, Ctrl *ctrl, const uint32_t *skip, uint32_t *Z,
+                         const uint32_t *sel, uint32_t *log, unsigned long long *work) {
+  static_assert(kDirect || !kZ, "the zero-tree form resolves in place");
   extern __shared__ uint32_t ring_smem[];
   if (skip && ld_volatile_u32(skip)) return;
-  if (zsel && ((ld_volatile_u32(zsel) != 0u) != kZ)) return;
+  if (sel && ((ld_volatile_u32(sel) != 0u) != (kZ || !kDirect))) return;
   const F fn = F::load(ctrl);
   uint32_t *const S = slots<F>(P);
   const uint64_t pol = policy_evict_first();
   WarpRing ring;
-  // hub: nonzero when this run's selection certified a hub (the plain
-  // instance then always queues; see kDirectMin)
-  const bool queue_only = !kZ && hub && ld_volatile_u32(hub) != 0u;
-  ring.init(ring_smem, kZ ? Z : nullptr, log, queue_only ? kNeverDirect : kDirectMin);
+  ring.init(ring_smem, kZ ? Z : nullptr, log, kDirect ? kDirectMin : kNeverDirect);
   const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (t == 0 && head) single_edge(P, fn, head, n, ctrl, log);
   if (t == 1 % T && tail) single_edge(P, fn, tail, n, ctrl, log);
-  // the loop trip count must be warp-uniform: iterate on the warp's first lane
-  const uint64_t warp_t0 = t - (uint64_t)ring.lane;
-  for (uint64_t wbase = warp_t0; wbase < n_quads; wbase += T * Q) {
-    const uint64_t base = wbase + (uint64_t)ring.lane;
+  // One warp step: lane l takes quads base + j * stride (j < Q), base being
+  // the warp's first quad plus l; the trip counts stay warp-uniform.
+  auto step = [&](uint64_t base, uint64_t stride) {
     uint4 e[Q];
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
-      const uint64_t q = base + (uint64_t)j * T;
+      const uint64_t q = base + (uint64_t)j * stride;
       e[j] = q < n_quads ? ld_edges(e4 + q, pol) : make_uint4(0u, 0u, 0u, 0u);
     }
     uint32_t p[4 * Q];
@@ -220,6 +228,22 @@ __global__ void __launch_bounds__(512) k_edge_pass_filtered(const uint4 *__restr
       const uint32_t pa = p[2 * k], pb = p[2 * k + 1];
       ring.push(S, pa != pb, fn.f(a), pa, fn.f(b), pb);
     }
+  };
+  if (work) {
+    // dynamic: warps claim kGrab steps of 32 * Q consecutive quads at a time,
+    // so warps whose edges need longer searches do not set the kernel's end
+    const uint64_t steps = (n_quads + 32u * Q - 1) / (32u * Q);
+    for (;;) {
+      unsigned long long g0 = 0;
+      if (ring.lane == 0) g0 = atomicAdd(work, (unsigned long long)kGrab);
+      g0 = __shfl_sync(0xFFFFFFFFu, g0, 0);
+      if (g0 >= steps) break;
+      const uint64_t g1 = g0 + kGrab < steps ? g0 + kGrab : steps;
+      for (uint64_t g = g0; g < g1; ++g) step(g * 32u * Q + ring.lane, 32u);
+    }
+  } else {
+    const uint64_t warp_t0 = t - (uint64_t)ring.lane;
+    for (uint64_t wbase = warp_t0; wbase < n_quads; wbase += T * Q) step(wbase + ring.lane, T);
   }
   ring.drain(S);
 }
@@ -531,7 +555,7 @@ constexpr uint64_t kMinWaves = 8;
 template <class F, int Q>
 cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, uint32_t n, Ctrl *ctrl,
                         const uint32_t *skip, uint32_t *Z, const uint32_t *zsel, bool one_shot, uint32_t *log,
-                        const uint32_t *hub, cudaStream_t s) {
+                        const uint32_t *hub, bool dyn, cudaStream_t s) {
   const uint64_t per_block = (uint64_t)block * Q;
   // At least kMinWaves grid iterations per thread: when a whole graph fits
   // one wave, every edge reads P before any hooking and duplicate hub edges
@@ -542,18 +566,37 @@ cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, u
   const uint64_t want = (e.n_quads + per_block * kMinWaves - 1) / (per_block * kMinWaves);
   const uint64_t cap_big = 0x7FFFFFFFull;
   if (filter) {
+    unsigned long long *work = nullptr;
+    if (dyn) {  // one counter serves both instances: only one of them runs
+      cudaError_t err = cudaMemsetAsync(&ctrl->work, 0, sizeof(unsigned long long), s);
+      if (err != cudaSuccess) return err;
+      work = &ctrl->work;
+    }
     const size_t smem = (size_t)(block / 32) * 4 * kRing * sizeof(uint32_t);
     static_assert((1024 / 32) * 4 * kRing * sizeof(uint32_t) <= 48 * 1024,
                   "the ring of a 1024-thread block fits the default dynamic shared memory limit");
-    if (Z) {  // the zero-tree instance (alone, or chosen on the device by *zsel)
-      const unsigned g = clamp_grid(want, one_shot ? cap_big : persistent_cap((const void *)k_edge_pass_filtered<F, Q, true>, block, smem));
-      k_edge_pass_filtered<F, Q, true><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
-                                                              skip, Z, zsel, log, hub); note_launch();
+    // the certificate word chooses among the launched instances (see
+    // k_edge_pass_filtered); zsel: with Z, hub: without it
+    if (Z) {
+      const void *k = (const void *)k_edge_pass_filtered<F, Q, true, true>;
+      const unsigned g = clamp_grid(want, one_shot ? cap_big : persistent_cap(k, block, smem));
+      k_edge_pass_filtered<F, Q, true, true><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
+                                                                    skip, Z, zsel, log, work);
+      note_launch();
+    }
+    if (!Z && hub) {
+      const void *k = (const void *)k_edge_pass_filtered<F, Q, false, false>;
+      const unsigned g = clamp_grid(want, one_shot ? cap_big : persistent_cap(k, block, smem));
+      k_edge_pass_filtered<F, Q, false, false><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n,
+                                                                      ctrl, skip, nullptr, hub, log, work);
+      note_launch();
     }
     if (!Z || zsel) {
-      const unsigned g = clamp_grid(want, one_shot ? cap_big : persistent_cap((const void *)k_edge_pass_filtered<F, Q, false>, block, smem));
-      k_edge_pass_filtered<F, Q, false><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
-                                                               skip, nullptr, Z ? zsel : nullptr, log, hub);
+      const void *k = (const void *)k_edge_pass_filtered<F, Q, false, true>;
+      const unsigned g = clamp_grid(want, one_shot ? cap_big : persistent_cap(k, block, smem));
+      k_edge_pass_filtered<F, Q, false, true><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n,
+                                                                     ctrl, skip, nullptr, Z ? zsel : hub, log,
+                                                                     work);
       note_launch();
     }
   } else {
@@ -568,23 +611,23 @@ cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, u
 template <class F>
 cudaError_t edge_pass_f(int filter, int ept, int block, const EdgeSpan &e, uint32_t *P, uint32_t n,
                         Ctrl *ctrl, const uint32_t *skip, uint32_t *Z, const uint32_t *zsel, bool one_shot,
-                        uint32_t *log, const uint32_t *hub, cudaStream_t s) {
+                        uint32_t *log, const uint32_t *hub, bool dyn, cudaStream_t s) {
   switch (ept) {
-    case 2: return edge_pass_q<F, 1>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, hub, s);
-    case 8: return edge_pass_q<F, 4>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, hub, s);
-    default: return edge_pass_q<F, 2>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, hub, s);
+    case 2: return edge_pass_q<F, 1>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, hub, dyn, s);
+    case 8: return edge_pass_q<F, 4>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, hub, dyn, s);
+    default: return edge_pass_q<F, 2>(filter, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, hub, dyn, s);
   }
 }
 }  // namespace
 
 cudaError_t launch_edge_pass(bool rf, int filter, int ept, int block, const EdgeSpan &e, uint32_t *P,
                              uint32_t n, Ctrl *ctrl, const uint32_t *skip, cudaStream_t s, uint32_t *Z,
-                             const uint32_t *zsel, bool one_shot, uint32_t *log, const uint32_t *hub) {
+                             const uint32_t *zsel, bool one_shot, uint32_t *log, const uint32_t *hub, bool dyn) {
   if (block != 128 && block != 256 && block != 512) block = 256;
   if (e.n_quads == 0 && !e.head && !e.tail) return cudaSuccess;
   if (log) filter = 1;  // the log is kept by the filtered form
-  return rf ? edge_pass_f<RootR>(filter, ept, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, hub, s)
-            : edge_pass_f<RootId>(filter, ept, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, hub, s);
+  return rf ? edge_pass_f<RootR>(filter, ept, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, hub, dyn, s)
+            : edge_pass_f<RootId>(filter, ept, block, e, P, n, ctrl, skip, Z, zsel, one_shot, log, hub, dyn, s);
 }
 
 cudaError_t launch_validate(const EdgeSpan &e, uint32_t n, Ctrl *ctrl, cudaStream_t s, uint32_t *reject) {
