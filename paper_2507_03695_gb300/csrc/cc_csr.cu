@@ -99,21 +99,27 @@ __global__ void __launch_bounds__(256) k_csr_tile_rows(const uint64_t *__restric
 
 // The edge pass over CSR: warp-sized chunks of consecutive entries, the row
 // of each lane found by walking the offsets forward from the warp's current
-// row (bounded by n), the filter and the warp ring as in the COO pass.
+// row (bounded by n), the filter and the warp ring as in the COO pass. Warps
+// claim tiles one at a time from *work (the dynamic schedule of the COO pass).
 template <class F>
 __global__ void __launch_bounds__(512) k_edge_pass_csr(const uint64_t *__restrict__ off,
                                                        const uint32_t *__restrict__ nb, uint64_t n_entries,
                                                        uint32_t n, uint32_t tile, const uint32_t *tile_row,
-                                                       uint32_t *P, Ctrl *ctrl) {
+                                                       uint32_t *P, Ctrl *ctrl, unsigned long long *work) {
   extern __shared__ uint32_t ring_smem[];
   const F fn = F::load(ctrl);
   uint32_t *const S = slots<F>(P);
   const uint64_t pol = policy_evict_first();
   WarpRing ring;
-  ring.init(ring_smem);
+  // always through the queue: the lanes of a chunk share row endpoints, and
+  // resolving them in place measured slower (R-MAT 24 and the grid)
+  ring.init(ring_smem, nullptr, nullptr, kNeverDirect);
   const uint64_t n_tiles = (n_entries + tile - 1) / tile;
-  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t t = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < n_tiles; t += warps) {
+  for (;;) {
+    unsigned long long t = 0;
+    if (ring.lane == 0) t = atomicAdd(work, 1ULL);
+    t = __shfl_sync(0xFFFFFFFFu, t, 0);
+    if (t >= n_tiles) break;
     uint32_t r = tile_row[t];  // warp-uniform: the row of the tile's first entry
     const uint64_t end = (t + 1) * tile < n_entries ? (t + 1) * tile : n_entries;
     for (uint64_t base = t * tile; base < end; base += 32u) {
@@ -194,16 +200,20 @@ cudaError_t launch_edge_pass_csr(bool rf, const uint64_t *off, const uint32_t *n
   const unsigned gt = clamp_grid((n_tiles + 255) / 256, persistent_cap((const void *)k_csr_tile_rows, 256, 0));
   k_csr_tile_rows<<<gt, 256, 0, s>>>(off, n, n_tiles, kCsrTile, tile_row);
   note_launch();
+  cudaError_t err = cudaMemsetAsync(&ctrl->work, 0, sizeof(unsigned long long), s);
+  if (err != cudaSuccess) return err;
   const int block = 256;
   const size_t smem = (size_t)(block / 32) * 4 * kRing * sizeof(uint32_t);
   // at least eight tiles per warp (as the COO pass keeps eight waves)
   const uint64_t want = (n_tiles + (block / 32) * 8 - 1) / ((block / 32) * 8);
   if (rf) {
     const unsigned g = clamp_grid(want, persistent_cap((const void *)k_edge_pass_csr<RootR>, block, smem));
-    k_edge_pass_csr<RootR><<<g, block, smem, s>>>(off, nb, n_entries, n, kCsrTile, tile_row, P, ctrl);
+    k_edge_pass_csr<RootR><<<g, block, smem, s>>>(off, nb, n_entries, n, kCsrTile, tile_row, P, ctrl,
+                                                   &ctrl->work);
   } else {
     const unsigned g = clamp_grid(want, persistent_cap((const void *)k_edge_pass_csr<RootId>, block, smem));
-    k_edge_pass_csr<RootId><<<g, block, smem, s>>>(off, nb, n_entries, n, kCsrTile, tile_row, P, ctrl);
+    k_edge_pass_csr<RootId><<<g, block, smem, s>>>(off, nb, n_entries, n, kCsrTile, tile_row, P, ctrl,
+                                                    &ctrl->work);
   }
   note_launch();
   return cudaGetLastError();
