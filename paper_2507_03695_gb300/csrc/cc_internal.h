@@ -168,8 +168,10 @@ cudaError_t launch_edge_pass_csr(bool rf, const uint64_t *off, const uint32_t *n
 // Unpacks n_edges edges of 3-byte ids (cc_pack.cu; src 16-byte aligned) into
 // uint32 pairs at dst (16-byte aligned).
 cudaError_t launch_unpack3(const uint8_t *src, uint64_t n_edges, uint32_t *dst, cudaStream_t s);
+// track: also put the largest sampled count in the high half of track->maxkey
 cudaError_t launch_degree_sampled_u32(const uint2 *edges, uint64_t n_edges, uint64_t edge_base,
-                                      uint32_t stride, uint32_t *cnt, uint32_t n, cudaStream_t s);
+                                      uint32_t stride, uint32_t *cnt, uint32_t n, cudaStream_t s,
+                                      Ctrl *track = nullptr);
 cudaError_t launch_argmax_u32(const uint32_t *cnt, uint32_t n, Ctrl *ctrl, cudaStream_t s);
 // Z: the zero-tree bitmap (one bit per name, zeroed at every init), or null.
 // With Z and zsel null only the zero-tree instance runs; with both, the device

@@ -87,10 +87,14 @@ __global__ void __launch_bounds__(256) k_degree(const uint4 *__restrict__ e4, ui
 }
 
 // Sampled histogram: edge i (global index edge_base + i) is counted iff
-// ((edge_base + i) / 1024) % stride == 0.
+// ((edge_base + i) / 1024) % stride == 0. With track, the largest count also
+// goes to the high half of track->maxkey (from the atomics' old values: the
+// last increment of a counter sees its final value), which spares an argmax
+// pass over the counters when only the largest count is needed.
 __global__ void __launch_bounds__(256) k_degree_sampled(const uint2 *__restrict__ e, uint64_t n_edges,
                                                         uint64_t edge_base, uint32_t stride,
-                                                        uint32_t *__restrict__ cnt, uint32_t n) {
+                                                        uint32_t *__restrict__ cnt, uint32_t n, Ctrl *track) {
+  uint32_t top = 0;
   const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t g_first = edge_base / 1024u;
   const uint64_t g_last = (edge_base + n_edges + 1023u) / 1024u;  // exclusive
@@ -101,7 +105,16 @@ __global__ void __launch_bounds__(256) k_degree_sampled(const uint2 *__restrict_
     const uint64_t gi = grp * 1024u + (k % 1024u);
     if (gi < edge_base || gi >= edge_base + n_edges) continue;
     const uint2 x = ld_edge(e + (gi - edge_base));
-    count_edge(cnt, n, x.x, x.y);
+    if (!track) {
+      count_edge(cnt, n, x.x, x.y);
+    } else {
+      if (x.x < n) top = max(top, atomicAdd(cnt + x.x, 1u) + 1u);
+      if (x.y < n) top = max(top, atomicAdd(cnt + x.y, 1u) + 1u);
+    }
+  }
+  if (track) {
+    top = __reduce_max_sync(0xFFFFFFFFu, top);
+    if ((threadIdx.x & 31) == 0 && top) atomicMax(&track->maxkey, (unsigned long long)top << 32);
   }
 }
 
@@ -480,12 +493,12 @@ cudaError_t launch_degree_u32(const EdgeSpan &e, uint32_t *cnt, uint32_t n, cuda
 }
 
 cudaError_t launch_degree_sampled_u32(const uint2 *edges, uint64_t n_edges, uint64_t edge_base,
-                                      uint32_t stride, uint32_t *cnt, uint32_t n, cudaStream_t s) {
+                                      uint32_t stride, uint32_t *cnt, uint32_t n, cudaStream_t s, Ctrl *track) {
   if (n_edges == 0) return cudaSuccess;
   if (stride == 0) stride = 1;
   const uint64_t groups = (n_edges + 1023) / 1024 / stride + 2;
   const unsigned g = clamp_grid(groups * 1024 / 256, persistent_cap((const void *)k_degree_sampled, 256, 0));
-  k_degree_sampled<<<g, 256, 0, s>>>(edges, n_edges, edge_base, stride, cnt, n);
+  k_degree_sampled<<<g, 256, 0, s>>>(edges, n_edges, edge_base, stride, cnt, n, track);
   note_launch();
   return cudaGetLastError();
 }
@@ -508,11 +521,12 @@ cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges
   if ((err = cudaMemsetAsync(&ctrl->m_sel, 0xFF, sizeof(uint32_t), s)) != cudaSuccess) return err;
   if ((err = cudaMemsetAsync(&ctrl->n_cand, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) return err;
   uint32_t *c32 = static_cast<uint32_t *>(cnt);
-  // 1. sampled histogram and its maximum
-  if ((err = launch_degree_sampled_u32(reinterpret_cast<const uint2 *>(edges), n_edges, 0, kCertSample, c32, n, s)) !=
-      cudaSuccess)
+  // 1. sampled histogram and its largest count; the push list also needs the
+  // vertex holding it (the argmax pass)
+  if ((err = launch_degree_sampled_u32(reinterpret_cast<const uint2 *>(edges), n_edges, 0, kCertSample, c32, n, s,
+                                       push_buf ? nullptr : ctrl)) != cudaSuccess)
     return err;
-  if ((err = launch_argmax_u32(c32, n, ctrl, s)) != cudaSuccess) return err;
+  if (push_buf && (err = launch_argmax_u32(c32, n, ctrl, s)) != cudaSuccess) return err;
   // 2. candidates: the owners of their buckets
   const unsigned gsel = clamp_grid(((uint64_t)n + 255) / 256, persistent_cap((const void *)k_select_candidates, 256, 0));
   k_select_candidates<<<gsel, 256, 0, s>>>(c32, n, ctrl, cs);
