@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(512) k_edge_pass_direct(const uint4 *__restric
 // work: the dynamic schedule. Warps claim kGrab steps of 32 * Q consecutive
 // quads at a time from *work, so warps whose edges need long searches do not
 // set the end of the kernel; null: each warp takes a fixed stride of steps.
-constexpr uint64_t kGrab = 8;
+constexpr uint64_t kGrab = 16;
 
 template <class F, int Q, bool kZ, bool kDirect>
 __global__ void __launch_bounds__(512, Q >= 4 ? (kZ ? 1 : 2) : (kZ ? 2 : (kDirect ? 4 : 3)))
