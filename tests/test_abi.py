@@ -113,6 +113,11 @@ def test_host_side_errors(lib):
     assert L.cc_labels(None, None, None) == lib.CC_ERR_INVALID_ARGUMENT
     assert L.cc_connected(None, None, 0, None, None) == lib.CC_ERR_INVALID_ARGUMENT
     assert L.cc_sync(None) == lib.CC_ERR_INVALID_ARGUMENT
+    assert L.cc_run_host(None, None, 0, None, None) == lib.CC_ERR_INVALID_ARGUMENT
+    assert L.cc_run_host_async(None, None, 0, None, None) == lib.CC_ERR_INVALID_ARGUMENT
+    assert L.cc_run_host_packed(None, None, 0, 3, None, None) == lib.CC_ERR_INVALID_ARGUMENT
+    assert L.cc_run_host_packed_async(None, None, 0, 3, None, None) == lib.CC_ERR_INVALID_ARGUMENT
+    assert L.cc_run_csr(None, None, None, 0, None, None) == lib.CC_ERR_INVALID_ARGUMENT
     out = ctypes.c_uint64()
     assert L.cc_num_components(None, ctypes.byref(out)) == lib.CC_ERR_INVALID_ARGUMENT
     L.cc_destroy(None)
