@@ -20,6 +20,8 @@ with the passage of the paper it follows:
   transitive-closure (Warshall) matrix, then the minimum of each row.
 * :func:`max_degree_vertex` -- ``m`` of Eq. 1 (Algorithm 4, ``max_degree()``):
   endpoint occurrences, ties to the smaller id.
+* :func:`degree_add` -- the same endpoint counts accumulated chunk by chunk,
+  for inputs too large to hold at once.
 * :func:`rfjt_init`, :func:`rfjt_hook`, :func:`rfjt_pointer_jump` --
   Algorithm 3 (Algorithm 1 when ``use_r=False``) run sequentially.
 """
@@ -154,6 +156,15 @@ def max_degree_vertex(n: int, edges, return_degrees: bool = False):
                                       deg.ctypes.data if deg is not None else None)
     _ok(int(m), "max_degree_vertex")
     return (int(m), deg) if return_degrees else int(m)
+
+
+def degree_add(n: int, edges, deg: np.ndarray) -> np.ndarray:
+    """Adds the endpoint occurrences of one chunk of edges to deg (uint64[n],
+    in place, and returned): deg[x] += number of times x occurs as u or v."""
+    assert deg.dtype == np.uint64 and deg.flags.c_contiguous and len(deg) == n
+    e = _edges(edges)
+    _ok(_L().oracle_degree_add(n, e.ctypes.data, len(e), deg.ctypes.data), "degree_add")
+    return deg
 
 
 def num_components(L: np.ndarray) -> int:

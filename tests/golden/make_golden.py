@@ -40,14 +40,13 @@ def golden_for(w: graphgen.Workload) -> dict:
     h_edges = hashlib.sha256()
     uf = oracle.StreamingUnionFind(n)
     deg = np.zeros(n, dtype=np.uint64)
-    lib = oracle._L()
     if w.kind == "rmat":
         total = w.n_edges
         for b in range(0, total, CHUNK):
             e = graphgen.rmat(w.scale, total, w.seed, w.scramble, b, min(total, b + CHUNK))
             h_edges.update(e.view(np.uint8))
             uf.add(e)
-            assert lib.oracle_degree_add(n, e.ctypes.data, len(e), deg.ctypes.data) == 0
+            oracle.degree_add(n, e, deg)
         chunks_for_rv = lambda: (graphgen.rmat(w.scale, total, w.seed, w.scramble, b, min(total, b + CHUNK))  # noqa: E731
                                  for b in range(0, total, CHUNK))
     else:
@@ -55,7 +54,7 @@ def golden_for(w: graphgen.Workload) -> dict:
         total = len(e_all)
         h_edges.update(e_all.view(np.uint8))
         uf.add(e_all)
-        assert lib.oracle_degree_add(n, e_all.ctypes.data, len(e_all), deg.ctypes.data) == 0
+        oracle.degree_add(n, e_all, deg)
         chunks_for_rv = lambda: iter([e_all])  # noqa: E731
     L = uf.min_labels()
     uf.close()

@@ -31,6 +31,11 @@ MUTANTS = {
     "csr_row_tie_to_larger": ("if (len > best_len) {", "if (len >= best_len) {"),
     "csr_row_len_dropped_term": ("const uint64_t len = offsets[v + 1] - offsets[v];",
                                  "const uint64_t len = offsets[v + 1];"),
+    "degree_add_counts_only_u": ("  for (uint64_t i = 0; i < 2 * n_edges; ++i) {\n    if (edges[i] >= n) return -1;",
+                                 "  for (uint64_t i = 0; i < 2 * n_edges; i += 2) {\n    if (edges[i] >= n) return -1;"),
+    "degree_add_first_half_only": ("  for (uint64_t i = 0; i < 2 * n_edges; ++i) {\n    if (edges[i] >= n) return -1;",
+                                   "  for (uint64_t i = 0; i < n_edges; ++i) {\n    if (edges[i] >= n) return -1;"),
+    "degree_add_no_range_check": ("    if (edges[i] >= n) return -1;\n    deg[edges[i]]++;", "    deg[edges[i]]++;"),
 }
 
 
@@ -55,6 +60,8 @@ def _load(so):
     lib.oracle_rfjt_init.argtypes = [u64, i32, u64, p]
     lib.oracle_rfjt_hook.argtypes = [u64, i32, u64, p, u64, p]
     lib.oracle_rfjt_pointer_jump.argtypes = [u64, i32, u64, p]
+    lib.oracle_degree_add.argtypes = [u64, p, u64, p]
+    lib.oracle_degree_add.restype = i32
     return lib
 
 
@@ -82,6 +89,22 @@ def _pins_pass(lib) -> bool:
     # the tie rule of the degree argmax
     e = np.array([[1, 1], [2, 3], [2, 4], [0, 5]], np.uint32)
     if lib.oracle_max_degree_vertex(6, e.ctypes.data, len(e), None) != 1:
+        return False
+    # the streaming degree count, fed in uneven chunks, against bincount of
+    # both endpoint columns; an out-of-range id is rejected
+    for trial in range(10):
+        n = int(rng.integers(1, 60))
+        e = rng.integers(0, n, size=(int(rng.integers(1, 200)), 2)).astype(np.uint32)
+        deg = np.zeros(n, np.uint64)
+        for chunk in np.array_split(e, int(rng.integers(1, 5))):
+            chunk = np.ascontiguousarray(chunk)
+            if lib.oracle_degree_add(n, chunk.ctypes.data, len(chunk), deg.ctypes.data) != 0:
+                return False
+        if not (deg == np.bincount(e.ravel(), minlength=n)).all():
+            return False
+    deg = np.zeros(8, np.uint64)
+    e = np.array([[0, 1], [2, 9]], np.uint32)
+    if lib.oracle_degree_add(4, e.ctypes.data, len(e), deg.ctypes.data) != -1:
         return False
     # CSR rows: on a symmetric graph without self-loops the longest row is
     # the vertex of largest degree (same tie rule); ties and empty rows

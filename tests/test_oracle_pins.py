@@ -182,6 +182,44 @@ def test_max_degree_vertex():
         assert oracle.max_degree_vertex(n, e) == int(np.flatnonzero(cnt == cnt.max())[0])
 
 
+def test_degree_add_chunked():
+    """The streaming degree count (the maximum-degree vertex of Algorithm 4's
+    max_degree() for inputs fed in chunks) against numpy's bincount of both
+    endpoint columns: random edge lists with self-loops and duplicates, split
+    at every kind of chunk boundary (empty chunks, one-edge chunks, uneven
+    splits); its argmax (smallest id on ties) is max_degree_vertex; closed
+    forms for a star and for self-loops; an out-of-range id is rejected."""
+    rng = np.random.default_rng(23)
+    for trial in range(40):
+        n = int(rng.integers(1, 500))
+        k = int(rng.integers(0, 2000))
+        e = rng.integers(0, n, size=(k, 2)).astype(np.uint32)
+        if k:
+            loops = rng.random(k) < 0.05
+            e[loops, 1] = e[loops, 0]  # self-loops
+            dup = rng.integers(0, k, size=k // 10)
+            e = np.concatenate([e, e[dup]])  # duplicates
+        cuts = np.sort(rng.integers(0, len(e) + 1, size=int(rng.integers(0, 6))))
+        deg = np.zeros(n, np.uint64)
+        for chunk in np.split(e, cuts):
+            oracle.degree_add(n, chunk, deg)
+        want = np.bincount(e[:, 0], minlength=n) + np.bincount(e[:, 1], minlength=n)
+        np.testing.assert_array_equal(deg, want.astype(np.uint64))
+        assert int(np.flatnonzero(deg == deg.max())[0]) == oracle.max_degree_vertex(n, e)
+    # closed forms: a star on k leaves gives the centre k and each leaf 1; a
+    # self-loop counts twice
+    k = 37
+    star = np.stack([np.full(k, 3), np.arange(4, 4 + k)], 1).astype(np.uint32)
+    deg = oracle.degree_add(4 + k, star, np.zeros(4 + k, np.uint64))
+    assert deg[3] == k and (deg[4:] == 1).all() and (deg[:3] == 0).all()
+    deg = oracle.degree_add(3, np.array([[1, 1], [1, 1], [2, 0]], np.uint32), np.zeros(3, np.uint64))
+    np.testing.assert_array_equal(deg, [1, 4, 1])
+    with pytest.raises(ValueError):
+        oracle.degree_add(4, np.array([[0, 1], [2, 4]], np.uint32), np.zeros(4, np.uint64))
+    with pytest.raises(ValueError):
+        oracle.degree_add(4, np.array([[7, 1]], np.uint32), np.zeros(4, np.uint64))
+
+
 def test_root_value_identity_rmat16():
     """L_root[v] = 0 if v ~ m else L_min[v] + 1 (Eq. 1 relabelling), and with
     f = id the root-value labels are the min-id labels (Section IV)."""
