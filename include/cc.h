@@ -306,9 +306,10 @@ CC_API cc_status cc_device_bytes(const cc_graph *g, uint64_t *bytes);
  *  - Scratch: a fixed static device array inside the library (about 16 MiB
  *    per GPU that loads the library, held until the process exits). The first
  *    call on a device looks up its address (cudaGetSymbolAddress); make that
- *    first call before any stream capture. All calls share the array and
- *    each clears what it uses, so calls whose work overlaps on the GPU race:
- *    serialise them (one stream, or events).
+ *    first call before any stream capture. The address is kept per device and
+ *    context: the first call after cudaDeviceReset looks it up again. All
+ *    calls share the array and each clears what it uses, so calls whose work
+ *    overlaps on the GPU race: serialise them (one stream, or events).
  * Errors: CC_ERR_INVALID_ARGUMENT (NULL or misaligned pointer, n_vertices 0),
  * CC_ERR_TOO_LARGE (n_vertices or n_edges over the limits), CC_ERR_CUDA. */
 CC_API cc_status cc_max_degree_vertex_noalloc(const uint32_t *edges_dev, uint64_t n_edges,

@@ -13,10 +13,14 @@
 // about 16 MiB) until the process exits. Host code cannot use the array's
 // name as a device address, so the first call on each device looks the
 // address up with cudaGetSymbolAddress while that device is current and
-// caches it; that first call should therefore come before any stream
-// capture. Every call shares the one array and leaves its contents behind,
-// so each call clears the counters it uses first, and calls whose work
-// overlaps on the GPU (different streams, or several host threads) race.
+// caches it together with the id of the device's current context; that
+// first call should therefore come before any stream capture. A later call
+// in another context (after cudaDeviceReset, which reloads the module at a
+// possibly different address) looks the address up again. Every call shares
+// the one array and leaves its contents behind, so each call clears the
+// counters it uses first, and calls whose work overlaps on the GPU
+// (different streams, or several host threads) race.
+#include <cuda.h>  // CUcontext and CUresult, for the context id (no libcuda link)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -39,21 +43,56 @@ static_assert(sizeof(cc::Ctrl) <= kHeaderWords * sizeof(uint32_t), "header too s
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 uint32_t *g_ptr[kMaxDevices] = {};
+unsigned long long g_ctx[kMaxDevices] = {};  // context id the cached address belongs to
 
-// Device address of the scratch array on the current device (looked up once
-// per device).
+// Id of the calling thread's current context (unique for the process's
+// lifetime), or 0 when there is none or the driver does not say. The two
+// driver calls are reached through the runtime's entry-point query, so the
+// library needs no link to libcuda.
+unsigned long long current_ctx_id() {
+  using GetCurrent = CUresult (*)(CUcontext *);
+  using GetId = CUresult (*)(CUcontext, unsigned long long *);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  });
+  if (!get_current || !get_id) return 0;
+  CUcontext c = nullptr;
+  if (get_current(&c) != CUDA_SUCCESS || !c) return 0;
+  unsigned long long id = 0;
+  if (get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device: looked up once
+// per device and context (every call, if the context id is unknown).
 cudaError_t scratch_address(uint32_t **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_ptr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_ptr[dev] = static_cast<uint32_t *>(p);
+  const unsigned long long ctx = current_ctx_id();
+  if (g_ptr[dev] && ctx != 0 && ctx == g_ctx[dev]) {
+    *out = g_ptr[dev];
+    return cudaSuccess;
   }
+  void *p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // also makes the context current if it was not
+  if (e != cudaSuccess) return e;
+  g_ptr[dev] = static_cast<uint32_t *>(p);
+  g_ctx[dev] = ctx != 0 ? ctx : current_ctx_id();
   *out = g_ptr[dev];
   return cudaSuccess;
 }
