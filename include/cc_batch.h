@@ -35,7 +35,12 @@ typedef struct cc_batch_config {
   int32_t filter;           /* 1: warp filter + compaction, 0: per-lane */
   uint32_t tile_edges;      /* edges per tile, a multiple of 256, >= 256 */
   uint32_t tile_vertices;   /* vertices per tile of the label phase, >= 256 */
-  int32_t reserved[3];      /* must be zero */
+  uint32_t barrier_wait_us; /* bounded wait of each grid barrier, at most 60 s; 0 = 4 s. A
+                               wait that expires aborts the run (every block leaves at its
+                               next barrier; the labels are then undefined) and cc_batch_sync
+                               returns CC_ERR_TIMEOUT; the next run starts afresh. The
+                               autotuner keeps the context's value */
+  int32_t reserved[2];      /* must be zero */
 } cc_batch_config;
 
 /* A batch context for up to max_graphs graphs per call: its tile-offset

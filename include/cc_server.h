@@ -87,7 +87,25 @@ typedef struct cc_server_config {
   uint32_t idle_timeout_us;        /* executor leaves after this much idleness; 0 = 20000 */
   int32_t mode;                    /* cc_root_mode of new graphs; default CC_ROOT_MAXDEG */
   int32_t label_space;             /* cc_label_space of snapshots; default MIN_ID   */
-  int32_t reserved[4];             /* must be zero */
+  /* Bounded waits of the executor (at most 600 s each). publish_wait_us: how
+   * long an executor block waits for a tile it has claimed but the host has
+   * not published; expiry makes the executor leave (the host then fails the
+   * requests in flight with CC_ERR_TIMEOUT, counts executor_timeouts and
+   * relaunches it for later requests); 0 = 30 s. Keep it above the idle
+   * timeout: an idle executor is asked to leave before its waits expire,
+   * whereas blocks whose wait expired while idle cannot take tiles published
+   * just then (those requests would fail the same way). gate_wait_us: how long an
+   * insert's apply tile waits for the request's validate tiles; expiry fails
+   * the insert with CC_ERR_TIMEOUT, and apply tiles that had already passed
+   * the gate stay applied (a subset of a valid batch: P is still a forest
+   * of the graph's edges plus some of the batch); 0 = 2 s. */
+  uint32_t publish_wait_us;
+  uint32_t gate_wait_us;
+  /* Fault injection for tests (a stuck producer): the first executor request
+   * has its tiles written to the ring but published only this long later, so
+   * an executor whose publish wait is shorter gives up on it. 0 = off. */
+  uint32_t fault_hold_publish_us;
+  int32_t reserved[1];             /* must be zero */
 } cc_server_config;
 
 typedef struct cc_server_stats {
@@ -95,6 +113,7 @@ typedef struct cc_server_stats {
   uint64_t resident_graphs, arena_bytes_used, arena_bytes;
   uint64_t executor_launches, tiles_run;
   uint64_t side_drains;  /* executor drains forced by starved side-stream work */
+  uint64_t executor_timeouts;  /* executor launches that ended on an expired publish wait */
 } cc_server_stats;
 
 CC_API void cc_server_config_init(cc_server_config *cfg);

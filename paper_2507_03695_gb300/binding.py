@@ -48,7 +48,7 @@ class cc_options(ctypes.Structure):
 class cc_batch_config(ctypes.Structure):
     _fields_ = [
         ("block_size", _i32), ("edges_per_thread", _i32), ("filter", _i32), ("tile_edges", _u32),
-        ("tile_vertices", _u32), ("reserved", _i32 * 3),
+        ("tile_vertices", _u32), ("barrier_wait_us", _u32), ("reserved", _i32 * 2),
     ]
 
     def as_dict(self) -> dict:
@@ -66,13 +66,14 @@ class cc_server_config(ctypes.Structure):
     _fields_ = [
         ("hbm_budget_bytes", _u64), ("max_graphs", _u32), ("executor_blocks_per_sm", _u32),
         ("tile_edges", _u32), ("idle_timeout_us", _u32), ("mode", _i32), ("label_space", _i32),
-        ("reserved", _i32 * 4),
+        ("publish_wait_us", _u32), ("gate_wait_us", _u32), ("fault_hold_publish_us", _u32), ("reserved", _i32 * 1),
     ]
 
 
 class cc_server_stats(ctypes.Structure):
     _fields_ = [(k, _u64) for k in ("submitted", "completed", "failed", "resident_graphs", "arena_bytes_used",
-                                    "arena_bytes", "executor_launches", "tiles_run", "side_drains")]
+                                    "arena_bytes", "executor_launches", "tiles_run", "side_drains",
+                                    "executor_timeouts")]
 
 
 CC_REQ_NEW_GRAPH, CC_REQ_INSERT, CC_REQ_QUERY, CC_REQ_SNAPSHOT, CC_REQ_DROP_GRAPH = 1, 2, 3, 4, 5

@@ -43,12 +43,13 @@ struct BatchArgs {
   uint64_t *etile_off;  // n_graphs + 1
   uint64_t *vtile_off;  // n_graphs + 1
   uint32_t tile_edges, tile_vertices;
+  unsigned long long barrier_ns;  // bounded wait of every grid barrier
   BatchCtrl *ctrl;
 };
 
 namespace {
 
-constexpr unsigned long long kBarrierTimeoutNs = 4000000000ULL;  // 4 s
+constexpr unsigned long long kBarrierTimeoutNs = 4000000000ULL;  // 4 s: default barrier wait
 
 __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;
@@ -64,9 +65,10 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
 
 // Grid barrier for a cooperative launch (all blocks co-resident). Arrivals
 // are counted cumulatively, so barrier k completes when the count reaches
-// k * gridDim.x. Every wait gives up after kBarrierTimeoutNs, flags
-// kErrTimeout and aborts the run. Returns false when the run must stop.
-__device__ bool grid_barrier(BatchCtrl *c, unsigned int &gen) {
+// k * gridDim.x. Every wait gives up after limit_ns, flags kErrTimeout and
+// aborts the run (every block then leaves at its next barrier). Returns false
+// when the run must stop.
+__device__ bool grid_barrier(BatchCtrl *c, unsigned int &gen, unsigned long long limit_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -80,7 +82,7 @@ __device__ bool grid_barrier(BatchCtrl *c, unsigned int &gen) {
     } else {
       const unsigned long long t0 = globaltimer();
       while (ld_acquire_u32(&c->bar_gen) < target) {
-        if (globaltimer() - t0 > kBarrierTimeoutNs) {
+        if (globaltimer() - t0 > limit_ns) {
           atomicOr(&c->err, kErrTimeout);
           atomicExch(&c->abort, 1u);
           ok = 0;
@@ -199,14 +201,14 @@ __global__ void __launch_bounds__(512) k_batched(BatchArgs a) {
   BatchCtrl *c = a.ctrl;
   unsigned int gen = 0;
   if (blockIdx.x == 0) scan_tiles(a);
-  if (!grid_barrier(c, gen)) return;
+  if (!grid_barrier(c, gen, a.barrier_ns)) return;
 
   // 1. initialisation: P[x] = x
   const uint64_t V = a.vtx_off[a.n_graphs];
   const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   for (uint64_t x = tid; x < V; x += T) a.P[x] = (uint32_t)x;
-  if (!grid_barrier(c, gen)) return;
+  if (!grid_barrier(c, gen, a.barrier_ns)) return;
 
   // 2. hooking over edge tiles
   uint32_t *const P = a.P;  // names are global ids: the slot of name x is P[x]
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(512) k_batched(BatchArgs a) {
     }
   }
   if (FILTER) ring.drain(P);
-  if (!grid_barrier(c, gen)) return;
+  if (!grid_barrier(c, gen, a.barrier_ns)) return;
 
   // 3. compression: each vertex stores its root's name (read-only walks)
   for (uint64_t x = tid; x < V; x += T) {
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(512) k_batched(BatchArgs a) {
     }
     if (r != px) stP(P + x, r);
   }
-  if (!grid_barrier(c, gen)) return;
+  if (!grid_barrier(c, gen, a.barrier_ns)) return;
 
   // 4. graph-local labels, in place
   const uint64_t n_vtiles = a.vtile_off[a.n_graphs];
@@ -319,6 +321,7 @@ bool cfg_valid(const cc_batch_config &c) {
   if (c.edges_per_thread != 1 && c.edges_per_thread != 2 && c.edges_per_thread != 4) return false;
   if (c.filter != 0 && c.filter != 1) return false;
   if (c.tile_edges < 256 || c.tile_edges % 256 || c.tile_vertices < 256) return false;
+  if (c.barrier_wait_us > 60u * 1000u * 1000u) return false;
   for (int r : c.reserved)
     if (r) return false;
   return true;
@@ -394,6 +397,7 @@ cc_status enqueue(cc_batch *b, const cc_batch_config &cfg, uint32_t n_graphs, co
   a.vtile_off = b->tile_off + (b->max_graphs + 1);
   a.tile_edges = cfg.tile_edges;
   a.tile_vertices = cfg.tile_vertices;
+  a.barrier_ns = cfg.barrier_wait_us ? (unsigned long long)cfg.barrier_wait_us * 1000ULL : cc::kBarrierTimeoutNs;
   a.ctrl = b->ctrl;
   return from_cuda(launch_batched(cfg, a, s));
 }
@@ -511,6 +515,7 @@ cc_status cc_batch_tune(cc_batch *b, uint32_t n_graphs, const uint64_t *vtx_off_
       for (int flt : filters)
         for (uint32_t te : tiles) {
           cc_batch_config c = default_cfg();
+          c.barrier_wait_us = b->cfg.barrier_wait_us;
           c.block_size = blk;
           c.edges_per_thread = ept;
           c.filter = flt;

@@ -40,6 +40,8 @@ namespace srv {
 constexpr uint32_t kRingCap = 1u << 16;  // work items in the ring
 constexpr uint32_t kSlots = 4096;        // requests with executor tiles in flight
 enum : uint32_t { kItemEdges = 1, kItemValidate = 2, kItemApply = 3, kItemQuery = 4 };
+// Default bounded waits of the executor (cc_server_config.gate_wait_us and
+// publish_wait_us set others).
 constexpr unsigned long long kGateTimeoutNs = 2000000000ULL;  // gated apply tile: 2 s
 constexpr unsigned long long kWaitLimitNs = 30000000000ULL;   // waiting for an item: 30 s
 // Side-stream requests in flight at once: bounds the launches queued on the
@@ -149,9 +151,12 @@ __device__ __forceinline__ void walk_step(const uint32_t *S, uint32_t &c, uint32
 constexpr int kEpt = 4;  // elements per thread per round
 
 // The persistent executor: each block claims the next item index, waits
-// (bounded) until the host has published it, runs it, and counts the
-// request's finished tiles. Blocks leave when the host sets `stop`.
-__global__ void __launch_bounds__(256) k_executor(HostShared *hs, DevShared *ds) {
+// (at most wait_ns) until the host has published it, runs it, and counts the
+// request's finished tiles. Blocks leave when the host sets `stop`, or when
+// a wait expires (exec_err tells the host). A gated apply tile waits at most
+// gate_ns for its request's validate tiles.
+__global__ void __launch_bounds__(256) k_executor(HostShared *hs, DevShared *ds, unsigned long long wait_ns,
+                                                  unsigned long long gate_ns) {
   __shared__ WorkItem it;
   __shared__ int s_leave;
   __shared__ unsigned int s_bad, s_skip;
@@ -167,7 +172,7 @@ __global__ void __launch_bounds__(256) k_executor(HostShared *hs, DevShared *ds)
           leave = 1;
           break;
         }
-        if (now_ns() - t0 > kWaitLimitNs) {  // the host stopped answering
+        if (now_ns() - t0 > wait_ns) {  // the host stopped answering
           *(volatile unsigned int *)&hs->exec_err = 1u;
           leave = 1;
           break;
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(256) k_executor(HostShared *hs, DevShared *ds)
       if (!leave && it.kind == kItemApply && it.n_gate) {
         const unsigned long long g0 = now_ns();
         while (ld_volatile_sys_u32(&ds->validated[it.slot]) < it.n_gate) {
-          if (now_ns() - g0 > kGateTimeoutNs) {
+          if (now_ns() - g0 > gate_ns) {
             s_skip = 1u;
             s_bad = 2u;  // reported as a timeout
             break;
@@ -514,6 +519,14 @@ struct cc_server {
   std::vector<Req *> side_running;  // requests with side-stream work in flight
   bool exec_running = false, exec_stopping = false;
   uint64_t idle_since = 0;
+  unsigned long long wait_ns = 0, gate_ns = 0;  // the executor's bounded waits
+  std::atomic<uint64_t> executor_timeouts{0};
+  // fault injection (cfg.fault_hold_publish_us): executor requests still to
+  // hold, and the one whose tiles are written but not yet published
+  uint32_t hold_left = 0;
+  Req *held = nullptr;
+  unsigned long long held_pub = 0;
+  uint64_t held_until = 0;
   std::thread thread;
 };
 
@@ -599,7 +612,7 @@ bool start_exec(cc_server *s, Req *r, GraphState &g) {
     complete(s, r, CC_OK);
     return true;
   }
-  if (s->exec_stopping) return false;
+  if (s->exec_stopping || s->held) return false;
   const uint64_t tile = tile_for(s, count, 256);
   const uint64_t n_work = n_tiles_of(count, tile);
   const uint64_t vtile = insert && n_work > 1 ? tile_for(s, count, 16384) : 0;
@@ -627,7 +640,16 @@ bool start_exec(cc_server *s, Req *r, GraphState &g) {
                 pub);
   }
   std::atomic_thread_fence(std::memory_order_seq_cst);
-  *(volatile unsigned long long *)&s->hs->published = pub;
+  if (s->hold_left) {
+    // fault injection: a stuck producer, whose tiles are in the ring but not
+    // published until held_until (manage_executor publishes or drops them)
+    s->hold_left--;
+    s->held = r;
+    s->held_pub = pub;
+    s->held_until = host_ns() + (uint64_t)s->cfg.fault_hold_publish_us * 1000ULL;
+  } else {
+    *(volatile unsigned long long *)&s->hs->published = pub;
+  }
   s->in_flight_items += need;
   s->tiles_run += need;
   return true;
@@ -909,6 +931,10 @@ void manage_executor(cc_server *s) {
     // the executor has left (asked to, or after its own bounded wait); its
     // last completions may have become visible only now
     reap_executor(s, nullptr);
+    if (*(volatile unsigned int *)&s->hs->exec_err) {  // a publish wait expired
+      *(volatile unsigned int *)&s->hs->exec_err = 0u;
+      s->executor_timeouts++;
+    }
     if (s->in_flight_items > 0) {
       // it left without finishing: fail what was in flight (not expected
       // unless the host stalled for longer than the executor's wait limit)
@@ -920,6 +946,9 @@ void manage_executor(cc_server *s) {
         complete(s, r, CC_ERR_TIMEOUT);
         finish_graph_request(s->graphs[r->graph]);
       }
+      // tiles held back by the fault injection are never published: the
+      // ring positions after `published` are written again by later requests
+      s->held = nullptr;
     }
     unsigned long long pub = s->hs->published;
     cudaMemcpyAsync(&s->ds->taken, &pub, sizeof(pub), cudaMemcpyHostToDevice, s->exec_stream);
@@ -928,11 +957,16 @@ void manage_executor(cc_server *s) {
     s->exec_running = false;
     s->exec_stopping = false;
   }
+  if (s->held && now >= s->held_until) {  // the stuck producer publishes at last
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    *(volatile unsigned long long *)&s->hs->published = s->held_pub;
+    s->held = nullptr;
+  }
   if (s->in_flight_items > 0) {
     s->idle_since = 0;
     if (!s->exec_running) {
       const unsigned grid = (unsigned)(cc::num_sms() * s->cfg.executor_blocks_per_sm);
-      cc::srv::k_executor<<<grid, 256, 0, s->exec_stream>>>(s->hs_dev, s->ds);
+      cc::srv::k_executor<<<grid, 256, 0, s->exec_stream>>>(s->hs_dev, s->ds, s->wait_ns, s->gate_ns);
       cc::note_launch();
       cudaEventRecord(s->exec_ev, s->exec_stream);
       s->exec_running = true;
@@ -1133,7 +1167,7 @@ cudaError_t warm_up(cc_server *s) {
   // the executor: told to leave before it starts
   if (e == cudaSuccess) {
     *(volatile unsigned int *)&s->hs->stop = 1u;
-    cc::srv::k_executor<<<1, 256, 0, s->exec_stream>>>(s->hs_dev, s->ds);
+    cc::srv::k_executor<<<1, 256, 0, s->exec_stream>>>(s->hs_dev, s->ds, s->wait_ns, s->gate_ns);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->exec_stream);
     *(volatile unsigned int *)&s->hs->stop = 0u;
@@ -1185,9 +1219,15 @@ cc_status cc_server_create(const cc_server_config *cfg_in, cc_server **out) {
     return CC_ERR_INVALID_ARGUMENT;
   for (int r : cfg.reserved)
     if (r) return CC_ERR_INVALID_ARGUMENT;
+  constexpr uint32_t kMaxWaitUs = 600u * 1000u * 1000u;  // 10 minutes
+  if (cfg.publish_wait_us > kMaxWaitUs || cfg.gate_wait_us > kMaxWaitUs || cfg.fault_hold_publish_us > kMaxWaitUs)
+    return CC_ERR_INVALID_ARGUMENT;
   cc_server *s = new (std::nothrow) cc_server();
   if (!s) return CC_ERR_OOM;
   s->cfg = cfg;
+  s->wait_ns = cfg.publish_wait_us ? (unsigned long long)cfg.publish_wait_us * 1000ULL : cc::srv::kWaitLimitNs;
+  s->gate_ns = cfg.gate_wait_us ? (unsigned long long)cfg.gate_wait_us * 1000ULL : cc::srv::kGateTimeoutNs;
+  s->hold_left = cfg.fault_hold_publish_us ? 1u : 0u;
   cudaError_t e = cudaGetDevice(&s->device);
   if (e == cudaSuccess) e = cudaMalloc((void **)&s->arena_base, cfg.hbm_budget_bytes);
   if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->hs, sizeof(HostShared), cudaHostAllocMapped);
@@ -1339,6 +1379,7 @@ cc_status cc_server_get_stats(cc_server *s, cc_server_stats *st) {
   st->executor_launches = s->executor_launches;
   st->tiles_run = s->tiles_run;
   st->side_drains = s->side_drains;
+  st->executor_timeouts = s->executor_timeouts;
   return CC_OK;
 }
 

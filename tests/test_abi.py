@@ -60,9 +60,11 @@ def test_options_layout_matches_header(tmp_path, lib):
 def test_batch_and_server_layouts_match_headers(tmp_path, lib):
     c = tmp_path / "layout2.c"
     c.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "cc_batch.h"\n#include "cc_server.h"\n'
-                 'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(cc_batch_config),'
+                 'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(cc_batch_config),'
                  'offsetof(cc_batch_config, tile_vertices), sizeof(cc_request), offsetof(cc_request, labels_dev),'
-                 'sizeof(cc_server_config), offsetof(cc_server_config, label_space), sizeof(cc_server_stats));'
+                 'sizeof(cc_server_config), offsetof(cc_server_config, label_space), sizeof(cc_server_stats),'
+                 'offsetof(cc_batch_config, barrier_wait_us), offsetof(cc_server_config, publish_wait_us),'
+                 'offsetof(cc_server_config, fault_hold_publish_us), offsetof(cc_server_stats, executor_timeouts));'
                  'return 0;}\n')
     exe = tmp_path / "layout2"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(c)])
@@ -70,7 +72,9 @@ def test_batch_and_server_layouts_match_headers(tmp_path, lib):
     assert got == [ctypes.sizeof(lib.cc_batch_config), lib.cc_batch_config.tile_vertices.offset,
                    ctypes.sizeof(lib.cc_request), lib.cc_request.labels_dev.offset,
                    ctypes.sizeof(lib.cc_server_config), lib.cc_server_config.label_space.offset,
-                   ctypes.sizeof(lib.cc_server_stats)]
+                   ctypes.sizeof(lib.cc_server_stats), lib.cc_batch_config.barrier_wait_us.offset,
+                   lib.cc_server_config.publish_wait_us.offset, lib.cc_server_config.fault_hold_publish_us.offset,
+                   lib.cc_server_stats.executor_timeouts.offset]
 
 
 def test_defaults_and_status_strings(lib):
