@@ -124,8 +124,8 @@ def kernel_source_sha() -> str:
         text = f.read()
     start = text.index("k_edge_pass_filtered(const uint4")  # the definition, not a launch
     start = text.rindex("template", 0, start)
-    grab = text.index("constexpr uint64_t kGrab")  # the dynamic schedule's claim size
-    h.update(text[grab:text.index("\n", grab)].encode())
+    grab = text.index("uint32_t grab_for(")  # the dynamic schedule's claim size
+    h.update(text[grab:text.index("\n}\n", grab)].encode())
     depth, i = 0, text.index("{", start)
     while True:
         if text[i] == "{":
@@ -613,6 +613,16 @@ def bench_batched(args, cc, graphgen, torch, stream):
     L = torch.empty(V, dtype=torch.int32, device="cuda")
     b = cc.Batch(G)
     best, tune_ms = b.tune(G, d.vtx_off, d.edge_off, d.edges, L, stream=stream)
+    table = sorted(cc.cc_batch_tune_results(b.h), key=lambda r: r[1])
+    best2, tune_ms2 = b.tune(G, d.vtx_off, d.edge_off, d.edges, L, stream=stream)  # stability: tune again
+    if best2 != best:  # keep the faster of the two choices
+        cc.cc_batch_set_config(b.h, **(best if tune_ms <= tune_ms2 else best2))
+    tuner = {"first": {"config": best, "ms": tune_ms}, "second": {"config": best2, "ms": tune_ms2},
+             "same_choice": best2 == best,
+             "runner_up": {"config": table[1][0], "ms": table[1][1]} if len(table) > 1 else None,
+             "within_5pct_of_best": sum(1 for _, t in table if t <= table[0][1] * 1.05),
+             "candidates": len(table), "slowest_ms": table[-1][1] if table else None}
+    best = best if tune_ms <= tune_ms2 else best2
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         b.run(G, d.vtx_off, d.edge_off, d.edges, L, stream=s)
@@ -661,12 +671,21 @@ def bench_batched(args, cc, graphgen, torch, stream):
         h.close()
     med = percentile(lat, 50)
     pmed = percentile(plain_ms, 50)
+    peak, peak_kind = measured_peaks()
+    alg = 8 * E + 12 * V
     return {"workload": f"{G} graphs (40% G(n,m), 40% R-MAT, 20% grid p=0.9), |V| log-uniform in [2^8,2^18)",
             "n_vertices": V, "n_edges": E, "gteps": E / (med * 1e-3) / 1e9, "ms_p50": med,
-            "ms_p99": percentile(lat, 99), "runs": reps, "tuned_config": best,
+            "ms_p99": percentile(lat, 99), "runs": reps, "tuned_config": best, "tuner": tuner,
             "plain_gteps": E / (pmed * 1e-3) / 1e9, "plain_ms_p50": pmed, "plain_ms_p99": percentile(plain_ms, 99),
             "speedup_vs_plain": pmed / med, "labels_equal_plain": same,
-            "launch": "one cooperative persistent kernel, replayed from a CUDA graph"}
+            "launch": "one cooperative persistent kernel, replayed from a CUDA graph",
+            "roofline": {"bound": "hbm", "achieved": alg / (med * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / (med * 1e-3) / 1e9 / peak, "traffic": None,
+                         "algorithmic_bytes_per_launch": alg,
+                         "algorithmic_bytes": "8 B per edge + 12 B per vertex (init write, compression "
+                                              "read, label write)",
+                         "kernel": "k_batched, one launch per replay; time = median replay (CUDA events)",
+                         "peak_source": f"{peak_kind} (HBM copy bandwidth)"}}
 
 
 def bench_serving(args, cc, graphgen, torch):
@@ -799,18 +818,66 @@ def bench_serving(args, cc, graphgen, torch):
             "edges_per_s": edges_total / makespan, "plain_edges_per_s": edges_total / max(done[-1], arrivals[-1]),
             "executor_launches": st["executor_launches"], "side_drains": st["side_drains"],
         })
+    executor = bench_executor(cc, torch, n, e_res, pool, qpool, qout)
     del pool, qpool, new_edges, snap, e_res
     torch.cuda.empty_cache()
     return {"resident": w.name, "requests_per_rate": R,
             "mix": "45% inserts (10^3..10^7 uniform pairs), 45% queries (10^4 pairs), 5% snapshots, "
                    "5% new R-MAT graphs scale 12..22 (each dropped 5 requests later)",
-            "plain_capacity_req_per_s": capacity, "rates": results,
+            "plain_capacity_req_per_s": capacity, "rates": results, "executor": executor,
             "latency": "serving runtime: arrival to completion, host clock, measured",
             "plain_latency": "FIFO recurrence over measured alone service times (each request run alone, "
                              "synchronously, on the plain single-graph calls; queueing computed, not run)",
             "throughput_note": "below saturation (loads 0.25/0.5/0.9) both paths complete requests as they "
                                "arrive, so throughput is arrival-bound and equal; the wins there are p50/p99 "
                                "latency. The burst (every request at once) compares saturated throughput"}
+
+
+def bench_executor(cc, torch, n, e_res, pool, qpool, qout):
+    """Throughput of the serving executor alone: bursts of equal insert
+    batches (2^17 uniform pairs each, below the side-stream size, so all run as
+    executor tiles on the live parent array of the resident graph) and of
+    query batches (10^4 pairs), submitted at once and timed on the host from
+    the first submission to the last completion (host scheduling included)."""
+    import time
+    peak, peak_kind = measured_peaks()
+    out = {}
+    srv = cc.Server(24 << 30, idle_timeout_us=200000)
+    try:
+        t, gid = srv.new_graph(n, e_res)
+        if srv.wait(t, 120) != cc.CC_OK:
+            raise RuntimeError("resident graph admission failed")
+        size, K = 1 << 17, 512
+        span = pool.shape[0] - size
+        batches = [pool[(i * 104729) % span:(i * 104729) % span + size] for i in range(K)]
+        q_batches = [qpool[(i * 7919) % (qpool.shape[0] - 10 ** 4):(i * 7919) % (qpool.shape[0] - 10 ** 4) + 10 ** 4]
+                     for i in range(K)]
+        for kind in ("insert", "query"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if kind == "insert":
+                tickets = [srv.insert(gid, b) for b in batches]
+            else:
+                tickets = [srv.query(gid, q, qout[i % 64 * 10 ** 4:(i % 64 + 1) * 10 ** 4])
+                           for i, q in enumerate(q_batches)]
+            for tk in tickets:
+                if srv.wait(tk, 120) != cc.CC_OK:
+                    raise RuntimeError(f"executor {kind} burst failed")
+            dt = time.perf_counter() - t0
+            units = K * (size if kind == "insert" else 10 ** 4)
+            per_unit = 8 if kind == "insert" else 9
+            achieved = per_unit * units / dt / 1e9
+            out[kind] = {"requests": K, "units": units, "seconds": dt,
+                         ("edges_per_s" if kind == "insert" else "pairs_per_s"): units / dt,
+                         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                      "frac": achieved / peak, "traffic": None,
+                                      "algorithmic_bytes": "8 B per inserted edge" if kind == "insert"
+                                      else "8 B per query pair read + 1 B answer written",
+                                      "timing": "host clock over the burst (submission to last completion)",
+                                      "peak_source": f"{peak_kind} (HBM copy bandwidth)"}}
+    finally:
+        srv.close()
+    return out
 
 
 def main(argv=None):

@@ -68,6 +68,13 @@ CC_API cc_status cc_batch_tune(cc_batch *b, uint32_t n_graphs, const uint64_t *v
                                uint32_t *L_out_dev, cc_stream_t stream, cc_batch_config *best,
                                float *best_ms);
 
+/* The candidates timed by the last cc_batch_tune on this context, in the
+ * order tried, each with its best time in ms (the spread between them shows
+ * how decisive the choice was). Copies min(cap, count) entries; *count
+ * receives how many there are (0 before any tuning). Not synchronising. */
+CC_API cc_status cc_batch_tune_results(const cc_batch *b, cc_batch_config *cfgs, float *ms, uint32_t cap,
+                                       uint32_t *count);
+
 CC_API cc_status cc_batch_set_config(cc_batch *b, const cc_batch_config *cfg);
 CC_API cc_status cc_batch_get_config(const cc_batch *b, cc_batch_config *cfg);
 

@@ -128,6 +128,7 @@ def lib():
             "cc_batch_tune": (_i32, [_ptr, _u32, _ptr, _ptr, _ptr, _ptr, _ptr, P(cc_batch_config),
                                      P(ctypes.c_float)]),
             "cc_batch_set_config": (_i32, [_ptr, P(cc_batch_config)]),
+            "cc_batch_tune_results": (_i32, [_ptr, P(cc_batch_config), P(ctypes.c_float), _u32, P(_u32)]),
             "cc_batch_get_config": (_i32, [_ptr, P(cc_batch_config)]),
             "cc_batch_sync": (_i32, [_ptr]),
             "cc_batch_destroy": (None, [_ptr]),
@@ -410,6 +411,15 @@ def cc_batch_tune(b: int, n_graphs: int, vtx_off, edge_off, edges, L_out, stream
     _check(lib().cc_batch_tune(b, n_graphs, _addr(vtx_off), _addr(edge_off), _addr(edges), _addr(L_out),
                                _stream(stream), ctypes.byref(cfg), ctypes.byref(ms)), "cc_batch_tune")
     return cfg.as_dict(), float(ms.value)
+
+
+def cc_batch_tune_results(b: int) -> list:
+    """[(config dict, best ms)] of every candidate of the last cc_batch_tune."""
+    cfgs = (cc_batch_config * 64)()
+    ms = (ctypes.c_float * 64)()
+    count = _u32(0)
+    _check(lib().cc_batch_tune_results(b, cfgs, ms, 64, ctypes.byref(count)), "cc_batch_tune_results")
+    return [(cfgs[i].as_dict(), float(ms[i])) for i in range(min(count.value, 64))]
 
 
 def cc_batch_set_config(b: int, **cfg) -> None:

@@ -446,6 +446,17 @@ static cc_status run_host_impl(cc_graph *g, const void *edges_host, uint64_t n_e
   g->z_auto_ok = chunked && !g->z_forced;
   uint32_t *Zf = g->z_forced ? g->z : nullptr;
   if (!select) CC_TRY(cc::launch_init(g->rf, g->P, n, g->ctrl, cc::kMFromHint, hint, s));
+  // Chunks hooked under a speculative m' use the bitmap too when the first
+  // chunk's sample showed a hub (its bits name the tree of m', and are
+  // cleared before a rerun under another vertex); the hub-mode word picks
+  // the instance on the device.
+  uint32_t *Zc = Zf;
+  const uint32_t *zc_sel = nullptr, *hub_c = nullptr;
+  if (chunked && !g->z_forced) {
+    hub_c = &g->ctrl->skip[cc::kSkipHist];
+    Zc = g->z;
+    zc_sel = g->z ? hub_c : nullptr;
+  }
   // the copy stream starts after everything already enqueued on s
   CC_TRY(cudaEventRecord(g->copy_ev, s));
   CC_TRY(cudaStreamWaitEvent(g->copy_stream, g->copy_ev, 0));
@@ -475,7 +486,7 @@ static cc_status run_host_impl(cc_graph *g, const void *edges_host, uint64_t n_e
     // every chunk is hooked as it lands, under m' when m is still unknown
     if (chunked && off == 0) CC_TRY(cc::launch_init(true, g->P, n, g->ctrl, cc::kMFromPackedMax, 0u, s));
     CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), chunk, g->P, n, g->ctrl, nullptr,
-                                s, Zf, nullptr, false, nullptr, nullptr, true));
+                                s, Zc, zc_sel, false, nullptr, hub_c, true));
   }
   const cc::EdgeSpan all = cc::split_edges(g->staging, n_edges);
   if (chunked) {
@@ -486,7 +497,7 @@ static cc_status run_host_impl(cc_graph *g, const void *edges_host, uint64_t n_e
     // a rerun starts from a fresh P in which another vertex holds name 0, so
     // a forced bitmap must start empty again (when m' held, the reset only
     // forgets bits: an empty bitmap is always valid)
-    if (Zf) CC_TRY(cudaMemsetAsync(Zf, 0, g->z_bytes, s));
+    if (Zc) CC_TRY(cudaMemsetAsync(Zc, 0, g->z_bytes, s));
     CC_TRY(cc::launch_edge_pass(true, eff_filter(g), eff_ept(g), eff_block(g), all, g->P, n, g->ctrl, held, s,
                                 g->z, Zf ? nullptr : &g->ctrl->cert, false, nullptr, nullptr, true));
   } else if (select) {

@@ -312,6 +312,10 @@ struct cc_batch {
   BatchCtrl *host_ctrl = nullptr;
   uint64_t *tile_off = nullptr;  // 2 * (max_graphs + 1)
   cudaStream_t last = nullptr;
+  // the last cc_batch_tune: every candidate with its best time
+  cc_batch_config tuned[64];
+  float tuned_ms[64];
+  uint32_t n_tuned = 0;
 };
 
 namespace {
@@ -458,6 +462,18 @@ cc_status cc_run_batched(cc_batch *b, uint32_t n_graphs, const uint64_t *vtx_off
   return enqueue(b, b->cfg, n_graphs, vtx_off_dev, edge_off_dev, edges_dev, L_out_dev, b->last);
 }
 
+cc_status cc_batch_tune_results(const cc_batch *b, cc_batch_config *cfgs, float *ms, uint32_t cap,
+                                uint32_t *count) {
+  if (!b || !count || (cap && (!cfgs || !ms))) return CC_ERR_INVALID_ARGUMENT;
+  const uint32_t k = b->n_tuned < cap ? b->n_tuned : cap;
+  for (uint32_t i = 0; i < k; ++i) {
+    cfgs[i] = b->tuned[i];
+    ms[i] = b->tuned_ms[i];
+  }
+  *count = b->n_tuned;
+  return CC_OK;
+}
+
 cc_status cc_batch_set_config(cc_batch *b, const cc_batch_config *cfg) {
   if (!b || !cfg || !cfg_valid(*cfg)) return CC_ERR_INVALID_ARGUMENT;
   b->cfg = *cfg;
@@ -510,6 +526,7 @@ cc_status cc_batch_tune(cc_batch *b, uint32_t n_graphs, const uint64_t *vtx_off_
   const uint32_t tiles[] = {4096, 16384, 65536};
   cc_batch_config top = b->cfg;
   float top_ms = 1e30f;
+  b->n_tuned = 0;
   for (int blk : blocks)
     for (int ept : epts)
       for (int flt : filters)
@@ -535,6 +552,10 @@ cc_status cc_batch_tune(cc_batch *b, uint32_t n_graphs, const uint64_t *vtx_off_
             if (rep > 0 && ms < ms_min) ms_min = ms;  // the first run warms up
           }
           if (st != CC_OK) break;
+          if (b->n_tuned < 64) {
+            b->tuned[b->n_tuned] = c;
+            b->tuned_ms[b->n_tuned++] = ms_min;
+          }
           if (ms_min < top_ms) {
             top_ms = ms_min;
             top = c;

@@ -151,16 +151,16 @@ __global__ void __launch_bounds__(512) k_edge_pass_direct(const uint4 *__restric
 // The hub-serving instances run only when *sel is nonzero, the other only
 // when it is zero; with sel null the launched instance runs.
 //
-// work: the dynamic schedule. Warps claim kGrab steps of 32 * Q consecutive
+// work: the dynamic schedule. Warps claim `grab` steps of 32 * Q consecutive
 // quads at a time from *work, so warps whose edges need long searches do not
 // set the end of the kernel; null: each warp takes a fixed stride of steps.
-constexpr uint64_t kGrab = 16;
+// The claim size is chosen by the launcher (grab_for).
 
 template <class F, int Q, bool kZ, bool kDirect>
 __global__ void __launch_bounds__(512, Q >= 4 ? (kZ ? 1 : 2) : (kZ ? 2 : (kDirect ? 4 : 3)))
     k_edge_pass_filtered(const uint4 *__restrict__ e4, uint64_t n_quads, const uint2 *head, const uint2 *tail,
                          uint32_t *P, uint32_t n, Ctrl *ctrl, const uint32_t *skip, uint32_t *Z,
-                         const uint32_t *sel, uint32_t *log, unsigned long long *work) {
+                         const uint32_t *sel, uint32_t *log, unsigned long long *work, uint32_t grab) {
   static_assert(kDirect || !kZ, "the zero-tree form resolves in place");
   extern __shared__ uint32_t ring_smem[];
   if (skip && ld_volatile_u32(skip)) return;
@@ -230,15 +230,15 @@ __global__ void __launch_bounds__(512, Q >= 4 ? (kZ ? 1 : 2) : (kZ ? 2 : (kDirec
     }
   };
   if (work) {
-    // dynamic: warps claim kGrab steps of 32 * Q consecutive quads at a time,
+    // dynamic: warps claim `grab` steps of 32 * Q consecutive quads at a time,
     // so warps whose edges need longer searches do not set the kernel's end
     const uint64_t steps = (n_quads + 32u * Q - 1) / (32u * Q);
     for (;;) {
       unsigned long long g0 = 0;
-      if (ring.lane == 0) g0 = atomicAdd(work, (unsigned long long)kGrab);
+      if (ring.lane == 0) g0 = atomicAdd(work, (unsigned long long)grab);
       g0 = __shfl_sync(0xFFFFFFFFu, g0, 0);
       if (g0 >= steps) break;
-      const uint64_t g1 = g0 + kGrab < steps ? g0 + kGrab : steps;
+      const uint64_t g1 = g0 + grab < steps ? g0 + grab : steps;
       for (uint64_t g = g0; g < g1; ++g) step(g * 32u * Q + ring.lane, 32u);
     }
   } else {
@@ -552,6 +552,20 @@ cudaError_t launch_init(bool rf, uint32_t *P, uint32_t n, Ctrl *ctrl, int m_src,
 namespace {
 constexpr uint64_t kMinWaves = 8;
 
+// Claim size of the dynamic schedule, in warp steps. From 2^20 edges up,
+// 16 steps at a time (measured best there: fewer warps start on the hub's
+// trees at once, so fewer CAS collide). Below that, a smaller graph would
+// leave most warps of the grid idle, so the claim shrinks to about half the
+// steps per warp (at least one).
+uint32_t grab_for(uint64_t n_quads, int Q, unsigned grid, int block) {
+  constexpr uint32_t kGrabMax = 16;
+  if (n_quads >= (1ULL << 19)) return kGrabMax;
+  const uint64_t steps = (n_quads + 32u * Q - 1) / (32u * Q);
+  const uint64_t warps = (uint64_t)grid * (uint64_t)(block / 32);
+  const uint64_t g = steps / (2 * (warps ? warps : 1));
+  return g < 1 ? 1u : (g > kGrabMax ? kGrabMax : (uint32_t)g);
+}
+
 template <class F, int Q>
 cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, uint32_t n, Ctrl *ctrl,
                         const uint32_t *skip, uint32_t *Z, const uint32_t *zsel, bool one_shot, uint32_t *log,
@@ -580,23 +594,26 @@ cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, u
     if (Z) {
       const void *k = (const void *)k_edge_pass_filtered<F, Q, true, true>;
       const unsigned g = clamp_grid(want, one_shot ? cap_big : persistent_cap(k, block, smem));
+      const uint32_t grab = grab_for(e.n_quads, Q, g, block);
       k_edge_pass_filtered<F, Q, true, true><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n, ctrl,
-                                                                    skip, Z, zsel, log, work);
+                                                                    skip, Z, zsel, log, work, grab);
       note_launch();
     }
     if (!Z && hub) {
       const void *k = (const void *)k_edge_pass_filtered<F, Q, false, false>;
       const unsigned g = clamp_grid(want, one_shot ? cap_big : persistent_cap(k, block, smem));
+      const uint32_t grab = grab_for(e.n_quads, Q, g, block);
       k_edge_pass_filtered<F, Q, false, false><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n,
-                                                                      ctrl, skip, nullptr, hub, log, work);
+                                                                      ctrl, skip, nullptr, hub, log, work, grab);
       note_launch();
     }
     if (!Z || zsel) {
       const void *k = (const void *)k_edge_pass_filtered<F, Q, false, true>;
       const unsigned g = clamp_grid(want, one_shot ? cap_big : persistent_cap(k, block, smem));
+      const uint32_t grab = grab_for(e.n_quads, Q, g, block);
       k_edge_pass_filtered<F, Q, false, true><<<g, block, smem, s>>>(e.quads, e.n_quads, e.head, e.tail, P, n,
                                                                      ctrl, skip, nullptr, Z ? zsel : hub, log,
-                                                                     work);
+                                                                     work, grab);
       note_launch();
     }
   } else {

@@ -92,9 +92,16 @@ def test_tune_then_run(small_batch):
     with cc.Batch(b.n_graphs) as bt:
         L = torch.empty(int(b.vtx_off[-1]), dtype=torch.int32, device="cuda")
         args = (b.n_graphs, dev(b.vtx_off, np.int64), dev(b.edge_off, np.int64), dev(b.edges, np.int32), L)
+        assert cc.cc_batch_tune_results(bt.h) == []
         best, ms = bt.tune(*args)
         assert ms > 0 and best["block_size"] in (256, 512)
         assert cc.cc_batch_get_config(bt.h) == best
+        # the candidate table: every block size x edges per thread x filter x
+        # tile size, the kept one being the fastest
+        table = cc.cc_batch_tune_results(bt.h)
+        assert len(table) == 2 * 3 * 2 * 3
+        assert min(t for _, t in table) == ms
+        assert [c for c, t in table if t == ms][0] == best
         L.fill_(-1)
         bt.run(*args)
         bt.sync()

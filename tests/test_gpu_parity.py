@@ -668,3 +668,54 @@ def test_root_select_many_candidates():
     e = e[rng.permutation(len(e))]
     _, _, m = run_labels(n, e, mode=cc.CC_ROOT_MAXDEG)
     assert m == oracle.max_degree_vertex(n, e)
+
+
+def _leader_not_max_graph():
+    """Hub A = 500 leads the root-selection sample (every second edge of the
+    sampled groups, one group of 1024 in 128) but hub B = 100, a candidate
+    with an eighth of A's sampled count, has the larger exact degree (most of
+    its edges lie in unsampled groups). Other endpoints avoid both hubs."""
+    n, E = 1 << 16, 1 << 18
+    rng = np.random.default_rng(13)
+    e = rng.integers(1000, n, size=(E, 2)).astype(np.uint32)
+    idx = np.arange(E)
+    sampled = (idx // 1024) % 128 == 0
+    e[sampled & (idx % 2 == 0), 0] = 500
+    e[sampled & (idx % 16 == 1), 1] = 100
+    e[np.flatnonzero(~sampled)[:3000], 1] = 100
+    deg = np.bincount(e.ravel(), minlength=n)
+    assert deg[100] > deg[500] > deg[1000:].max()
+    return n, e
+
+
+@pytest.mark.parametrize("flt", [cc.CC_FILTER_AUTO, cc.CC_FILTER_BITMAP])
+def test_sampled_leader_is_not_the_exact_m(flt):
+    """The certificate proves a vertex other than the sampled leader. On
+    device input (cc_run) the exact selection plants that vertex; on host
+    input (cc_run_host) the chunks are first hooked under the sampled leader
+    m', then init and one edge pass run again under the exact m, with the
+    zero-tree bitmap cleared of the bits set under m'. m, the labels in both
+    spaces and the component count equal the oracle's, on a fresh handle and
+    on reuse."""
+    n, e = _leader_not_max_graph()
+    m_want = oracle.max_degree_vertex(n, e)
+    assert m_want == 100
+    want = oracle.min_labels(n, e)
+    h_e = torch.from_numpy(np.ascontiguousarray(e).view(np.int32)).pin_memory()
+    for label_space in (cc.CC_LABEL_MIN_ID, cc.CC_LABEL_ROOT_VALUE):
+        want_l = want if label_space == cc.CC_LABEL_MIN_ID else oracle.root_value_labels(n, e, m_want)
+        with cc.Graph(n, len(e), filter=flt, label_space=label_space) as g:
+            L = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+            h_L = torch.full((n,), -1, dtype=torch.int32).pin_memory()
+            d = dev_edges(e)
+            for _ in range(2):
+                g.run(d, L)
+                g.sync()
+                assert g.root_vertex() == m_want
+                assert g.num_components() == oracle.num_components(want)
+                np.testing.assert_array_equal(L.cpu().numpy().view(np.uint32), want_l)
+                h_L.fill_(-1)
+                cc.cc_run_host(g.h, h_e, len(e), h_L)
+                assert g.root_vertex() == m_want
+                assert g.num_components() == oracle.num_components(want)
+                np.testing.assert_array_equal(h_L.numpy().view(np.uint32), want_l)
