@@ -27,7 +27,10 @@
  * Ordering. Per graph, requests take effect in submission order: a query or
  * snapshot sees exactly the inserts submitted before it for that graph.
  * Consecutive inserts run together, and so do consecutive reads (queries
- * and snapshots).
+ * and snapshots). A snapshot reads a copy of the graph's parent array taken
+ * when it starts (one device copy of 4 bytes per vertex), so inserts
+ * submitted after it start as soon as that copy has run, while the snapshot
+ * still computes its labels; one snapshot per graph computes at a time.
  *
  * Memory. The server owns one device arena of hbm_budget_bytes, allocated at
  * creation; graphs are placed in it by first fit and a new graph waits until
@@ -114,6 +117,7 @@ typedef struct cc_server_stats {
   uint64_t executor_launches, tiles_run;
   uint64_t side_drains;  /* executor drains forced by starved side-stream work */
   uint64_t executor_timeouts;  /* executor launches that ended on an expired publish wait */
+  uint64_t snapshot_overlaps;  /* inserts started while a snapshot of their graph still computed */
 } cc_server_stats;
 
 CC_API void cc_server_config_init(cc_server_config *cfg);

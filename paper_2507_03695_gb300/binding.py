@@ -73,7 +73,7 @@ class cc_server_config(ctypes.Structure):
 class cc_server_stats(ctypes.Structure):
     _fields_ = [(k, _u64) for k in ("submitted", "completed", "failed", "resident_graphs", "arena_bytes_used",
                                     "arena_bytes", "executor_launches", "tiles_run", "side_drains",
-                                    "executor_timeouts")]
+                                    "executor_timeouts", "snapshot_overlaps")]
 
 
 CC_REQ_NEW_GRAPH, CC_REQ_INSERT, CC_REQ_QUERY, CC_REQ_SNAPSHOT, CC_REQ_DROP_GRAPH = 1, 2, 3, 4, 5

@@ -99,7 +99,12 @@ cudaError_t launch_init(bool rf, uint32_t *P, uint32_t n, Ctrl *ctrl, int m_src,
 constexpr uint32_t kCertCand = 4096;     // more candidates than this: no proof is tried
 constexpr uint32_t kCertBuckets = 8192;  // hash buckets of the degree bound
 constexpr uint32_t kCertTop = 4;         // candidates whose degree is counted exactly
-constexpr uint32_t kCertSample = 128;    // the sampled pass keeps 1 group of 1024 edges in this many
+// Build option CC_CERT_SAMPLE: the sampled pass keeps 1 group of 1024 edges
+// in this many (default 128).
+#ifndef CC_CERT_SAMPLE
+#define CC_CERT_SAMPLE 128
+#endif
+constexpr uint32_t kCertSample = CC_CERT_SAMPLE;
 struct CertScratch {
   unsigned long long owner[kCertBuckets];   // per bucket, its best sampled (count << 32) | ~vertex; 0 = none
   unsigned long long top[kCertTop];         // the best owners, same packing; 0 = empty slot

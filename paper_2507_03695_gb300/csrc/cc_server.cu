@@ -457,6 +457,10 @@ struct Req {
   cudaEvent_t ev = nullptr;
   uint64_t t_side = 0;  // side-stream work issued (or the executor last drained for it) at
   int flag = -1;        // side insert: index of its pinned rejection word
+  // snapshot: its read point (the copy of P) and whether the graph's later
+  // requests were released once that point had passed
+  cudaEvent_t ev_point = nullptr;
+  bool detached = false;
 };
 
 struct GraphState {
@@ -469,10 +473,15 @@ struct GraphState {
   cc::Ctrl *ctrl = nullptr;
   uint32_t *Z = nullptr;  // zero-tree bitmap (large graphs under R), or null
   uint64_t z_bytes = 0;
-  // incremental snapshots: last labels, changed-root log, label remap, bitmap
-  uint32_t *Llast = nullptr, *log = nullptr, *rem = nullptr, *chg = nullptr, *words = nullptr;
+  // incremental snapshots: last labels, two changed-root logs (inserts append
+  // to logs[cur_log]; a snapshot takes the other one over), label remap,
+  // bitmap, and the copy of P that a snapshot reads
+  uint32_t *Llast = nullptr, *rem = nullptr, *chg = nullptr, *words = nullptr, *Psnap = nullptr;
+  uint32_t *logs[2] = {nullptr, nullptr};
+  int cur_log = 0;
   uint64_t chg_bytes = 0;
-  bool has_last = false;  // Llast holds the labels of a snapshot (or of the admission)
+  bool has_last = false;   // Llast holds the labels of a snapshot (or of the admission)
+  bool snap_busy = false;  // a snapshot still computes from Psnap and its log
   uint32_t m = 0;
   std::deque<Req *> fifo;
   int group = kIdle;
@@ -508,7 +517,7 @@ struct cc_server {
   std::mutex done_mu;
   std::condition_variable done_cv;
   std::atomic<uint64_t> submitted{0}, completed{0}, failed{0}, executor_launches{0}, tiles_run{0};
-  std::atomic<uint64_t> arena_used{0}, resident{0}, side_drains{0};
+  std::atomic<uint64_t> arena_used{0}, resident{0}, side_drains{0}, snapshot_overlaps{0};
   // scheduler-thread state
   Arena arena;
   std::vector<GraphState> graphs;
@@ -535,10 +544,11 @@ namespace {
 bool wants_z(uint64_t n, bool rf) { return rf && n * 4 >= cc::srv::kZMinBytes; }
 uint64_t z_bytes_for(uint64_t n) { return (n + 1 + 31) / 32 * 4; }
 
-// Incremental-snapshot buffers: labels (n), log (count + n), remap (n + 1:
-// root-value labels reach n), changed-label bitmap, a few words.
+// Incremental-snapshot buffers: labels (n), two logs (count + n each), remap
+// (n + 1: root-value labels reach n), changed-label bitmap, a few words, and
+// the snapshot's copy of P (n).
 uint64_t inc_bytes(uint64_t n) {
-  return align256((size_t)((n + 3) / 4 * 4) * 4) + align256((size_t)(n + 1) * 4) + align256((size_t)(n + 1) * 4) +
+  return 2 * align256((size_t)((n + 3) / 4 * 4) * 4) + 3 * align256((size_t)(n + 1) * 4) +
          align256((size_t)((n + 1 + 31) / 32) * 4) + align256(16);
 }
 
@@ -561,12 +571,16 @@ void complete(cc_server *s, Req *r, cc_status st) {
   if (st != CC_OK) s->failed++;
 }
 
-// Elements per tile: enough tiles to spread a request over every executor
-// block twice, at least at_least, at most the configured tile size, and few
-// enough to fit the ring.
+// Elements per tile: with an idle executor, enough tiles to spread a request
+// over every executor block twice (latency); the more tiles already wait in
+// the ring, the fewer and larger the new request's tiles (a backlog keeps the
+// blocks busy anyway, and every tile costs a claim, a wait on the host ring
+// and an item read from host memory). At least at_least, at most the
+// configured tile size, and few enough to fit the ring.
 uint64_t tile_for(const cc_server *s, uint64_t count, uint64_t at_least) {
   const uint64_t blocks = (uint64_t)cc::num_sms() * s->cfg.executor_blocks_per_sm;
-  uint64_t t = (count + 2 * blocks - 1) / (2 * blocks);
+  const uint64_t spread = 2 * blocks * blocks / (blocks + s->in_flight_items);
+  uint64_t t = (count + spread - 1) / (spread ? spread : 1);
   t = (t + 255) / 256 * 256;
   if (t < at_least) t = at_least;
   if (t > s->cfg.tile_edges) t = s->cfg.tile_edges;
@@ -595,7 +609,7 @@ void write_tiles(cc_server *s, const Req &r, uint32_t kind, uint64_t count, cons
     w.begin = i * tile;
     w.end = w.begin + tile < count ? w.begin + tile : count;
     w.out = (uint64_t)(uintptr_t)r.r.out_dev;
-    w.log = (uint64_t)(uintptr_t)g.log;
+    w.log = (uint64_t)(uintptr_t)g.logs[g.cur_log];
   }
   pub += nt;
 }
@@ -691,8 +705,14 @@ bool start_new_graph(cc_server *s, Req *r, GraphState &g) {
   }
   g.Llast = reinterpret_cast<uint32_t *>(p);
   p += align256((size_t)((g.n + 3) / 4 * 4) * 4);
-  g.log = reinterpret_cast<uint32_t *>(p);
+  g.logs[0] = reinterpret_cast<uint32_t *>(p);
   p += align256((size_t)(g.n + 1) * 4);
+  g.logs[1] = reinterpret_cast<uint32_t *>(p);
+  p += align256((size_t)(g.n + 1) * 4);
+  g.cur_log = 0;
+  g.snap_busy = false;
+  g.Psnap = reinterpret_cast<uint32_t *>(p);
+  p += align256((size_t)((g.n + 3) / 4 * 4) * 4);
   g.rem = reinterpret_cast<uint32_t *>(p);
   p += align256((size_t)(g.n + 1) * 4);
   g.chg = reinterpret_cast<uint32_t *>(p);
@@ -704,6 +724,7 @@ bool start_new_graph(cc_server *s, Req *r, GraphState &g) {
   cudaError_t e = cudaMemsetAsync(g.ctrl, 0, sizeof(cc::Ctrl), ss);
   if (e == cudaSuccess && g.Z) e = cudaMemsetAsync(g.Z, 0, g.z_bytes, ss);
   if (e == cudaSuccess) e = cudaMemsetAsync(g.chg, 0, g.chg_bytes, ss);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g.logs[1], 0, sizeof(uint32_t), ss);  // logs[0] is emptied below
   const uint32_t n = (uint32_t)g.n;
   const cc::EdgeSpan span = cc::split_edges(r->r.edges_dev, r->r.n_edges);
   int m_src = cc::kMFromHint;
@@ -723,7 +744,7 @@ bool start_new_graph(cc_server *s, Req *r, GraphState &g) {
   if (e == cudaSuccess && g.has_last)
     e = cudaMemcpyAsync(r->r.labels_dev, g.Llast, (size_t)n * 4, cudaMemcpyDeviceToDevice, ss);
   if (e == cudaSuccess) {
-    cc::srv::k_srv_inc_finish<<<1, 1, 0, ss>>>(g.log, g.words, g.ctrl);  // empty log, gmin of these labels
+    cc::srv::k_srv_inc_finish<<<1, 1, 0, ss>>>(g.logs[0], g.words, g.ctrl);  // empty log, gmin of these labels
     cc::note_launch();
     e = cudaGetLastError();
   }
@@ -743,39 +764,56 @@ bool start_new_graph(cc_server *s, Req *r, GraphState &g) {
   return true;
 }
 
+// A snapshot reads a copy of P taken on the graph's side stream (its read
+// point, an event) and takes over the changed-root log of the inserts before
+// it; inserts submitted after it append to the other log and may start as
+// soon as the copy has run, while the relabelling still works on the copy.
+// One snapshot per graph computes at a time.
 bool start_snapshot(cc_server *s, Req *r, GraphState &g) {
   if (s->side_running.size() >= cc::srv::kMaxSideRunning) return false;
+  if (g.snap_busy) return false;
   r->state.store(kRunning);
   cudaStream_t ss = side_stream_of(s, r->graph);
   cudaError_t e = cudaSuccess;
-  if (g.n && !g.has_last) {
+  uint32_t *const log = g.logs[g.cur_log];
+  if (g.n) {
+    e = cudaMemcpyAsync(g.Psnap, g.P, (size_t)((g.n + 3) / 4 * 4) * 4, cudaMemcpyDeviceToDevice, ss);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev_point, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(r->ev_point, ss);
+    if (e == cudaSuccess) {
+      g.cur_log ^= 1;  // later inserts log into the other (empty) log
+      g.snap_busy = true;
+    }
+  }
+  if (e == cudaSuccess && g.n && !g.has_last) {
     // the first snapshot: a full flatten into the graph's copy, then the
     // caller's buffer; the log starts over
     const uint32_t n = (uint32_t)g.n;
     cc::srv::k_srv_prep_flatten<<<1, 1, 0, ss>>>(g.ctrl);
     cc::note_launch();
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = cc::launch_flatten(g.rf, s->cfg.label_space, g.P, n, g.Llast, g.ctrl, ss);
+    if (e == cudaSuccess) e = cc::launch_flatten(g.rf, s->cfg.label_space, g.Psnap, n, g.Llast, g.ctrl, ss);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(r->r.labels_dev, g.Llast, (size_t)n * 4, cudaMemcpyDeviceToDevice, ss);
     if (e == cudaSuccess) {
-      cc::srv::k_srv_inc_finish<<<1, 1, 0, ss>>>(g.log, g.words, g.ctrl);
+      cc::srv::k_srv_inc_finish<<<1, 1, 0, ss>>>(log, g.words, g.ctrl);
       cc::note_launch();
       e = cudaGetLastError();
     }
-    g.has_last = true;
-  } else if (g.n) {
+    if (e == cudaSuccess) g.has_last = true;
+  } else if (e == cudaSuccess && g.n) {
     // incremental: remap the labels the logged roots led, rewrite Llast
     const uint32_t n = (uint32_t)g.n;
     const uint32_t min_id = s->cfg.label_space == cc::kLabelMinId ? 1u : 0u;
     cc::srv::k_srv_prep_flatten<<<1, 1, 0, ss>>>(g.ctrl);
     cc::note_launch();
     e = cudaGetLastError();
-    if (e == cudaSuccess && g.rf && min_id) e = cc::launch_gmin_probe(g.P, n, g.ctrl, ss);
+    if (e == cudaSuccess && g.rf && min_id) e = cc::launch_gmin_probe(g.Psnap, n, g.ctrl, ss);
     if (e == cudaSuccess) {
       const unsigned gr = cc::clamp_grid(((uint64_t)n + 255) / 256,
                                          cc::persistent_cap((const void *)cc::srv::k_srv_inc_remap, 256, 0));
-      cc::srv::k_srv_inc_remap<<<gr, 256, 0, ss>>>(g.P, g.rf ? 1u : 0u, min_id, g.log, g.rem, g.chg, g.words, g.ctrl);
+      cc::srv::k_srv_inc_remap<<<gr, 256, 0, ss>>>(g.Psnap, g.rf ? 1u : 0u, min_id, log, g.rem, g.chg, g.words,
+                                                   g.ctrl);
       cc::note_launch();
       const unsigned gl = cc::clamp_grid(((uint64_t)n + 255) / 256,
                                          cc::persistent_cap((const void *)cc::srv::k_srv_inc_relabel, 256, 0));
@@ -785,7 +823,7 @@ bool start_snapshot(cc_server *s, Req *r, GraphState &g) {
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(g.chg, 0, g.chg_bytes, ss);
     if (e == cudaSuccess) {
-      cc::srv::k_srv_inc_finish<<<1, 1, 0, ss>>>(g.log, g.words, g.ctrl);
+      cc::srv::k_srv_inc_finish<<<1, 1, 0, ss>>>(log, g.words, g.ctrl);
       cc::note_launch();
       e = cudaGetLastError();
     }
@@ -793,6 +831,9 @@ bool start_snapshot(cc_server *s, Req *r, GraphState &g) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(r->ev, ss);
   if (e != cudaSuccess) {
+    // the stream's work is unknown: wait for it before the graph moves on
+    cudaStreamSynchronize(ss);
+    g.snap_busy = false;
     complete(s, r, CC_ERR_CUDA);
     return true;
   }
@@ -812,7 +853,9 @@ bool start_side_insert(cc_server *s, Req *r, GraphState &g) {
   s->free_flags.pop_back();
   s->side_flags[r->flag] = 0u;
   r->state.store(kRunning);
+  // not the graph's own side stream, where a snapshot of it may still compute
   cudaStream_t ss = s->side_streams[s->next_side++ % cc::srv::kSideStreams];
+  if (ss == side_stream_of(s, r->graph)) ss = s->side_streams[s->next_side++ % cc::srv::kSideStreams];
   const uint32_t n = (uint32_t)g.n;
   const cc::EdgeSpan span = cc::split_edges(r->r.edges_dev, r->r.n_edges);
   uint32_t *rej = s->side_reject + r->flag;
@@ -820,7 +863,7 @@ bool start_side_insert(cc_server *s, Req *r, GraphState &g) {
   if (e == cudaSuccess) e = cc::launch_validate(span, n, g.ctrl, ss, rej);
   if (e == cudaSuccess)
     e = cc::launch_edge_pass(g.rf, 1, 4, 256, span, g.P, n, g.ctrl, rej, ss, g.Z, g.Z ? &g.ctrl->cert : nullptr,
-                             true, g.log);
+                             true, g.logs[g.cur_log]);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&s->side_flags[r->flag], rej, sizeof(uint32_t), cudaMemcpyDeviceToHost, ss);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
@@ -857,7 +900,7 @@ void try_start(cc_server *s, uint32_t gid) {
     const int cls = class_of(r->r.kind);
     if (g.group == kExclusive) return;
     if (cls == kExclusive) {
-      if (g.active) return;
+      if (g.active || g.snap_busy) return;  // a detached snapshot still reads the graph's memory
       if (r->r.kind == CC_REQ_NEW_GRAPH) {
         if (!start_new_graph(s, r, g)) return;  // no memory yet
         g.fifo.pop_front();
@@ -885,6 +928,7 @@ void try_start(cc_server *s, uint32_t gid) {
     }
     if (g.active && g.group != cls) return;
     bool started;
+    if (r->r.kind == CC_REQ_INSERT && g.snap_busy) s->snapshot_overlaps++;
     if (r->r.kind == CC_REQ_SNAPSHOT)
       started = start_snapshot(s, r, g);
     else if (r->r.kind == CC_REQ_INSERT && r->r.n_edges >= cc::srv::kSideInsertMin && g.n)
@@ -1014,12 +1058,26 @@ bool scheduler_step(cc_server *s, std::vector<Req *> &incoming) {
     Req *r = s->side_running[i];
     const cudaError_t q = cudaEventQuery(r->ev);
     if (q == cudaErrorNotReady) {
+      // a snapshot whose copy of P has been taken releases the graph's later
+      // requests (it no longer reads the live P)
+      if (r->ev_point && !r->detached && cudaEventQuery(r->ev_point) == cudaSuccess) {
+        r->detached = true;
+        finish_graph_request(s->graphs[r->graph]);
+        touched.push_back(r->graph);
+        progress = true;
+      }
       ++i;
       continue;
     }
     cudaEventDestroy(r->ev);
     r->ev = nullptr;
     GraphState &g = s->graphs[r->graph];
+    const bool was_detached = r->detached;
+    if (r->ev_point) {
+      cudaEventDestroy(r->ev_point);
+      r->ev_point = nullptr;
+      g.snap_busy = false;
+    }
     cc_status st = q == cudaSuccess ? CC_OK : CC_ERR_CUDA;
     if (r->r.kind == CC_REQ_NEW_GRAPH && st == CC_OK) {
       g.m = s->side_words[2 * r->graph];
@@ -1031,7 +1089,7 @@ bool scheduler_step(cc_server *s, std::vector<Req *> &incoming) {
       r->flag = -1;
     }
     complete(s, r, st);
-    finish_graph_request(g);
+    if (!was_detached) finish_graph_request(g);
     touched.push_back(r->graph);
     s->side_running[i] = s->side_running.back();
     s->side_running.pop_back();
@@ -1380,6 +1438,7 @@ cc_status cc_server_get_stats(cc_server *s, cc_server_stats *st) {
   st->tiles_run = s->tiles_run;
   st->side_drains = s->side_drains;
   st->executor_timeouts = s->executor_timeouts;
+  st->snapshot_overlaps = s->snapshot_overlaps;
   return CC_OK;
 }
 
@@ -1391,8 +1450,10 @@ void cc_server_destroy(cc_server *s) {
   }
   s->sub_cv.notify_all();
   if (s->thread.joinable()) s->thread.join();
-  for (auto &r : s->reqs)
+  for (auto &r : s->reqs) {
     if (r->ev) cudaEventDestroy(r->ev);
+    if (r->ev_point) cudaEventDestroy(r->ev_point);
+  }
   release_resources(s);
   delete s;
 }

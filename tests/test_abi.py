@@ -64,7 +64,7 @@ def test_batch_and_server_layouts_match_headers(tmp_path, lib):
                  'offsetof(cc_batch_config, tile_vertices), sizeof(cc_request), offsetof(cc_request, labels_dev),'
                  'sizeof(cc_server_config), offsetof(cc_server_config, label_space), sizeof(cc_server_stats),'
                  'offsetof(cc_batch_config, barrier_wait_us), offsetof(cc_server_config, publish_wait_us),'
-                 'offsetof(cc_server_config, fault_hold_publish_us), offsetof(cc_server_stats, executor_timeouts));'
+                 'offsetof(cc_server_config, fault_hold_publish_us), offsetof(cc_server_stats, snapshot_overlaps));'
                  'return 0;}\n')
     exe = tmp_path / "layout2"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(c)])
@@ -74,7 +74,7 @@ def test_batch_and_server_layouts_match_headers(tmp_path, lib):
                    ctypes.sizeof(lib.cc_server_config), lib.cc_server_config.label_space.offset,
                    ctypes.sizeof(lib.cc_server_stats), lib.cc_batch_config.barrier_wait_us.offset,
                    lib.cc_server_config.publish_wait_us.offset, lib.cc_server_config.fault_hold_publish_us.offset,
-                   lib.cc_server_stats.executor_timeouts.offset]
+                   lib.cc_server_stats.snapshot_overlaps.offset]
 
 
 def test_defaults_and_status_strings(lib):

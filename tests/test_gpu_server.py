@@ -306,3 +306,39 @@ def test_incremental_snapshots(mode, label_space, admit_labels):
                 torch.cuda.synchronize()
                 assert s.wait(s.snapshot(g, L)) == cc.CC_OK
                 np.testing.assert_array_equal(L.cpu().numpy().view(np.uint32), want())
+
+
+@pytest.mark.parametrize("mode", [cc.CC_ROOT_MAXDEG, cc.CC_ROOT_IDENTITY])
+def test_inserts_overlap_a_snapshot(mode):
+    """Inserts submitted right after a snapshot of the same graph start once
+    the snapshot has copied the parent array, while its labels are still
+    being computed (Section III: received pairs keep being applied while
+    results are produced). Each snapshot and query must still see exactly the
+    inserts submitted before it, equal to the oracle, and the mix must give
+    the same results as the same requests run one at a time."""
+    n = 1 << 25  # the parent array (128 MB) is large enough for a slow first flatten
+    base = graphgen.rmat(25, 1 << 26, 17, scramble=True)
+    rng = np.random.default_rng(5)
+    script = [(0, "new", base)]
+    for i in range(4):
+        script.append((0, "snapshot", None))
+        for size in (300000, 20000, 900):  # a side-stream insert, executor tiles, one tile
+            script.append((0, "insert", graphgen.pairs(n, size + int(rng.integers(0, 100)), 31, tag=10 * i + size)))
+        script.append((0, "query", graphgen.pairs(n, 5000, 32, tag=i)))
+    script.append((0, "snapshot", None))
+    graphs = {0: n}
+    want = expected(script, graphs)
+    with cc.Server(4 * GB, mode=mode) as s:
+        mixed, _ = run_script(s, script, graphs, one_at_a_time=False)
+        st = s.stats()
+        assert st["failed"] == 0
+        assert st["snapshot_overlaps"] >= 1
+    with cc.Server(4 * GB, mode=mode) as s:
+        alone, _ = run_script(s, script, graphs, one_at_a_time=True)
+    for i, (_, kind, _) in enumerate(script):
+        if kind == "query":
+            np.testing.assert_array_equal(mixed[i], want[i])
+            np.testing.assert_array_equal(alone[i], want[i])
+        elif kind == "snapshot":
+            np.testing.assert_array_equal(mixed[i].view(np.uint32), want[i])
+            np.testing.assert_array_equal(alone[i].view(np.uint32), want[i])
