@@ -33,7 +33,7 @@ typedef struct cc_batch_config {
   int32_t block_size;       /* 256 or 512 */
   int32_t edges_per_thread; /* 1, 2 or 4 per round */
   int32_t filter;           /* 1: warp filter + compaction, 0: per-lane */
-  uint32_t tile_edges;      /* edges per tile, a multiple of 256, >= 256 */
+  uint32_t tile_edges;      /* edges per hooking tile (one warp's unit of work), a multiple of 256, >= 256 */
   uint32_t tile_vertices;   /* vertices per tile of the label phase, >= 256 */
   uint32_t barrier_wait_us; /* bounded wait of each grid barrier, at most 60 s; 0 = 4 s. A
                                wait that expires aborts the run (every block leaves at its

@@ -210,30 +210,38 @@ __global__ void __launch_bounds__(512) k_batched(BatchArgs a) {
   for (uint64_t x = tid; x < V; x += T) a.P[x] = (uint32_t)x;
   if (!grid_barrier(c, gen, a.barrier_ns)) return;
 
-  // 2. hooking over edge tiles
+  // 2. hooking over edge tiles, one warp per tile: lane 0 finds the tile's
+  // graph and broadcasts it, so no block barrier is taken per tile (a block
+  // would wait for its slowest warp's searches). Tile t goes to warp
+  // t % warps of block t / warps % gridDim.x: consecutive tiles, often of one
+  // graph, stay on one SM and share its L1.
   uint32_t *const P = a.P;  // names are global ids: the slot of name x is P[x]
   WarpRing ring;
   if (FILTER) ring.init(ring_smem);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t wpb = blockDim.x >> 5;
+  const uint64_t wid = (uint64_t)blockIdx.x * wpb + (threadIdx.x >> 5);  // block-major
+  const uint64_t n_warps = wpb * gridDim.x;
   const uint64_t n_etiles = a.etile_off[a.n_graphs];
-  for (uint64_t t = blockIdx.x; t < n_etiles; t += gridDim.x) {
-    if (threadIdx.x == 0) {
+  for (uint64_t t = wid; t < n_etiles; t += n_warps) {
+    uint64_t nv = 0, e0 = 0, e1 = 0, base64 = 0;
+    if (lane == 0) {
       const uint32_t g = owner(a.etile_off, a.n_graphs, t);
-      const uint64_t e0 = a.edge_off[g] + (t - a.etile_off[g]) * a.tile_edges;
-      const uint64_t e1 = a.edge_off[g + 1];
-      s_tile[0] = a.vtx_off[g + 1] - a.vtx_off[g];
-      s_tile[1] = e0;
-      s_tile[2] = e0 + a.tile_edges < e1 ? e0 + a.tile_edges : e1;
-      s_tile[3] = a.vtx_off[g];
+      e0 = a.edge_off[g] + (t - a.etile_off[g]) * a.tile_edges;
+      const uint64_t ge = a.edge_off[g + 1];
+      e1 = e0 + a.tile_edges < ge ? e0 + a.tile_edges : ge;
+      nv = a.vtx_off[g + 1] - a.vtx_off[g];
+      base64 = a.vtx_off[g];
     }
-    __syncthreads();
-    const uint64_t nv = s_tile[0], e0 = s_tile[1], e1 = s_tile[2];
-    const uint32_t base = (uint32_t)s_tile[3];
-    __syncthreads();
-    for (uint64_t r0 = e0; r0 < e1; r0 += (uint64_t)blockDim.x * EPT) {
+    nv = __shfl_sync(0xFFFFFFFFu, nv, 0);
+    e0 = __shfl_sync(0xFFFFFFFFu, e0, 0);
+    e1 = __shfl_sync(0xFFFFFFFFu, e1, 0);
+    const uint32_t base = (uint32_t)__shfl_sync(0xFFFFFFFFu, base64, 0);
+    for (uint64_t r0 = e0; r0 < e1; r0 += 32u * EPT) {
       uint32_t u[EPT], v[EPT], pu[EPT], pv[EPT];
 #pragma unroll
       for (int j = 0; j < EPT; ++j) {
-        const uint64_t i = r0 + (uint64_t)j * blockDim.x + threadIdx.x;
+        const uint64_t i = r0 + (uint64_t)j * 32u + lane;
         uint2 ed = make_uint2(0u, 0u);
         bool ok = false;
         if (i < e1) {
@@ -523,7 +531,7 @@ cc_status cc_batch_tune(cc_batch *b, uint32_t n_graphs, const uint64_t *vtx_off_
   const int blocks[] = {256, 512};
   const int epts[] = {1, 2, 4};
   const int filters[] = {1, 0};
-  const uint32_t tiles[] = {4096, 16384, 65536};
+  const uint32_t tiles[] = {4096, 16384, 65536};  // edges per warp tile
   cc_batch_config top = b->cfg;
   float top_ms = 1e30f;
   b->n_tuned = 0;

@@ -246,19 +246,9 @@ constexpr uint32_t kNeverDirect = 33;
 // only after a walk or a parent value proved the fact, which holds for good
 // because name 0 is never hooked; a stale 0 bit only costs the parent load
 // it would have saved.
-// Build option CC_ZLOAD selects the L1 policy of the bitmap loads: 0
-// (default) the normal policy, 1 evict-last (bitmap lines of hot vertices
-// stay in L1 against the parent loads' misses).
-#ifndef CC_ZLOAD
-#define CC_ZLOAD 0
-#endif
 __device__ __forceinline__ bool zbit(const uint32_t *Z, uint32_t c) {
   uint32_t w;
-#if CC_ZLOAD == 1
-  asm volatile("ld.global.L1::evict_last.u32 %0, [%1];" : "=r"(w) : "l"(Z + (c >> 5)) : "memory");
-#else
   asm volatile("ld.global.u32 %0, [%1];" : "=r"(w) : "l"(Z + (c >> 5)) : "memory");
-#endif
   return (w >> (c & 31u)) & 1u;
 }
 

@@ -99,12 +99,15 @@ cudaError_t launch_init(bool rf, uint32_t *P, uint32_t n, Ctrl *ctrl, int m_src,
 constexpr uint32_t kCertCand = 4096;     // more candidates than this: no proof is tried
 constexpr uint32_t kCertBuckets = 8192;  // hash buckets of the degree bound
 constexpr uint32_t kCertTop = 4;         // candidates whose degree is counted exactly
-// Build option CC_CERT_SAMPLE: the sampled pass keeps 1 group of 1024 edges
-// in this many (default 128).
-#ifndef CC_CERT_SAMPLE
-#define CC_CERT_SAMPLE 128
-#endif
-constexpr uint32_t kCertSample = CC_CERT_SAMPLE;
+// The sampled pass keeps 1 group of 1024 edges in cert_sample_stride(E):
+// kCertSample, or more from 2^30 edges up, so that it samples about 2^23
+// edges at most (its random atomics into the n counters cost more than the
+// candidates they find need: R-MAT scale 28 root select 7.6 -> 6.1 ms).
+constexpr uint32_t kCertSample = 128;
+inline uint32_t cert_sample_stride(uint64_t n_edges) {
+  const uint64_t s = n_edges >> 23;
+  return s > kCertSample ? (uint32_t)(s < 4096 ? s : 4096) : kCertSample;
+}
 struct CertScratch {
   unsigned long long owner[kCertBuckets];   // per bucket, its best sampled (count << 32) | ~vertex; 0 = none
   unsigned long long top[kCertTop];         // the best owners, same packing; 0 = empty slot

@@ -162,6 +162,11 @@ __global__ void __launch_bounds__(512, Q >= 4 ? (kZ ? 1 : 2) : (kZ ? 2 : (kDirec
                          uint32_t *P, uint32_t n, Ctrl *ctrl, const uint32_t *skip, uint32_t *Z,
                          const uint32_t *sel, uint32_t *log, unsigned long long *work, uint32_t grab) {
   static_assert(kDirect || !kZ, "the zero-tree form resolves in place");
+  // The queue form (a certified hub, P within L2) reads P through L2 only:
+  // its random parent loads almost never hit L1, and skipping L1 allocation
+  // measured faster there (R-MAT scale 24: 2.02 -> 1.94 ms); the other forms
+  // keep L1 (the grid's searches hit it: 1.27 ms without it against 0.94).
+  constexpr bool kCG = !kZ && !kDirect;
   extern __shared__ uint32_t ring_smem[];
   if (skip && ld_volatile_u32(skip)) return;
   if (sel && ((ld_volatile_u32(sel) != 0u) != (kZ || !kDirect))) return;
@@ -215,10 +220,10 @@ __global__ void __launch_bounds__(512, Q >= 4 ? (kZ ? 1 : 2) : (kZ ? 2 : (kDirec
     } else {
 #pragma unroll
       for (int j = 0; j < Q; ++j) {
-        p[4 * j + 0] = ldP(P + e[j].x);
-        p[4 * j + 1] = ldP(P + e[j].y);
-        p[4 * j + 2] = ldP(P + e[j].z);
-        p[4 * j + 3] = ldP(P + e[j].w);
+        p[4 * j + 0] = ldP_t<kCG>(P + e[j].x);
+        p[4 * j + 1] = ldP_t<kCG>(P + e[j].y);
+        p[4 * j + 2] = ldP_t<kCG>(P + e[j].z);
+        p[4 * j + 3] = ldP_t<kCG>(P + e[j].w);
       }
     }
 #pragma unroll
@@ -226,7 +231,7 @@ __global__ void __launch_bounds__(512, Q >= 4 ? (kZ ? 1 : 2) : (kZ ? 2 : (kDirec
       const uint32_t a = (k & 1) ? e[k >> 1].z : e[k >> 1].x;
       const uint32_t b = (k & 1) ? e[k >> 1].w : e[k >> 1].y;
       const uint32_t pa = p[2 * k], pb = p[2 * k + 1];
-      ring.push(S, pa != pb, fn.f(a), pa, fn.f(b), pb);
+      ring.push<kCG>(S, pa != pb, fn.f(a), pa, fn.f(b), pb);
     }
   };
   if (work) {
@@ -245,7 +250,7 @@ __global__ void __launch_bounds__(512, Q >= 4 ? (kZ ? 1 : 2) : (kZ ? 2 : (kDirec
     const uint64_t warp_t0 = t - (uint64_t)ring.lane;
     for (uint64_t wbase = warp_t0; wbase < n_quads; wbase += T * Q) step(wbase + ring.lane, T);
   }
-  ring.drain(S);
+  ring.drain<kCG>(S);
 }
 
 __global__ void __launch_bounds__(256) k_validate(const uint4 *__restrict__ e4, uint64_t n_quads,

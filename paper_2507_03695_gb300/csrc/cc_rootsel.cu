@@ -6,7 +6,8 @@
 // A global histogram needs one random atomic per endpoint, which on R-MAT
 // graphs is slower than the edge pass itself. The default exact selection is
 // therefore certified instead:
-//   1. a histogram over 1 group of 1024 edges in 128 (global atomics) gives
+//   1. a histogram over 1 group of 1024 edges in 128 (more above 2^30 edges:
+//      cert_sample_stride; global atomics) gives
 //      candidate hubs: every vertex with at least 1/32 of the largest sampled
 //      count (at most kCertCand of them); the best per hash bucket of vertex
 //      ids competes, and the kCertTop best of those are kept;
@@ -523,7 +524,8 @@ cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges
   uint32_t *c32 = static_cast<uint32_t *>(cnt);
   // 1. sampled histogram and its largest count; the push list also needs the
   // vertex holding it (the argmax pass)
-  if ((err = launch_degree_sampled_u32(reinterpret_cast<const uint2 *>(edges), n_edges, 0, kCertSample, c32, n, s,
+  const uint32_t stride = cert_sample_stride(n_edges);
+  if ((err = launch_degree_sampled_u32(reinterpret_cast<const uint2 *>(edges), n_edges, 0, stride, c32, n, s,
                                        push_buf ? nullptr : ctrl)) != cudaSuccess)
     return err;
   if (push_buf && (err = launch_argmax_u32(c32, n, ctrl, s)) != cudaSuccess) return err;
@@ -561,7 +563,7 @@ cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges
     note_launch();
   } else {
     // the sampled counts are kept: only the edges outside the sample are added
-    k_degree<uint32_t><<<gd, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, c32, n, skip, kCertSample);
+    k_degree<uint32_t><<<gd, 256, 0, s>>>(e.quads, e.n_quads, e.head, e.tail, c32, n, skip, stride);
     note_launch();
     k_argmax_u32<<<gz, 256, 0, s>>>(c32, n, ctrl, skip);
     note_launch();
