@@ -67,6 +67,9 @@ def parse_args(argv=None):
     p.add_argument("--extra-workload", choices=sorted(WORKLOADS) + [""], default="rmat24+grid8192",
                    help="a second workload timed after the first and reported under extra_workload "
                         "(the CSR leg runs on it); empty: none")
+    p.add_argument("--sharded", action="store_true",
+                   help="under torchrun: every rank takes an edge-balanced slice of each graph and one Reducer "
+                        "joins the ranks' forests (Section III); strong scaling. Default: independent replicas")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-batched", action="store_true")
@@ -376,6 +379,8 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
+    if args.sharded:
+        return run_sharded_bench(args, cc, graphgen, torch, dist, dev, rank, world, barrier, max_over_ranks)
     names = WORKLOADS[args.workload]
     ws = [graphgen.WORKLOADS[nm] for nm in names]
     graphs = []
@@ -553,6 +558,72 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+def run_sharded_bench(args, cc, graphgen, torch, dist, dev, rank, world, barrier, max_over_ranks):
+    """Edge sharding with one Reducer step: each rank hooks its edge-balanced
+    slice of every graph on a private parent array and sends its forest; rank
+    0 joins the forests in one more pass and writes the labels. One step = all
+    graphs of the workload; value = all edges / the slowest rank's time."""
+    from paper_2507_03695_gb300 import sharded
+    if dist is None:  # one rank: a group of one, so the exchange runs as it would on N
+        import torch.distributed as tdist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29511")
+        tdist.init_process_group("nccl", rank=0, world_size=1, device_id=dev)
+        dist = tdist
+    names = WORKLOADS[args.workload]
+    work = []
+    for nm in names:
+        w = graphgen.WORKLOADS[nm]
+        if w.kind == "rmat":
+            a, b = sharded.edge_range(w.n_edges, rank, world)
+            e_local = graphgen.rmat_dev(w.scale, w.n_edges, w.seed, w.scramble, e_begin=a, e_end=b)
+            E = w.n_edges
+        else:
+            full = w.device_edges()
+            E = int(full.shape[0])
+            a, b = sharded.edge_range(E, rank, world)
+            e_local = full[a:b].clone()
+            del full
+        h = cc.Graph(w.n_vertices, **BENCH_OPTIONS)
+        red = cc.Graph(w.n_vertices, **BENCH_OPTIONS) if rank == 0 else None
+        L = torch.empty(w.n_vertices, dtype=torch.int32, device=dev) if rank == 0 else None
+        work.append((w, e_local, E, h, red, L))
+    torch.cuda.synchronize()
+    E_total = sum(E for _, _, E, _, _, _ in work)
+
+    def step():
+        for w, e_local, _, h, red, L in work:
+            sharded.run_sharded(w.n_vertices, e_local, dist, L, graph=h, reducer_graph=red)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    elapsed = max_over_ranks(time.perf_counter() - t0) if world > 1 else time.perf_counter() - t0
+    if rank == 0:
+        line = {
+            "metric": "GTEPS", "value": E_total * args.steps / elapsed / 1e9, "unit": "GTEPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic, generated in HBM (each rank its own slice)",
+            "config": {"workload": args.workload, "graphs": names, "n_edges": [E for _, _, E, _, _, _ in work],
+                       "parallelism": f"edge shards x{world}, one reducer (rank 0)"},
+            "timing": "host clock around the steps (each step ends with the reducer's labels)",
+        }
+        print(json.dumps(line), flush=True)
+    for _, _, _, h, red, _ in work:
+        h.close()
+        if red is not None:
+            red.close()
+    dist.destroy_process_group()
     return 0
 
 

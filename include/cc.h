@@ -245,6 +245,22 @@ CC_API cc_status cc_labels(cc_graph *g, uint32_t *L_out_dev, cc_stream_t stream)
 CC_API cc_status cc_connected(cc_graph *g, const uint32_t *pairs_dev, uint64_t n_pairs, uint8_t *out_dev,
                        cc_stream_t stream);
 
+/* The forest of the live P as edges, for a Reducer (Section III: each
+ * machine, after processing its share of the edges, sends the pairs
+ * (v, P_v) with P_v != f(v) to the Reducer, which processes them like graph
+ * edges and finishes with pointer jumping; Algorithm 2). For every non-root
+ * vertex v the pair (v, parent of v) is written to pairs_dev as COO
+ * (uint32[2 * count], 8-byte aligned, in no particular order), so the pairs
+ * have exactly the components of the edges applied so far and can be given
+ * to cc_run or cc_stream_insert of another handle. After cc_labels (which
+ * compresses P) every pair names the root directly. At most `capacity` pairs
+ * are written; *count receives the number of non-root vertices
+ * (n_vertices - cc_num_components), and CC_ERR_TOO_LARGE is returned when it
+ * exceeds capacity (call again with a larger buffer). Synchronising; also
+ * reports earlier device errors. */
+CC_API cc_status cc_forest_pairs(cc_graph *g, uint32_t *pairs_dev, uint64_t capacity, uint64_t *count,
+                                 cc_stream_t stream);
+
 /* One query, synchronising: *out = 1 if u and v are connected, else 0. */
 CC_API cc_status cc_connected1(cc_graph *g, uint64_t u, uint64_t v, int *out);
 

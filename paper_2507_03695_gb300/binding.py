@@ -110,6 +110,7 @@ def lib():
             "cc_labels": (_i32, [_ptr, _ptr, _ptr]),
             "cc_connected": (_i32, [_ptr, _ptr, _u64, _ptr, _ptr]),
             "cc_connected1": (_i32, [_ptr, _u64, _u64, P(ctypes.c_int)]),
+            "cc_forest_pairs": (_i32, [_ptr, _ptr, _u64, P(_u64), _ptr]),
             "cc_num_components": (_i32, [_ptr, P(_u64)]),
             "cc_root_vertex": (_i32, [_ptr, P(_u64)]),
             "cc_sync": (_i32, [_ptr]),
@@ -265,6 +266,21 @@ def cc_connected1(g: int, u: int, v: int) -> bool:
     return bool(r.value)
 
 
+def cc_forest_pairs(g: int, pairs_out, capacity: int | None = None, stream=None) -> int:
+    """Writes the forest of P as (v, parent) pairs into pairs_out (an (m, 2)
+    int32 device tensor or an address with `capacity` pairs); returns the
+    number of non-root vertices. Raises CCError(CC_ERR_TOO_LARGE) when the
+    buffer is too small (the exception's `count` holds the number needed)."""
+    cap = _count_pairs(pairs_out, capacity) if pairs_out is not None else 0
+    cnt = _u64(0)
+    st = lib().cc_forest_pairs(g, _addr(pairs_out), cap, ctypes.byref(cnt), _stream(stream))
+    if st != CC_OK:
+        err = CCError(st, "cc_forest_pairs")
+        err.count = int(cnt.value)
+        raise err
+    return int(cnt.value)
+
+
 def cc_num_components(g: int) -> int:
     r = _u64(0)
     _check(lib().cc_num_components(g, ctypes.byref(r)), "cc_num_components")
@@ -364,6 +380,17 @@ class Graph:
         cc_connected(self.h, pairs, out, None, stream)
         return out
 
+    def forest_pairs(self, stream=None):
+        """The forest of P as an (count, 2) int32 device tensor of (v, parent)
+        pairs: a view of one device buffer of n pairs kept with the handle and
+        rewritten by the next call (see cc_forest_pairs)."""
+        import torch
+        buf = getattr(self, "_pairs_buf", None)
+        if buf is None:
+            buf = self._pairs_buf = torch.empty((max(self.n, 1), 2), dtype=torch.int32, device="cuda")
+        count = cc_forest_pairs(self.h, buf, self.n, stream)
+        return buf[:count]
+
     def num_components(self) -> int:
         return cc_num_components(self.h)
 
@@ -377,6 +404,7 @@ class Graph:
         if self.h:
             cc_destroy(self.h)
             self.h = 0
+        self._pairs_buf = None
 
     def __enter__(self):
         return self

@@ -649,6 +649,22 @@ cc_status cc_connected(cc_graph *g, const uint32_t *pairs_dev, uint64_t n_pairs,
   return CC_OK;
 }
 
+cc_status cc_forest_pairs(cc_graph *g, uint32_t *pairs_dev, uint64_t capacity, uint64_t *count,
+                          cc_stream_t stream) {
+  if (!g || !count) return CC_ERR_INVALID_ARGUMENT;
+  if (capacity && (!pairs_dev || !aligned(pairs_dev, 8))) return CC_ERR_INVALID_ARGUMENT;
+  DeviceGuard dg(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  g->last = s;
+  *count = 0;
+  if (g->n == 0) return CC_OK;
+  CC_TRY(cc::launch_forest_pairs(g->rf, g->P, (uint32_t)g->n, pairs_dev, capacity, g->ctrl, s));
+  const cc_status st = fetch_ctrl(g, s);  // waits; also reports earlier device errors
+  *count = g->host_ctrl->pairs;
+  if (st != CC_OK) return st;
+  return *count > capacity ? CC_ERR_TOO_LARGE : CC_OK;
+}
+
 cc_status cc_connected1(cc_graph *g, uint64_t u, uint64_t v, int *out) {
   if (!g || !out) return CC_ERR_INVALID_ARGUMENT;
   if (u >= g->n || v >= g->n) return CC_ERR_OUT_OF_RANGE;

@@ -39,6 +39,7 @@ struct alignas(128) Ctrl {
   uint32_t skip[3];           // chunked root select: skip words (kSkip*), set on the device
   unsigned long long stats[4];  // optional edge-pass counters
   unsigned long long work;      // edge pass, dynamic schedule: steps claimed so far
+  unsigned long long pairs;     // cc_forest_pairs: non-root vertices found
 };
 static_assert(offsetof(Ctrl, q_u) % 8 == 0, "the query pair is loaded with an 8-byte access");
 static_assert(offsetof(Ctrl, maxkey) % 8 == 0 && offsetof(Ctrl, ncomp) % 8 == 0, "64-bit atomics");
@@ -203,5 +204,10 @@ cudaError_t launch_gmin_probe(uint32_t *P, uint32_t n, Ctrl *ctrl, cudaStream_t 
 cudaError_t launch_count_roots(bool rf, const uint32_t *P, uint32_t n, Ctrl *ctrl, cudaStream_t s);
 cudaError_t launch_connected(bool rf, uint32_t *P, uint32_t n, const uint2 *pairs, uint64_t n_pairs,
                              uint8_t *out, Ctrl *ctrl, cudaStream_t s);
+// The forest of P as edges: for every non-root vertex v, the pair (v, parent
+// of v) goes to out[2i], out[2i + 1] for i < cap; ctrl->pairs counts them all
+// (reset on s before the launch).
+cudaError_t launch_forest_pairs(bool rf, const uint32_t *P, uint32_t n, uint32_t *out, uint64_t cap, Ctrl *ctrl,
+                                cudaStream_t s);
 
 }  // namespace cc

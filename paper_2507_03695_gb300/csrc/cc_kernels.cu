@@ -476,6 +476,35 @@ __global__ void __launch_bounds__(256) k_connected(uint32_t *P, uint32_t n,
   }
 }
 
+// The forest as edges (the pairs (v, P_v) that each machine sends to the
+// Reducer, Section III): a non-root v (P[v] != f(v)) gives (v, f^-1(P[v])),
+// the vertex its parent name names. One atomic per warp reserves the slots.
+template <class F>
+__global__ void __launch_bounds__(256) k_forest_pairs(const uint32_t *__restrict__ P, uint32_t n, uint2 *out,
+                                                      uint64_t cap, Ctrl *ctrl) {
+  const F fn = F::load(ctrl);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  for (uint64_t base = t0 - lane; base < n; base += T) {  // warp-uniform trip count
+    const uint64_t v = base + lane;
+    bool mine = false;
+    uint32_t parent = 0;
+    if (v < n) {
+      const uint32_t pv = P[v];
+      mine = pv != fn.f((uint32_t)v);
+      parent = fn.finv(pv);
+    }
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, mine);
+    if (!bal) continue;
+    unsigned long long slot0 = 0;
+    if (lane == 0) slot0 = atomicAdd(&ctrl->pairs, (unsigned long long)__popc(bal));
+    slot0 = __shfl_sync(0xFFFFFFFFu, slot0, 0);
+    const uint64_t slot = slot0 + (uint64_t)__popc(bal & ((1u << lane) - 1u));
+    if (mine && slot < cap) out[slot] = make_uint2((uint32_t)v, parent);
+  }
+}
+
 }  // namespace
 
 // ======================================================================= host
@@ -710,6 +739,23 @@ cudaError_t launch_count_roots(bool rf, const uint32_t *P, uint32_t n, Ctrl *ctr
     const unsigned g = clamp_grid(want, persistent_cap((const void *)k_count_roots<RootId>, 256, 0));
     k_count_roots<RootId><<<g, 256, 0, s>>>(P, n, ctrl); note_launch();
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forest_pairs(bool rf, const uint32_t *P, uint32_t n, uint32_t *out, uint64_t cap, Ctrl *ctrl,
+                                cudaStream_t s) {
+  cudaError_t err = cudaMemsetAsync(&ctrl->pairs, 0, sizeof(unsigned long long), s);
+  if (err != cudaSuccess || n == 0) return err;
+  const uint64_t want = ((uint64_t)n + 255) / 256;
+  uint2 *o = reinterpret_cast<uint2 *>(out);
+  if (rf) {
+    const unsigned g = clamp_grid(want, persistent_cap((const void *)k_forest_pairs<RootR>, 256, 0));
+    k_forest_pairs<RootR><<<g, 256, 0, s>>>(P, n, o, cap, ctrl);
+  } else {
+    const unsigned g = clamp_grid(want, persistent_cap((const void *)k_forest_pairs<RootId>, 256, 0));
+    k_forest_pairs<RootId><<<g, 256, 0, s>>>(P, n, o, cap, ctrl);
+  }
+  note_launch();
   return cudaGetLastError();
 }
 
