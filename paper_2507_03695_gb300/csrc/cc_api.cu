@@ -407,7 +407,8 @@ cc_status cc_run(cc_graph *g, const uint32_t *edges_dev, uint64_t n_edges, uint3
   const uint32_t *zsel = (Z && !g->z_forced) ? &g->ctrl->cert : nullptr;
   record(g, 2, s);
   CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), span, g->P, n, g->ctrl,
-                              nullptr, s, Z, zsel, false, nullptr, exact ? &g->ctrl->cert : nullptr, true));
+                              nullptr, s, Z, zsel, false, nullptr, exact ? &g->ctrl->cert : nullptr, true,
+                              exact ? g->cert->hot : nullptr));
   record(g, 3, s);
   CC_TRY(cc::launch_flatten(g->rf, g->opt.label_space, g->P, n, L_out_dev, g->ctrl, s));
   record(g, 4, s);
@@ -486,7 +487,7 @@ static cc_status run_host_impl(cc_graph *g, const void *edges_host, uint64_t n_e
     // every chunk is hooked as it lands, under m' when m is still unknown
     if (chunked && off == 0) CC_TRY(cc::launch_init(true, g->P, n, g->ctrl, cc::kMFromPackedMax, 0u, s));
     CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), chunk, g->P, n, g->ctrl, nullptr,
-                                s, Zc, zc_sel, false, nullptr, hub_c, true));
+                                s, Zc, zc_sel, false, nullptr, hub_c, true, chunked ? g->cert->hot : nullptr));
   }
   const cc::EdgeSpan all = cc::split_edges(g->staging, n_edges);
   if (chunked) {
@@ -499,7 +500,7 @@ static cc_status run_host_impl(cc_graph *g, const void *edges_host, uint64_t n_e
     // forgets bits: an empty bitmap is always valid)
     if (Zc) CC_TRY(cudaMemsetAsync(Zc, 0, g->z_bytes, s));
     CC_TRY(cc::launch_edge_pass(true, eff_filter(g), eff_ept(g), eff_block(g), all, g->P, n, g->ctrl, held, s,
-                                g->z, Zf ? nullptr : &g->ctrl->cert, false, nullptr, nullptr, true));
+                                g->z, Zf ? nullptr : &g->ctrl->cert, false, nullptr, nullptr, true, g->cert->hot));
   } else if (select) {
     if (id_bytes != 3) {  // (packed chunks were unpacked on s already)
       CC_TRY(cudaEventRecord(g->copy_ev, g->copy_stream));
@@ -617,7 +618,8 @@ cc_status cc_stream_insert(cc_graph *g, const uint32_t *edges_dev, uint64_t n_ed
   // the last run's certificate (when its exact selection ran) picks the form
   const uint32_t *hub = g->z_auto_ok ? &g->ctrl->cert : nullptr;
   CC_TRY(cc::launch_edge_pass(g->rf, eff_filter(g), eff_ept(g), eff_block(g), span, g->P,
-                              (uint32_t)g->n, g->ctrl, &g->ctrl->reject, s, Z, zsel, false, nullptr, hub, true));
+                              (uint32_t)g->n, g->ctrl, &g->ctrl->reject, s, Z, zsel, false, nullptr, hub, true,
+                              g->z_auto_ok ? g->cert->hot : nullptr));
   g->ncomp_fresh = false;
   return CC_OK;
 }

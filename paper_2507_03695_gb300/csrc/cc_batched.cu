@@ -57,6 +57,19 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   return t;
 }
 
+// Built with -DCC_BATCH_CLOCK, block 0 records the global timer at the
+// kernel's start, after each grid barrier and at its end (diagnostics of the
+// phase times only, off in normal builds).
+#ifdef CC_BATCH_CLOCK
+__device__ unsigned long long g_batch_clock[8];
+#define CC_BATCH_TICK(i)                                                     \
+  do {                                                                       \
+    if (blockIdx.x == 0 && threadIdx.x == 0) g_batch_clock[(i)] = globaltimer(); \
+  } while (0)
+#else
+#define CC_BATCH_TICK(i) ((void)0)
+#endif
+
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
   unsigned int v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -97,6 +110,7 @@ __device__ bool grid_barrier(BatchCtrl *c, unsigned int &gen, unsigned long long
   }
   __syncthreads();
   ++gen;
+  CC_BATCH_TICK(gen);
   return s_ok != 0;
 }
 
@@ -200,6 +214,7 @@ __global__ void __launch_bounds__(512) k_batched(BatchArgs a) {
   __shared__ uint64_t s_tile[4];  // graph, first edge / vertex, end, name base
   BatchCtrl *c = a.ctrl;
   unsigned int gen = 0;
+  CC_BATCH_TICK(0);
   if (blockIdx.x == 0) scan_tiles(a);
   if (!grid_barrier(c, gen, a.barrier_ns)) return;
 
@@ -304,10 +319,18 @@ __global__ void __launch_bounds__(512) k_batched(BatchArgs a) {
     __syncthreads();
     for (uint64_t x = x0 + threadIdx.x; x < x1; x += blockDim.x) P[x] = ldP_strong(P + x) - base;
   }
+  CC_BATCH_TICK(5);
 }
 
 }  // namespace
 }  // namespace cc
+
+#ifdef CC_BATCH_CLOCK
+// Diagnostics builds only: the timer readings of the last batched run.
+extern "C" __attribute__((visibility("default"))) int cc_batch_clock_read(unsigned long long out[8]) {
+  return (int)cudaMemcpyFromSymbol(out, cc::g_batch_clock, 8 * sizeof(unsigned long long));
+}
+#endif
 
 using cc::BatchArgs;
 using cc::BatchCtrl;

@@ -254,6 +254,9 @@ __device__ __forceinline__ bool zbit(const uint32_t *Z, uint32_t c) {
 
 __device__ __forceinline__ void zset(uint32_t *Z, uint32_t c) { atomicOr(Z + (c >> 5), 1u << (c & 31u)); }
 
+// Slot of vertex x in the hot-vertex table (kHot entries).
+__device__ __forceinline__ uint32_t hot_slot(uint32_t x) { return (x * 2654435761u) >> (32 - kHotBits); }
+
 // A changed-root log: log[0] counts the entries that follow it, the names of
 // the roots hooked since the log was last cleared. Its capacity (one entry
 // per vertex) cannot be exceeded: a root is hooked once.

@@ -100,6 +100,12 @@ cudaError_t launch_init(bool rf, uint32_t *P, uint32_t n, Ctrl *ctrl, int m_src,
 constexpr uint32_t kCertCand = 4096;     // more candidates than this: no proof is tried
 constexpr uint32_t kCertBuckets = 8192;  // hash buckets of the degree bound
 constexpr uint32_t kCertTop = 4;         // candidates whose degree is counted exactly
+// The hot-vertex table of the edge pass: per slot (a multiplicative hash of
+// the vertex id, kHotBits bits) the vertex with the largest sampled count
+// among those with at least 1/64 of the largest, packed (count << 32) |
+// (vertex + 1); filled by the candidate scan of the root selection.
+constexpr uint32_t kHotBits = 12;
+constexpr uint32_t kHot = 1u << kHotBits;
 // The sampled pass keeps 1 group of 1024 edges in cert_sample_stride(E):
 // kCertSample, or more from 2^30 edges up, so that it samples about 2^23
 // edges at most (its random atomics into the n counters cost more than the
@@ -114,6 +120,7 @@ struct CertScratch {
   unsigned long long top[kCertTop];         // the best owners, same packing; 0 = empty slot
   unsigned long long top_cnt[kCertTop];     // their exact degrees
   unsigned long long bucket[kCertBuckets];  // endpoint occurrences of all vertices of the bucket
+  unsigned long long hot[kHot];             // the hot-vertex table (see kHotBits)
   unsigned int sel_done;                    // candidate-selection blocks finished (the last one ranks)
   unsigned int blocks_done;                 // counting blocks finished (the last one decides)
   // Initial Push (Algorithm 4): neighbours of the sampled argmax m', appended
@@ -189,10 +196,13 @@ cudaError_t launch_argmax_u32(const uint32_t *cnt, uint32_t n, Ctrl *ctrl, cudaS
 // persistent grid (for work that shares the GPU with a resident kernel).
 // log: a changed-root log (log[0] = entries, then the hooked root names), or
 // null.
+// hot: the hot-vertex table (CertScratch::hot) of this graph's last root
+// selection, for the instances that serve a certified hub, or null.
 cudaError_t launch_edge_pass(bool rf, int filter, int ept, int block, const EdgeSpan &e, uint32_t *P,
                              uint32_t n, Ctrl *ctrl, const uint32_t *skip, cudaStream_t s,
                              uint32_t *Z = nullptr, const uint32_t *zsel = nullptr, bool one_shot = false,
-                             uint32_t *log = nullptr, const uint32_t *hub = nullptr, bool dyn = false);
+                             uint32_t *log = nullptr, const uint32_t *hub = nullptr, bool dyn = false,
+                             const unsigned long long *hot = nullptr);
 // dyn: warps claim their edges from a counter in ctrl (reset on s before the
 // launch), so at most one dynamic edge pass per Ctrl may be in flight.
 // Sets *reject (ctrl->reject when null) and the range error bit when an id is >= n.

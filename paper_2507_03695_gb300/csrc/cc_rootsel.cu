@@ -194,12 +194,15 @@ __global__ void __launch_bounds__(256) k_select_candidates(const uint32_t *__res
   const uint32_t cmax = (uint32_t)(*(volatile unsigned long long *)&ctrl->maxkey >> 32);
   if (cmax < 64u) return;  // uniform over the grid: no block ranks, top stays empty
   const uint32_t thr = cmax >> 5;
+  const uint32_t hot_thr = cmax >> 6;  // the hot-vertex table takes vertices from 1/64 of the largest count
   const int lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   const uint64_t w0 = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
   for (uint64_t base = w0 * 32; base < n; base += warps * 32) {
     const uint64_t v = base + (uint64_t)lane;
     const uint32_t c = v < n ? cnt[v] : 0u;
+    if (c >= hot_thr && c != 0u)
+      atomicMax(&cs->hot[hot_slot((uint32_t)v)], ((unsigned long long)c << 32) | (uint32_t)(v + 1u));
     const bool q = c >= thr && c != 0u;
     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, q);
     if (!bal) continue;

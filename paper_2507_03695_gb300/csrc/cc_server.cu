@@ -735,7 +735,7 @@ bool start_new_graph(cc_server *s, Req *r, GraphState &g) {
   if (e == cudaSuccess && n) e = cc::launch_init(rf, g.P, n, g.ctrl, m_src, 0u, ss);
   if (e == cudaSuccess && n)
     e = cc::launch_edge_pass(rf, 1, 4, 256, span, g.P, n, g.ctrl, nullptr, ss, g.Z, g.Z ? &g.ctrl->cert : nullptr,
-                             true);
+                             true, nullptr, nullptr, false, rf ? g.cert->hot : nullptr);
   // with labels requested they also go to the graph's own copy (the base of
   // incremental snapshots); otherwise the first snapshot makes that copy
   g.has_last = r->r.labels_dev != nullptr && n;
