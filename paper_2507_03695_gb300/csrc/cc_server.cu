@@ -64,8 +64,10 @@ struct alignas(16) WorkItem {
   uint32_t rf, m, n, n_gate;          // n_gate: validate tiles an apply tile waits for
   uint64_t P, src, begin, end, out;
   uint64_t log;  // the graph's changed-root log (inserts append the roots they hook)
+  uint64_t Z;    // the graph's zero-tree bitmap, or 0
+  uint64_t pad;
 };
-static_assert(sizeof(WorkItem) == 80, "work item layout");
+static_assert(sizeof(WorkItem) == 96, "work item layout: six 16-byte loads");
 
 struct HostShared {
   unsigned long long published;
@@ -105,19 +107,28 @@ __device__ __forceinline__ void st_release_sys_u32(unsigned int *p, unsigned int
   asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// A work item from mapped host memory: five 16-byte loads in flight at once.
+// A work item from mapped host memory: six 16-byte loads in flight at once.
 __device__ __forceinline__ void load_item(const WorkItem *src, WorkItem *dst) {
   const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
   uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-  uint4 v[5];
+  uint4 v[6];
 #pragma unroll
-  for (int k = 0; k < 5; ++k)
+  for (int k = 0; k < 6; ++k)
     asm volatile("ld.volatile.global.v4.u32 {%0,%1,%2,%3}, [%4];"
                  : "=r"(v[k].x), "=r"(v[k].y), "=r"(v[k].z), "=r"(v[k].w)
                  : "l"(s4 + k)
                  : "memory");
 #pragma unroll
-  for (int k = 0; k < 5; ++k) d4[k] = v[k];
+  for (int k = 0; k < 6; ++k) d4[k] = v[k];
+}
+
+// Zero-tree bit of the vertex named c, through L2 only: the executor's blocks
+// outlive other kernels' writes, and an arena region reused by a new graph
+// must never show the bits of the old one from a stale L1 line.
+__device__ __forceinline__ bool zbit_cg(const uint32_t *Z, uint32_t c) {
+  uint32_t w;
+  asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(w) : "l"(Z + (c >> 5)) : "memory");
+  return (w >> (c & 31u)) & 1u;
 }
 
 // Request buffers may be rewritten by the client between requests while the
@@ -216,9 +227,10 @@ __global__ void __launch_bounds__(256) k_executor(HostShared *hs, DevShared *ds,
       if (bad) atomicMax(&s_bad, 1u);
     }
     __syncthreads();
+    uint32_t *const Zb = reinterpret_cast<uint32_t *>(it.Z);
     if ((it.kind == kItemEdges && !s_bad) || (it.kind == kItemApply && !s_skip)) {
       WarpRing ring;
-      ring.init(ring_smem, nullptr, reinterpret_cast<uint32_t *>(it.log));
+      ring.init(ring_smem, Zb, reinterpret_cast<uint32_t *>(it.log));
       // warp-uniform rounds of kEpt edges per thread, all parent loads issued together
       for (uint64_t r0 = it.begin; r0 < it.end; r0 += (uint64_t)blockDim.x * kEpt) {
         uint32_t a[kEpt], b[kEpt], pa[kEpt], pb[kEpt];
@@ -238,10 +250,13 @@ __global__ void __launch_bounds__(256) k_executor(HostShared *hs, DevShared *ds,
 #pragma unroll
         for (int j = 0; j < kEpt; ++j) {
           if (pa[j]) {
-            pa[j] = ldP_cg(P + a[j]);
-            pb[j] = ldP_cg(P + b[j]);
-            a[j] = name_of(a[j], rf, m);
-            b[j] = name_of(b[j], rf, m);
+            const uint32_t na = name_of(a[j], rf, m), nb = name_of(b[j], rf, m);
+            // a vertex known to be in the tree of name 0 needs no parent load
+            const bool za = Zb && zbit_cg(Zb, na), zb = Zb && zbit_cg(Zb, nb);
+            pa[j] = za ? 0u : ldP_cg(P + a[j]);
+            pb[j] = zb ? 0u : ldP_cg(P + b[j]);
+            a[j] = na;
+            b[j] = nb;
           }
         }
 #pragma unroll
@@ -268,8 +283,10 @@ __global__ void __launch_bounds__(256) k_executor(HostShared *hs, DevShared *ds,
             } else {
               c[2 * j] = name_of(q.x, rf, m);
               c[2 * j + 1] = name_of(q.y, rf, m);
-              p[2 * j] = ldP_cg(P + q.x);
-              p[2 * j + 1] = ldP_cg(P + q.y);
+              // an endpoint in the tree of name 0 has root 0: no walk
+              const bool zx = Zb && zbit_cg(Zb, c[2 * j]), zy = Zb && zbit_cg(Zb, c[2 * j + 1]);
+              p[2 * j] = zx ? 0u : ldP_cg(P + q.x);
+              p[2 * j + 1] = zy ? 0u : ldP_cg(P + q.y);
               done[2 * j] = done[2 * j + 1] = false;
               valid[j] = true;
             }
@@ -610,6 +627,8 @@ void write_tiles(cc_server *s, const Req &r, uint32_t kind, uint64_t count, cons
     w.end = w.begin + tile < count ? w.begin + tile : count;
     w.out = (uint64_t)(uintptr_t)r.r.out_dev;
     w.log = (uint64_t)(uintptr_t)g.logs[g.cur_log];
+    w.Z = (uint64_t)(uintptr_t)g.Z;
+    w.pad = 0;
   }
   pub += nt;
 }
