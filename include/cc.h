@@ -131,7 +131,7 @@ typedef struct cc_options {
   uint64_t root_hint;        /* vertex to plant as m, or CC_ROOT_AUTO (default)   */
   int32_t filter;            /* cc_filter, default CC_FILTER_AUTO                 */
   int32_t label_space;       /* cc_label_space, default CC_LABEL_MIN_ID           */
-  int32_t block_size;        /* edge-pass threads per block; 0 = auto             */
+  int32_t block_size;        /* edge-pass threads per block (128, 256, 512); 0 = 512 */
   int32_t edges_per_thread;  /* edges per thread per iteration (2, 4 or 8); 0 = auto */
   int32_t sample_stride;     /* sampled root select keeps 1 group in k; 0 = 16     */
   int32_t timing;            /* nonzero: record per-phase times (cc_phase_times)  */

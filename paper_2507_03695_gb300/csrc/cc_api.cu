@@ -125,7 +125,7 @@ int eff_filter(const cc_graph *g) {
   return 1;
 }
 int eff_ept(const cc_graph *g) { return g->opt.edges_per_thread ? g->opt.edges_per_thread : 4; }
-int eff_block(const cc_graph *g) { return g->opt.block_size ? g->opt.block_size : 256; }
+int eff_block(const cc_graph *g) { return g->opt.block_size ? g->opt.block_size : 512; }
 
 cudaError_t dev_alloc(cc_graph *g, void **p, size_t bytes) {
   if (g->opt.hbm_budget_bytes && g->owned + bytes > g->opt.hbm_budget_bytes)

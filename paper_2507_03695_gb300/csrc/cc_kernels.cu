@@ -164,18 +164,20 @@ __global__ void __launch_bounds__(512) k_edge_pass_direct(const uint4 *__restric
 // (measured edge pass, R-MAT 28: 32.50 -> 31.61 ms, R-MAT 24: 1.94 -> 1.79);
 // 8192 entries lost occupancy and ran slower.
 
-template <class F, int Q, bool kZ, bool kDirect>
+template <class F, int Q, bool kZ, bool kDirect, bool kL2 = false>
 __global__ void __launch_bounds__(512, Q >= 4 ? (kZ ? 1 : 2) : (kZ ? 2 : (kDirect ? 4 : 3)))
     k_edge_pass_filtered(const uint4 *__restrict__ e4, uint64_t n_quads, const uint2 *head, const uint2 *tail,
                          uint32_t *P, uint32_t n, Ctrl *ctrl, const uint32_t *skip, uint32_t *Z,
                          const uint32_t *sel, uint32_t *log, unsigned long long *work, uint32_t grab,
                          const unsigned long long *hot) {
   static_assert(kDirect || !kZ, "the zero-tree form resolves in place");
-  // The queue form (a certified hub, P within L2) reads P through L2 only:
-  // its random parent loads almost never hit L1, and skipping L1 allocation
-  // measured faster there (R-MAT scale 24: 2.02 -> 1.94 ms); the other forms
-  // keep L1 (the grid's searches hit it: 1.27 ms without it against 0.94).
-  constexpr bool kCG = !kZ && !kDirect;
+  // kL2 (the queue form on a parent array of at least kL2MinVertices): P is
+  // read through L2 only. Its random parent loads almost never hit L1 then,
+  // and skipping L1 allocation measured faster (R-MAT scale 24: 2.02 -> 1.94
+  // ms); a small P lives in L1 (R-MAT 16's 256 KB: 0.077 ms with L1, 0.13
+  // without), and the grid's searches hit L1 (1.27 ms without it, 0.94 with).
+  static_assert(!kL2 || (!kZ && !kDirect), "L2-only loads only in the queue form");
+  constexpr bool kCG = kL2;
   extern __shared__ uint32_t ring_smem[];
   if (skip && ld_volatile_u32(skip)) return;
   if (sel && ((ld_volatile_u32(sel) != 0u) != (kZ || !kDirect))) return;
@@ -640,6 +642,8 @@ cudaError_t launch_init(bool rf, uint32_t *P, uint32_t n, Ctrl *ctrl, int m_src,
 
 namespace {
 constexpr uint64_t kMinWaves = 8;
+// The queue form reads P through L2 only from this many vertices up (16 MB).
+constexpr uint32_t kL2MinVertices = 1u << 22;
 
 // Claim size of the dynamic schedule, in warp steps. From 2^20 edges up,
 // 16 steps at a time (measured best there: fewer warps start on the hub's
@@ -691,12 +695,17 @@ cudaError_t edge_pass_q(int filter, int block, const EdgeSpan &e, uint32_t *P, u
       note_launch();
     }
     if (!Z && hub) {
-      const void *k = (const void *)k_edge_pass_filtered<F, Q, false, false>;
+      const bool l2 = n >= kL2MinVertices;
+      const void *k = l2 ? (const void *)k_edge_pass_filtered<F, Q, false, false, true>
+                         : (const void *)k_edge_pass_filtered<F, Q, false, false, false>;
       const unsigned g = clamp_grid(want, one_shot ? cap_big : persistent_cap(k, block, smem_hub));
       const uint32_t grab = grab_for(e.n_quads, Q, g, block);
-      k_edge_pass_filtered<F, Q, false, false><<<g, block, smem_hub, s>>>(e.quads, e.n_quads, e.head, e.tail, P,
-                                                                          n, ctrl, skip, nullptr, hub, log, work,
-                                                                          grab, hot);
+      if (l2)
+        k_edge_pass_filtered<F, Q, false, false, true><<<g, block, smem_hub, s>>>(
+            e.quads, e.n_quads, e.head, e.tail, P, n, ctrl, skip, nullptr, hub, log, work, grab, hot);
+      else
+        k_edge_pass_filtered<F, Q, false, false, false><<<g, block, smem_hub, s>>>(
+            e.quads, e.n_quads, e.head, e.tail, P, n, ctrl, skip, nullptr, hub, log, work, grab, hot);
       note_launch();
     }
     if (!Z || zsel) {
