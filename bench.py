@@ -76,6 +76,11 @@ def parse_args(argv=None):
     p.add_argument("--batched-graphs", type=int, default=4096)
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-csr", action="store_true")
+    p.add_argument("--executor-only", action="store_true",
+                   help="run only the serving executor's insert and query bursts on the resident R-MAT "
+                        "scale-26 graph and print their line (the command of the executor's ncu summary)")
+    p.add_argument("--publish-wait-us", type=int, default=0,
+                   help="the executor's bounded wait for an unpublished ring item (0: the library default)")
     p.add_argument("--serving-requests", type=int, default=20000,
                    help="requests per arrival rate")
     p.add_argument("--cpu-fraction", type=float, default=None,
@@ -140,6 +145,33 @@ def kernel_source_sha() -> str:
         i += 1
     h.update(text[start:i + 1].encode())
     return h.hexdigest()[:16]
+
+
+def executor_source_sha() -> str:
+    """Hash of the serving executor's code: csrc/cc_device.cuh and all of
+    csrc/cc_server.cu (its host scheduler sets the tile sizes, which change
+    the executor's traffic too)."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2507_03695_gb300", "csrc")
+    for name in ("cc_device.cuh", "cc_server.cu"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_executor_traffic():
+    """DRAM bytes per inserted edge and per query pair of the executor bursts,
+    from the committed ncu summary, if it was taken on the current source."""
+    path = os.path.join(ROOT, "profiles", "executor_rmat26.md")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for line in f:
+            if line.startswith("traffic_per_unit:"):
+                parts = dict(kv.split("=") for kv in line.split(":", 1)[1].split())
+                if parts.get("source_sha") == executor_source_sha():
+                    return {"insert": float(parts["insert"]), "query": float(parts["query"])}
+    return None
 
 
 def profiled_traffic(workload: str, graphs):
@@ -348,6 +380,42 @@ def edge_pass_roofline(graphs, phase_ms, workload: str, names, peak: float, peak
             "algorithmic_bytes": "8 B per edge per launch"}
 
 
+ZERO_TREE_MIN_P_BYTES = 128 << 20  # the library keeps the zero-tree bitmap from this parent-array size up
+
+
+def lookup_array_bytes(name: str, n: int) -> tuple[int, str]:
+    """The array whose random 4-byte reads the edge pass's endpoint lookups
+    are: R-MAT graphs certify a hub, and from a 128 MiB parent array up their
+    lookups read the zero-tree bitmap (n/8 bytes); otherwise they read P."""
+    if name.startswith("rmat") and 4 * n >= ZERO_TREE_MIN_P_BYTES:
+        return (n + 7) // 8, "zero-tree bitmap"
+    return 4 * n, "parent array P"
+
+
+def request_roofline(cc, graphs, phase_ms, cache) -> dict:
+    """The edge pass against the rate at which the device serves random
+    4-byte loads from an array of the size its lookups read (measured now
+    by cc_measure_random_loads): 2 lookups per edge, each its own request."""
+    by_graph = {}
+    for (w, _, E), p in zip(graphs, phase_ms):
+        nbytes, what = lookup_array_bytes(w.name, w.n_vertices)
+        size = 1 << max(16, (nbytes - 1).bit_length())
+        if size not in cache:
+            cache[size] = cc.cc_measure_random_loads(size)
+        achieved = 2 * E / (p[2] * 1e-3) / 1e9
+        by_graph[w.name] = {"achieved": achieved, "peak": cache[size] / 1e9, "frac": achieved * 1e9 / cache[size],
+                            "lookup_array": what, "lookup_array_bytes": nbytes, "probe_array_bytes": size}
+    lookups = sum(2 * E for _, _, E in graphs)
+    t = sum(p[2] for p in phase_ms) * 1e-3
+    peak = sum(2 * E / by_graph[w.name]["peak"] for w, _, E in graphs) / lookups  # time-weighted
+    peak = 1.0 / peak
+    return {"bound": "l2_random_requests", "achieved": lookups / t / 1e9, "peak": peak, "unit": "G lookups/s",
+            "frac": lookups / t / 1e9 / peak, "by_graph": by_graph,
+            "algorithmic_requests": "2 endpoint lookups per edge (random 4-byte reads, one L2 request each)",
+            "peak_source": "measured in this run: cc_measure_random_loads on an array of the lookup array's "
+                           "size rounded up to a power of two (best of 4 launch shapes)"}
+
+
 def phases_dict(names, phase_ms):
     return {nm: {"root_select": p[0], "init": p[1], "edge_pass": p[2], "flatten": p[3], "total": p[4]}
             for nm, p in zip(names, phase_ms)}
@@ -381,6 +449,8 @@ def run_ours(args):
 
     if args.sharded:
         return run_sharded_bench(args, cc, graphgen, torch, dist, dev, rank, world, barrier, max_over_ranks)
+    if args.executor_only:
+        return run_executor_only(args, cc, graphgen, torch)
     names = WORKLOADS[args.workload]
     ws = [graphgen.WORKLOADS[nm] for nm in names]
     graphs = []
@@ -402,6 +472,8 @@ def run_ours(args):
     elapsed_ms, value = replica_summary(elapsed_local, E_total, args.steps, world, max_over_ranks)
     peak, peak_kind = measured_peaks()
     roofline = edge_pass_roofline(graphs, phase_ms, args.workload, names, peak, peak_kind)
+    probe_cache = {}
+    req_roofline = request_roofline(cc, graphs, phase_ms, probe_cache)
     ms_per_step = elapsed_ms / args.steps
     path_bytes = sum(8 * E + 12 * w.n_vertices + 8 * E + 4 * w.n_vertices for w, _, E in graphs)
 
@@ -511,7 +583,8 @@ def run_ours(args):
                  "gteps": x_E * args.steps / (x_ms * 1e-3) / 1e9, "ms_per_step": x_ms / args.steps,
                  "steps": args.steps, "phases_ms": phases_dict(x_names, x_phase),
                  "gteps_without_root_select": x_E / (sum(p[4] - p[0] for p in x_phase) * 1e-3) / 1e9,
-                 "roofline": edge_pass_roofline(x_graphs, x_phase, args.extra_workload, x_names, peak, peak_kind)}
+                 "roofline": edge_pass_roofline(x_graphs, x_phase, args.extra_workload, x_names, peak, peak_kind),
+                 "request_roofline": request_roofline(cc, x_graphs, x_phase, probe_cache)}
         del x_labels
         if not args.no_csr:
             csr = bench_csr(args, cc, x_graphs, torch, stream)
@@ -543,6 +616,7 @@ def run_ours(args):
                              + " and ".join(f"{8 * E / 1e9:.2f} GB" for E in E_list)
                              + " vs 129 MB L2)"},
             "roofline": roofline,
+            "request_roofline": req_roofline,
             "phases_ms": phases_dict(names, phase_ms),
             "path_algorithmic_gbs": path_bytes / (ms_per_step * 1e-3) / 1e9,
             "gteps_without_root_select": E_total / (sum(p[4] - p[0] for p in phase_ms) * 1e-3) / 1e9,
@@ -844,7 +918,7 @@ def bench_serving(args, cc, graphgen, torch):
             done[i] = t_free
         plain_lat = (done - arrivals) * 1e3
         # the serving runtime
-        srv = cc.Server(24 << 30, idle_timeout_us=200000)
+        srv = cc.Server(24 << 30, idle_timeout_us=200000, publish_wait_us=publish_wait_us)
         t, gid = srv.new_graph(n, e_res)
         if srv.wait(t, 120) != cc.CC_OK:
             raise RuntimeError("resident graph admission failed")
@@ -889,7 +963,7 @@ def bench_serving(args, cc, graphgen, torch):
             "edges_per_s": edges_total / makespan, "plain_edges_per_s": edges_total / max(done[-1], arrivals[-1]),
             "executor_launches": st["executor_launches"], "side_drains": st["side_drains"],
         })
-    executor = bench_executor(cc, torch, n, e_res, pool, qpool, qout)
+    executor = bench_executor(cc, torch, n, e_res, pool, qpool, qout, args.publish_wait_us)
     del pool, qpool, new_edges, snap, e_res
     torch.cuda.empty_cache()
     return {"resident": w.name, "requests_per_rate": R,
@@ -904,7 +978,22 @@ def bench_serving(args, cc, graphgen, torch):
                                "latency. The burst (every request at once) compares saturated throughput"}
 
 
-def bench_executor(cc, torch, n, e_res, pool, qpool, qout):
+def run_executor_only(args, cc, graphgen, torch):
+    """The executor bursts of the serving section alone, on the same inputs
+    (resident R-MAT scale-26 graph, uniform insert pairs, query pairs)."""
+    w = graphgen.RMAT26
+    e_res = w.device_edges()
+    pool = graphgen.pairs_dev(w.n_vertices, 1 << 26, 61)
+    qpool = graphgen.pairs_dev(w.n_vertices, 1 << 22, 62)
+    qout = torch.empty(10 ** 4 * 64, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    executor = bench_executor(cc, torch, w.n_vertices, e_res, pool, qpool, qout, args.publish_wait_us)
+    print(json.dumps({"executor": executor, "resident": w.name, "n_gpus": 1,
+                      "data": "synthetic: seeded R-MAT and uniform pairs, generated in HBM"}), flush=True)
+    return 0
+
+
+def bench_executor(cc, torch, n, e_res, pool, qpool, qout, publish_wait_us=0):
     """Throughput of the serving executor alone: bursts of equal insert
     batches (2^17 uniform pairs each, below the side-stream size, so all run as
     executor tiles on the live parent array of the resident graph) and of
@@ -912,8 +1001,9 @@ def bench_executor(cc, torch, n, e_res, pool, qpool, qout):
     the first submission to the last completion (host scheduling included)."""
     import time
     peak, peak_kind = measured_peaks()
+    traffic = profiled_executor_traffic()
     out = {}
-    srv = cc.Server(24 << 30, idle_timeout_us=200000)
+    srv = cc.Server(24 << 30, idle_timeout_us=200000, publish_wait_us=publish_wait_us)
     try:
         t, gid = srv.new_graph(n, e_res)
         if srv.wait(t, 120) != cc.CC_OK:
@@ -941,7 +1031,10 @@ def bench_executor(cc, torch, n, e_res, pool, qpool, qout):
             out[kind] = {"requests": K, "units": units, "seconds": dt,
                          ("edges_per_s" if kind == "insert" else "pairs_per_s"): units / dt,
                          "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                                      "frac": achieved / peak, "traffic": None,
+                                      "frac": achieved / peak,
+                                      "traffic": traffic[kind] * units / K if traffic else None,
+                                      "traffic_note": "DRAM bytes per request (mean), from the ncu summary "
+                                                      "of the executor's launches on the current source",
                                       "algorithmic_bytes": "8 B per inserted edge" if kind == "insert"
                                       else "8 B per query pair read + 1 B answer written",
                                       "timing": "host clock over the burst (submission to last completion)",

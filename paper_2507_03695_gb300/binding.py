@@ -118,6 +118,7 @@ def lib():
             "cc_phase_times_total": (_i32, [_ptr, P(ctypes.c_float), P(_u64)]),
             "cc_kernel_launches": (_u64, []),
             "cc_max_degree_vertex_noalloc": (_i32, [_ptr, _u64, _u64, _ptr, _ptr]),
+            "cc_measure_random_loads": (_i32, [_u64, P(ctypes.c_double)]),
             "cc_checkpoint_size": (_i32, [_ptr, P(_u64)]),
             "cc_checkpoint": (_i32, [_ptr, _ptr, _u64]),
             "cc_restore": (_i32, [_ptr, _ptr, _u64]),
@@ -326,6 +327,14 @@ def cc_max_degree_vertex_noalloc(edges, n_vertices: int, m_out, n_edges: int | N
     _check(lib().cc_max_degree_vertex_noalloc(_addr(edges), _count_pairs(edges, n_edges), n_vertices,
                                               _addr(m_out), _stream(stream)),
            "cc_max_degree_vertex_noalloc")
+
+
+def cc_measure_random_loads(array_bytes: int) -> float:
+    """Random 4-byte loads per second from an array of array_bytes bytes on
+    the current device (a power of two in [2^16, 2^32])."""
+    r = ctypes.c_double()
+    _check(lib().cc_measure_random_loads(array_bytes, ctypes.byref(r)), "cc_measure_random_loads")
+    return r.value
 
 
 def cc_checkpoint_size(g: int) -> int:

@@ -985,11 +985,13 @@ bool reap_executor(cc_server *s, std::vector<uint32_t> *touched) {
   return any;
 }
 
-// Launches the executor when work is in flight; stops it after an idle
-// period; after it has left, rewinds `taken` to `published` (all published
-// items were processed) so that claims made while waiting are forgotten.
-void manage_executor(cc_server *s) {
-  const uint64_t now = host_ns();
+// Handles an executor that has left (asked to, or after its own bounded
+// wait): completes what it finished, fails what it left in flight, and
+// rewinds `taken` to `published` (all published items were processed or
+// failed) so that claims made while waiting are forgotten. Runs before new
+// requests are started in a scheduler pass, so that tiles published after the
+// executor left wait for the next launch instead of being failed with it.
+void executor_departed(cc_server *s) {
   if (s->exec_running && cudaEventQuery(s->exec_ev) == cudaSuccess) {
     // the executor has left (asked to, or after its own bounded wait); its
     // last completions may have become visible only now
@@ -1020,6 +1022,13 @@ void manage_executor(cc_server *s) {
     s->exec_running = false;
     s->exec_stopping = false;
   }
+}
+
+// Launches the executor when work is in flight and stops it after an idle
+// period.
+void manage_executor(cc_server *s) {
+  const uint64_t now = host_ns();
+  executor_departed(s);
   if (s->held && now >= s->held_until) {  // the stuck producer publishes at last
     std::atomic_thread_fence(std::memory_order_seq_cst);
     *(volatile unsigned long long *)&s->hs->published = s->held_pub;
@@ -1072,6 +1081,7 @@ bool scheduler_step(cc_server *s, std::vector<Req *> &incoming) {
   }
   incoming.clear();
   if (reap_executor(s, &touched)) progress = true;
+  executor_departed(s);
   // side-stream completions
   for (size_t i = 0; i < s->side_running.size();) {
     Req *r = s->side_running[i];

@@ -111,6 +111,11 @@ def test_host_side_errors(lib):
     assert L.cc_create(1 << 20, 0, ctypes.byref(small), ctypes.byref(h)) == lib.CC_ERR_OOM
     assert h.value is None
     assert L.cc_create(10, 0, None, None) == lib.CC_ERR_INVALID_ARGUMENT
+    # the random-load measurement checks its arguments before touching a GPU
+    r = ctypes.c_double()
+    for bad_bytes in (0, 1 << 15, (1 << 20) + 4, 3 << 20, 1 << 33):
+        assert L.cc_measure_random_loads(bad_bytes, ctypes.byref(r)) == lib.CC_ERR_INVALID_ARGUMENT
+    assert L.cc_measure_random_loads(1 << 20, None) == lib.CC_ERR_INVALID_ARGUMENT
     # NULL handles
     assert L.cc_run(None, None, 0, None, None) == lib.CC_ERR_INVALID_ARGUMENT
     assert L.cc_stream_insert(None, None, 0, None) == lib.CC_ERR_INVALID_ARGUMENT
