@@ -51,6 +51,7 @@ WORKLOADS = {
     "rmat28": ["rmat28_ef16"],
     "rmat26ef4": ["rmat26_ef4"],
     "rmat16": ["rmat16_ef16"],
+    "rmat24u": ["rmat24_ef16_u"],
 }
 
 EDGE_PASS_BYTES_PER_EDGE = 8  # one streamed read of the (u, v) pair
@@ -569,6 +570,7 @@ def run_ours(args):
     torch.cuda.empty_cache()
     extra = None
     csr = None
+    unscrambled = None
     if args.extra_workload and args.extra_workload != args.workload:
         x_names = WORKLOADS[args.extra_workload]
         x_graphs = []
@@ -589,6 +591,19 @@ def run_ours(args):
         if not args.no_csr:
             csr = bench_csr(args, cc, x_graphs, torch, stream)
         del x_graphs
+        torch.cuda.empty_cache()
+        # secondary row: R-MAT 24 without the id scramble (hubs at low ids)
+        u = graphgen.WORKLOADS["rmat24_ef16_u"]
+        u_graphs = [(u, u.device_edges(), u.n_edges)]
+        torch.cuda.synchronize()
+        u_ms, u_phase, _, _, u_labels = measure_single(cc, torch, u_graphs, stream, args.steps, args.warmup)
+        unscrambled = {"workload": "rmat24u", "graphs": [u.name], "n_vertices": [u.n_vertices],
+                       "n_edges": [u.n_edges], "gteps": u.n_edges * args.steps / (u_ms * 1e-3) / 1e9,
+                       "ms_per_step": u_ms / args.steps, "steps": args.steps,
+                       "phases_ms": phases_dict([u.name], u_phase),
+                       "roofline": edge_pass_roofline(u_graphs, u_phase, "rmat24u", [u.name], peak, peak_kind),
+                       "request_roofline": request_roofline(cc, u_graphs, u_phase, probe_cache)}
+        del u_graphs, u_labels
         torch.cuda.empty_cache()
     batched = None if args.no_batched else bench_batched(args, cc, graphgen, torch, stream)
     serving = None
@@ -622,6 +637,7 @@ def run_ours(args):
             "gteps_without_root_select": E_total / (sum(p[4] - p[0] for p in phase_ms) * 1e-3) / 1e9,
             "e2e": e2e,
             "extra_workload": extra,
+            "unscrambled_rmat24": unscrambled,
             "csr": csr,
             "batched": batched,
             "serving": serving,

@@ -346,5 +346,8 @@ RMAT26 = rmat_workload("rmat26_ef16", 26, 16, 6, scramble=True)
 # A profiling case for the zero-tree edge pass: the parent array (268 MB) is
 # larger than L2 while the edges (2.1 GB) stay a few GB.
 RMAT26_EF4 = rmat_workload("rmat26_ef4", 26, 4, 7, scramble=True)
+# R-MAT scale 24 as generated, without the id scramble: the hubs keep low ids,
+# which changes the parent array's cache locality (a secondary row of C2).
+RMAT24_U = rmat_workload("rmat24_ef16_u", 24, 16, 2, scramble=False)
 
-WORKLOADS = {w.name: w for w in (RMAT16, RMAT24, GRID8K, RMAT28, RMAT26, RMAT26_EF4)}
+WORKLOADS = {w.name: w for w in (RMAT16, RMAT24, GRID8K, RMAT28, RMAT26, RMAT26_EF4, RMAT24_U)}

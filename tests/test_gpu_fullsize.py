@@ -26,7 +26,7 @@ def sha_tensor(t) -> str:
     return hashlib.sha256(t.contiguous().cpu().numpy().view(np.uint8)).hexdigest()
 
 
-@pytest.mark.parametrize("name", ["rmat24_ef16", "grid8192x8192_p0.9"])
+@pytest.mark.parametrize("name", ["rmat24_ef16", "grid8192x8192_p0.9", "rmat24_ef16_u"])
 def test_fullsize_against_oracle_values(name):
     with open(os.path.join(GOLDEN, f"{name}.json")) as f:
         gold = json.load(f)
