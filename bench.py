@@ -496,8 +496,29 @@ def run_ours(args):
             for h in e2e_handles:
                 cc.cc_sync(h.h)
 
+        def link_rates():
+            """Plain copies of the same bytes over the host link, timed with CUDA
+            events: the pinned edges into the device edge arrays (same values)
+            and the device labels into the pinned label buffers."""
+            st = torch.cuda.Stream()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            torch.cuda.synchronize()
+            with torch.cuda.stream(st):
+                ev[0].record(st)
+                for h_e, (_, e, _) in zip(host_e, graphs):
+                    e.copy_(h_e, non_blocking=True)
+                ev[1].record(st)
+                for h_l, L in zip(host_L, labels):
+                    h_l.copy_(L, non_blocking=True)
+                ev[2].record(st)
+            st.synchronize()
+            h2d = sum(8 * E for _, _, E in graphs) / (ev[0].elapsed_time(ev[1]) * 1e-3) / 1e9
+            d2h = sum(4 * w.n_vertices for w, _, _ in graphs) / (ev[1].elapsed_time(ev[2]) * 1e-3) / 1e9
+            return h2d, d2h
+
         for _ in range(max(1, min(args.warmup, 3))):
             e2e_step()
+        link_before = link_rates()
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -511,11 +532,23 @@ def run_ours(args):
         for h_l, L in zip(host_L, labels):
             if not torch.equal(h_l, L.cpu()):
                 raise RuntimeError("cc_run_host labels differ from cc_run labels")
+        link_after = link_rates()  # overwrites host_L with the same labels
         e2e = {"value": world * E_total * k_e2e / t_e2e / 1e9, "unit": "GTEPS",
                "h2d_bytes_per_step": int(sum(8 * E for _, _, E in graphs)),
                "d2h_bytes_per_step": int(sum(4 * w.n_vertices for w, _, _ in graphs)),
                "steps": k_e2e,
                "api": "cc_run_host_async per graph, one stream each, then cc_sync (pinned host buffers)"}
+        h2d_gbs = (link_before[0] + link_after[0]) / 2
+        d2h_gbs = (link_before[1] + link_after[1]) / 2
+        t_link = e2e["h2d_bytes_per_step"] / (h2d_gbs * 1e9) + e2e["d2h_bytes_per_step"] / (d2h_gbs * 1e9)
+        ceiling = E_total / t_link / 1e9
+        e2e["host_link"] = {
+            "h2d_gbs": h2d_gbs, "d2h_gbs": d2h_gbs,
+            "h2d_gbs_before_after": [link_before[0], link_after[0]],
+            "d2h_gbs_before_after": [link_before[1], link_after[1]],
+            "ceiling_gteps": ceiling, "frac_of_ceiling": e2e["value"] / world / ceiling,
+            "note": "plain copies of the step's bytes (edges in, labels out) timed just before and after the "
+                    "e2e loop; the ceiling is the step's bytes over those rates, with no compute"}
         # the same through the compact encoding: 3-byte ids where they suffice
         idb = [3 if w.n_vertices <= (1 << 24) else 4 for w, _, _ in graphs]
         if any(b == 3 for b in idb):
@@ -934,7 +967,7 @@ def bench_serving(args, cc, graphgen, torch):
             done[i] = t_free
         plain_lat = (done - arrivals) * 1e3
         # the serving runtime
-        srv = cc.Server(24 << 30, idle_timeout_us=200000, publish_wait_us=publish_wait_us)
+        srv = cc.Server(24 << 30, idle_timeout_us=200000, publish_wait_us=args.publish_wait_us)
         t, gid = srv.new_graph(n, e_res)
         if srv.wait(t, 120) != cc.CC_OK:
             raise RuntimeError("resident graph admission failed")
