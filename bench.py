@@ -1054,37 +1054,49 @@ def bench_executor(cc, torch, n, e_res, pool, qpool, qout, publish_wait_us=0):
     out = {}
     srv = cc.Server(24 << 30, idle_timeout_us=200000, publish_wait_us=publish_wait_us)
     try:
-        t, gid = srv.new_graph(n, e_res)
-        if srv.wait(t, 120) != cc.CC_OK:
-            raise RuntimeError("resident graph admission failed")
+        # two copies of the resident graph, so that both submission forms see
+        # the same history: per-request calls on the first, one call on the second
+        gids = {}
+        for form in ("one", "many"):
+            t, gids[form] = srv.new_graph(n, e_res)
+            if srv.wait(t, 120) != cc.CC_OK:
+                raise RuntimeError("resident graph admission failed")
         size, K = 1 << 17, 512
         span = pool.shape[0] - size
         batches = [pool[(i * 104729) % span:(i * 104729) % span + size] for i in range(K)]
         q_batches = [qpool[(i * 7919) % (qpool.shape[0] - 10 ** 4):(i * 7919) % (qpool.shape[0] - 10 ** 4) + 10 ** 4]
                      for i in range(K)]
-        for kind in ("insert", "query"):
+        q_outs = [qout[i % 64 * 10 ** 4:(i % 64 + 1) * 10 ** 4] for i in range(K)]
+        for kind in ("insert", "query", "insert_submit_many", "query_submit_many"):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             if kind == "insert":
-                tickets = [srv.insert(gid, b) for b in batches]
+                tickets = [srv.insert(gids["one"], b) for b in batches]
+            elif kind == "query":
+                tickets = [srv.query(gids["one"], q, o) for q, o in zip(q_batches, q_outs)]
+            elif kind == "insert_submit_many":
+                tickets = srv.insert_many(gids["many"], batches)
             else:
-                tickets = [srv.query(gid, q, qout[i % 64 * 10 ** 4:(i % 64 + 1) * 10 ** 4])
-                           for i, q in enumerate(q_batches)]
+                tickets = srv.query_many(gids["many"], q_batches, q_outs)
             for tk in tickets:
                 if srv.wait(tk, 120) != cc.CC_OK:
                     raise RuntimeError(f"executor {kind} burst failed")
             dt = time.perf_counter() - t0
-            units = K * (size if kind == "insert" else 10 ** 4)
-            per_unit = 8 if kind == "insert" else 9
+            is_insert = kind.startswith("insert")
+            units = K * (size if is_insert else 10 ** 4)
+            per_unit = 8 if is_insert else 9
             achieved = per_unit * units / dt / 1e9
             out[kind] = {"requests": K, "units": units, "seconds": dt,
-                         ("edges_per_s" if kind == "insert" else "pairs_per_s"): units / dt,
+                         "submission": "one cc_server_submit_many call" if kind.endswith("many")
+                         else "one cc_server_submit call per request",
+                         ("edges_per_s" if is_insert else "pairs_per_s"): units / dt,
                          "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                       "frac": achieved / peak,
-                                      "traffic": traffic[kind] * units / K if traffic else None,
+                                      "traffic": traffic["insert" if is_insert else "query"] * units / K
+                                      if traffic else None,
                                       "traffic_note": "DRAM bytes per request (mean), from the ncu summary "
                                                       "of the executor's launches on the current source",
-                                      "algorithmic_bytes": "8 B per inserted edge" if kind == "insert"
+                                      "algorithmic_bytes": "8 B per inserted edge" if is_insert
                                       else "8 B per query pair read + 1 B answer written",
                                       "timing": "host clock over the burst (submission to last completion)",
                                       "peak_source": f"{peak_kind} (HBM copy bandwidth)"}}

@@ -133,6 +133,17 @@ CC_API cc_status cc_server_create(const cc_server_config *cfg, cc_server **out);
  * can never fit the arena); device-side ones through the ticket. */
 CC_API cc_status cc_server_submit(cc_server *s, const cc_request *req, uint64_t *ticket);
 
+/* Queues reqs[0 .. count) in order, as count calls of cc_server_submit would,
+ * but under one lock and with one wake-up of the scheduler. Stops at the
+ * first request that fails its host-side checks: *n_queued requests were
+ * queued (tickets[0 .. *n_queued) are theirs) and the refused request's
+ * status is returned; CC_OK when all were queued. Requests of one call keep
+ * their order, so per-graph submission order holds across the batch.
+ * Errors: CC_ERR_INVALID_ARGUMENT (NULL pointers with count > 0, a closing
+ * server), and the per-request errors of cc_server_submit. */
+CC_API cc_status cc_server_submit_many(cc_server *s, const cc_request *reqs, uint32_t count,
+                                       uint64_t *tickets, uint32_t *n_queued);
+
 /* CC_OK with *result = the request's status when it has completed,
  * CC_ERR_NOT_READY otherwise. */
 CC_API cc_status cc_server_poll(cc_server *s, uint64_t ticket, cc_status *result);

@@ -137,6 +137,7 @@ def lib():
             "cc_server_config_init": (None, [P(cc_server_config)]),
             "cc_server_create": (_i32, [P(cc_server_config), P(_ptr)]),
             "cc_server_submit": (_i32, [_ptr, P(cc_request), P(_u64)]),
+            "cc_server_submit_many": (_i32, [_ptr, P(cc_request), _u32, P(_u64), P(_u32)]),
             "cc_server_poll": (_i32, [_ptr, _u64, P(_i32)]),
             "cc_server_wait": (_i32, [_ptr, _u64, _u64, P(_i32)]),
             "cc_server_result_graph": (_i32, [_ptr, _u64, P(_u32)]),
@@ -542,6 +543,26 @@ def cc_server_submit(srv: int, req: cc_request) -> int:
     return int(t.value)
 
 
+def _request_dtype():
+    """numpy view of cc_request: the same field offsets, pointers as uint64."""
+    import numpy as np
+    kinds = {_i32: np.int32, _u32: np.uint32, _u64: np.uint64, _ptr: np.uint64}
+    names = [f[0] for f in cc_request._fields_]
+    return np.dtype({"names": names, "formats": [kinds[f[1]] for f in cc_request._fields_],
+                     "offsets": [getattr(cc_request, nm).offset for nm in names],
+                     "itemsize": ctypes.sizeof(cc_request)})
+
+
+def cc_server_submit_many(srv: int, reqs) -> tuple[list, int]:
+    """Queues a ctypes array of cc_request in order; returns (tickets of the
+    queued requests, status of the first refused one or CC_OK)."""
+    count = len(reqs)
+    tickets = (_u64 * max(count, 1))()
+    queued = _u32(0)
+    st = lib().cc_server_submit_many(srv, reqs, count, tickets, ctypes.byref(queued))
+    return list(tickets[:queued.value]), int(st)
+
+
 def cc_server_poll(srv: int, ticket: int):
     """None while running, else the request's status."""
     r = _i32(0)
@@ -605,6 +626,40 @@ class Server:
     def insert(self, graph: int, edges) -> int:
         return self._submit((edges,), kind=CC_REQ_INSERT, graph=graph, edges_dev=_addr(edges),
                             n_edges=_count_pairs(edges, None))
+
+    def _submit_many(self, kind: int, graph: int, bufs, counts, keeps, **ptr_fields) -> list:
+        """One cc_server_submit_many call for requests that differ only in
+        their buffers (ptr_fields: field name -> list of addresses)."""
+        import numpy as np
+        n = len(counts)
+        arr = (cc_request * n)()
+        view = np.frombuffer(arr, dtype=_request_dtype(), count=n)  # fields filled column-wise
+        view["kind"] = kind
+        view["graph"] = graph
+        view["n_edges" if kind == CC_REQ_INSERT else "n_pairs"] = np.asarray(counts, dtype=np.uint64)
+        for name, addrs in ptr_fields.items():
+            view[name] = np.asarray(addrs, dtype=np.uint64)
+        tickets, st = cc_server_submit_many(self.h, arr)
+        for t, keep in zip(tickets, keeps):
+            self._keep[t] = keep
+        if st != CC_OK:
+            err = CCError(st, f"cc_server_submit_many (request {len(tickets)} of {n})")
+            err.tickets = tickets  # the requests before the refused one are queued
+            raise err
+        return tickets
+
+    def insert_many(self, graph: int, edge_batches) -> list:
+        """Insert batches (each a (k, 2) int32 device tensor) queued in one call."""
+        return self._submit_many(CC_REQ_INSERT, graph, edge_batches,
+                                 [_count_pairs(e, None) for e in edge_batches], [(e,) for e in edge_batches],
+                                 edges_dev=[_addr(e) for e in edge_batches])
+
+    def query_many(self, graph: int, pair_batches, outs) -> list:
+        """Query batches with their uint8 output tensors, queued in one call."""
+        return self._submit_many(CC_REQ_QUERY, graph, pair_batches,
+                                 [_count_pairs(p, None) for p in pair_batches],
+                                 [(p, o) for p, o in zip(pair_batches, outs)],
+                                 pairs_dev=[_addr(p) for p in pair_batches], out_dev=[_addr(o) for o in outs])
 
     def query(self, graph: int, pairs, out) -> int:
         return self._submit((pairs, out), kind=CC_REQ_QUERY, graph=graph, pairs_dev=_addr(pairs),

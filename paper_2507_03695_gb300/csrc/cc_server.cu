@@ -1360,9 +1360,10 @@ cc_status cc_server_create(const cc_server_config *cfg_in, cc_server **out) {
   return CC_OK;
 }
 
-cc_status cc_server_submit(cc_server *s, const cc_request *req, uint64_t *ticket) {
-  if (!s || !req || !ticket) return CC_ERR_INVALID_ARGUMENT;
-  const cc_request &r = *req;
+namespace {
+
+// Host-side argument checks of one request (no server state).
+cc_status check_request(const cc_server *s, const cc_request &r) {
   auto misaligned = [](const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) != 0; };
   switch (r.kind) {
     case CC_REQ_NEW_GRAPH:
@@ -1371,47 +1372,94 @@ cc_status cc_server_submit(cc_server *s, const cc_request *req, uint64_t *ticket
       if (r.labels_dev && misaligned(r.labels_dev, 4)) return CC_ERR_INVALID_ARGUMENT;
       if (graph_bytes(r.n_vertices, r.n_edges, s->cfg.mode == CC_ROOT_MAXDEG) > s->cfg.hbm_budget_bytes)
         return CC_ERR_TOO_LARGE;
-      break;
+      return CC_OK;
     case CC_REQ_INSERT:
       if (r.n_edges && (!r.edges_dev || misaligned(r.edges_dev, 8))) return CC_ERR_INVALID_ARGUMENT;
-      break;
+      return CC_OK;
     case CC_REQ_QUERY:
       if (r.n_pairs && (!r.pairs_dev || !r.out_dev || misaligned(r.pairs_dev, 8))) return CC_ERR_INVALID_ARGUMENT;
-      break;
+      return CC_OK;
     case CC_REQ_SNAPSHOT:
       if (!r.labels_dev || misaligned(r.labels_dev, 4)) return CC_ERR_INVALID_ARGUMENT;
-      break;
+      return CC_OK;
     case CC_REQ_DROP_GRAPH:
-      break;
+      return CC_OK;
     default:
       return CC_ERR_INVALID_ARGUMENT;
   }
-  std::unique_ptr<Req> q(new (std::nothrow) Req());
-  if (!q) return CC_ERR_OOM;
-  q->r = r;
-  q->t_submit = host_ns();
+}
+
+// Queues requests in order until one is refused. Returns the status of the
+// refused request (CC_OK when all were queued); *n_queued tells how many were.
+cc_status submit_in_order(cc_server *s, const cc_request *reqs, uint32_t count, uint64_t *tickets,
+                          uint32_t *n_queued) {
+  *n_queued = 0;
+  cc_status st = CC_OK;
+  std::vector<std::unique_ptr<Req>> made;
+  made.reserve(count);
+  uint32_t checked = 0;
+  for (; checked < count; ++checked) {
+    if ((st = check_request(s, reqs[checked])) != CC_OK) break;
+    std::unique_ptr<Req> q(new (std::nothrow) Req());
+    if (!q) {
+      st = CC_ERR_OOM;
+      break;
+    }
+    q->r = reqs[checked];
+    made.push_back(std::move(q));
+  }
+  const uint64_t t_submit = host_ns();
+  uint32_t done = 0;
   {
     std::lock_guard<std::mutex> lk(s->sub_mu);
     if (s->quit) return CC_ERR_INVALID_ARGUMENT;
-    uint32_t gid = r.graph;
-    if (r.kind == CC_REQ_NEW_GRAPH) {
-      if (s->free_ids.empty()) return CC_ERR_TOO_LARGE;
-      gid = s->free_ids.back();
-      s->free_ids.pop_back();
-      s->id_state[gid] = 1;
-    } else {
-      if (gid >= s->cfg.max_graphs || s->id_state[gid] != 1) return CC_ERR_INVALID_ARGUMENT;
-      if (r.kind == CC_REQ_DROP_GRAPH) s->id_state[gid] = 2;
+    for (; done < made.size(); ++done) {
+      std::unique_ptr<Req> &q = made[done];
+      const cc_request &r = q->r;
+      uint32_t gid = r.graph;
+      if (r.kind == CC_REQ_NEW_GRAPH) {
+        if (s->free_ids.empty()) {
+          st = CC_ERR_TOO_LARGE;
+          break;
+        }
+        gid = s->free_ids.back();
+        s->free_ids.pop_back();
+        s->id_state[gid] = 1;
+      } else {
+        if (gid >= s->cfg.max_graphs || s->id_state[gid] != 1) {
+          st = CC_ERR_INVALID_ARGUMENT;
+          break;
+        }
+        if (r.kind == CC_REQ_DROP_GRAPH) s->id_state[gid] = 2;
+      }
+      q->graph = gid;
+      q->t_submit = t_submit;
+      s->reqs.push_back(std::move(q));
+      tickets[done] = s->reqs.size();
+      s->reqs.back()->ticket = tickets[done];
+      s->inbox.push_back(s->reqs.back().get());
     }
-    q->graph = gid;
-    s->reqs.push_back(std::move(q));
-    *ticket = s->reqs.size();
-    s->reqs.back()->ticket = *ticket;
-    s->inbox.push_back(s->reqs.back().get());
   }
-  s->submitted++;
-  s->sub_cv.notify_one();
-  return CC_OK;
+  *n_queued = done;
+  if (done) {
+    s->submitted += done;
+    s->sub_cv.notify_one();
+  }
+  return st;
+}
+
+}  // namespace
+
+cc_status cc_server_submit(cc_server *s, const cc_request *req, uint64_t *ticket) {
+  if (!s || !req || !ticket) return CC_ERR_INVALID_ARGUMENT;
+  uint32_t n = 0;
+  return submit_in_order(s, req, 1, ticket, &n);
+}
+
+cc_status cc_server_submit_many(cc_server *s, const cc_request *reqs, uint32_t count, uint64_t *tickets,
+                                uint32_t *n_queued) {
+  if (!s || !n_queued || (count && (!reqs || !tickets))) return CC_ERR_INVALID_ARGUMENT;
+  return submit_in_order(s, reqs, count, tickets, n_queued);
 }
 
 cc_status cc_server_poll(cc_server *s, uint64_t ticket, cc_status *result) {

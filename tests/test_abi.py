@@ -116,6 +116,9 @@ def test_host_side_errors(lib):
     for bad_bytes in (0, 1 << 15, (1 << 20) + 4, 3 << 20, 1 << 33):
         assert L.cc_measure_random_loads(bad_bytes, ctypes.byref(r)) == lib.CC_ERR_INVALID_ARGUMENT
     assert L.cc_measure_random_loads(1 << 20, None) == lib.CC_ERR_INVALID_ARGUMENT
+    nq = ctypes.c_uint32(7)
+    assert L.cc_server_submit_many(None, None, 0, None, ctypes.byref(nq)) == lib.CC_ERR_INVALID_ARGUMENT
+    assert L.cc_server_submit_many(None, None, 0, None, None) == lib.CC_ERR_INVALID_ARGUMENT
     # NULL handles
     assert L.cc_run(None, None, 0, None, None) == lib.CC_ERR_INVALID_ARGUMENT
     assert L.cc_stream_insert(None, None, 0, None) == lib.CC_ERR_INVALID_ARGUMENT

@@ -342,3 +342,59 @@ def test_inserts_overlap_a_snapshot(mode):
         elif kind == "snapshot":
             np.testing.assert_array_equal(mixed[i].view(np.uint32), want[i])
             np.testing.assert_array_equal(alone[i].view(np.uint32), want[i])
+
+
+def test_submit_many_keeps_order_and_stops_at_a_refused_request():
+    """cc_server_submit_many: inserts and queries queued in one call take effect
+    in order (each query sees exactly the inserts before it), and a refused
+    request ends the batch with the earlier ones queued."""
+    n = 1 << 14
+    e0 = graphgen.rmat(14, n * 2, 301, scramble=True)
+    batches = [graphgen.pairs(n, size, 302, tag=i) for i, size in enumerate([1, 500, 20000, 3, 70000, 9])]
+    q = graphgen.pairs(n, 4000, 303, tag=0)
+    seen, expect = [e0], []
+    for b in batches:
+        seen.append(b)
+        L = oracle.min_labels(n, np.concatenate(seen))
+        expect.append(L[q[:, 0]] == L[q[:, 1]])
+    with cc.Server(2 * GB) as srv:
+        t, gid = srv.new_graph(n, dev(e0))
+        assert srv.wait(t, 60) == cc.CC_OK
+        # one call, inserts and queries alternating
+        ins = [dev(b) for b in batches]
+        qd = dev(q)
+        outs = [torch.empty(q.shape[0], dtype=torch.uint8, device="cuda") for _ in batches]
+        arr = (cc.cc_request * (2 * len(batches)))()
+        for i, (e, out) in enumerate(zip(ins, outs)):
+            r = arr[2 * i]
+            r.kind, r.graph, r.edges_dev, r.n_edges = cc.CC_REQ_INSERT, gid, e.data_ptr(), e.shape[0]
+            r = arr[2 * i + 1]
+            r.kind, r.graph, r.pairs_dev, r.n_pairs, r.out_dev = cc.CC_REQ_QUERY, gid, qd.data_ptr(), q.shape[0], \
+                out.data_ptr()
+        tickets, st = cc.cc_server_submit_many(srv.h, arr)
+        assert st == cc.CC_OK and len(tickets) == 2 * len(batches)
+        for tk in tickets:
+            assert srv.wait(tk, 60) == cc.CC_OK
+        for out, ex in zip(outs, expect):
+            assert np.array_equal(out.cpu().numpy().astype(bool), ex)
+        # the wrappers: all inserts in one call, then all queries in one, on a
+        # fresh copy of the graph: every query sees every insert
+        t2, g2 = srv.new_graph(n, dev(e0))
+        assert srv.wait(t2, 60) == cc.CC_OK
+        outs2 = [torch.empty(q.shape[0], dtype=torch.uint8, device="cuda") for _ in batches]
+        tk2 = srv.insert_many(g2, ins) + srv.query_many(g2, [qd] * len(batches), outs2)
+        for tk in tk2:
+            assert srv.wait(tk, 60) == cc.CC_OK
+        for out in outs2:
+            assert np.array_equal(out.cpu().numpy().astype(bool), expect[-1])
+        # a refused request (misaligned pairs) ends the batch: the two before it are queued
+        bad = torch.empty(2 * q.shape[0] + 1, dtype=torch.int32, device="cuda")[1:].view(-1, 2)
+        o = [torch.empty(q.shape[0], dtype=torch.uint8, device="cuda") for _ in range(4)]
+        with pytest.raises(cc.CCError) as ei:
+            srv.query_many(g2, [qd, qd, bad, qd], o)
+        assert ei.value.status == cc.CC_ERR_INVALID_ARGUMENT
+        assert len(ei.value.tickets) == 2
+        for tk in ei.value.tickets:
+            assert srv.wait(tk, 60) == cc.CC_OK
+        for out in o[:2]:
+            assert np.array_equal(out.cpu().numpy().astype(bool), expect[-1])
