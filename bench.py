@@ -417,6 +417,45 @@ def request_roofline(cc, graphs, phase_ms, cache) -> dict:
                            "size rounded up to a power of two (best of 4 launch shapes)"}
 
 
+def bench_c1(cc, graphgen, torch, runs: int = 200) -> dict:
+    """R-MAT scale 16 (2^20 edges) as its configuration states it: f = id,
+    min-id labels. A launch-bound size, so it is timed two ways: cc_run
+    launched per call, and the same call captured once in a CUDA graph and
+    replayed (cc_run enqueues only stream work, so it can be captured). Mean
+    over `runs` back-to-back runs after 10 warm-up runs, CUDA events."""
+    w = graphgen.WORKLOADS["rmat16_ef16"]
+    n, E = w.n_vertices, w.n_edges
+    e = w.device_edges()
+    L = torch.empty(n, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    out = {"workload": "rmat16", "n_vertices": n, "n_edges": E, "root_function": "id (Algorithm 1)",
+           "labels": "min vertex id", "runs": runs}
+    with cc.Graph(n, mode=cc.CC_ROOT_IDENTITY) as g, torch.cuda.stream(s):
+        def timed(fn):
+            for _ in range(10):
+                fn()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            for _ in range(runs):
+                fn()
+            b.record(s)
+            b.synchronize()
+            return a.elapsed_time(b) / runs
+        ms_call = timed(lambda: cc.cc_run(g.h, e, E, L, s))
+        ref = L.clone()
+        gr = torch.cuda.CUDAGraph()
+        gr.capture_begin()
+        cc.cc_run(g.h, e, E, L, s)
+        gr.capture_end()
+        ms_graph = timed(gr.replay)
+        s.synchronize()
+        if not torch.equal(L, ref):
+            raise RuntimeError("C1: CUDA-graph replay labels differ from the per-call labels")
+    out.update({"ms_per_run": ms_call, "gteps": E / (ms_call * 1e-3) / 1e9,
+                "ms_per_run_cuda_graph": ms_graph, "gteps_cuda_graph": E / (ms_graph * 1e-3) / 1e9})
+    return out
+
+
 def phases_dict(names, phase_ms):
     return {nm: {"root_select": p[0], "init": p[1], "edge_pass": p[2], "flatten": p[3], "total": p[4]}
             for nm, p in zip(names, phase_ms)}
@@ -604,6 +643,7 @@ def run_ours(args):
     extra = None
     csr = None
     unscrambled = None
+    c1 = None
     if args.extra_workload and args.extra_workload != args.workload:
         x_names = WORKLOADS[args.extra_workload]
         x_graphs = []
@@ -638,6 +678,7 @@ def run_ours(args):
                        "request_roofline": request_roofline(cc, u_graphs, u_phase, probe_cache)}
         del u_graphs, u_labels
         torch.cuda.empty_cache()
+        c1 = bench_c1(cc, graphgen, torch)
     batched = None if args.no_batched else bench_batched(args, cc, graphgen, torch, stream)
     serving = None
     if not args.no_serving:
@@ -671,6 +712,7 @@ def run_ours(args):
             "e2e": e2e,
             "extra_workload": extra,
             "unscrambled_rmat24": unscrambled,
+            "c1": c1,
             "csr": csr,
             "batched": batched,
             "serving": serving,

@@ -166,7 +166,12 @@ CC_API cc_status cc_create(uint64_t n_vertices, uint64_t n_edges_capacity, const
  * L_out_dev is not NULL, writes uint32[n_vertices] labels in the handle's
  * label space. Stream-ordered; returns once the work is enqueued.
  * An id >= n_vertices skips that edge and sets CC_ERR_OUT_OF_RANGE for the
- * next synchronising call; the labels are then undefined. */
+ * next synchronising call; the labels are then undefined.
+ * CUDA graphs: a call may allocate scratch the first time the handle sees an
+ * edge count of its size class (below or from 2^31 edges); after that, a call
+ * with the same buffers enqueues only stream work (kernels and memsets) and
+ * can be captured into a CUDA graph. Each replay reads the captured edge
+ * buffer as it is at replay time and rewrites P and the labels. */
 CC_API cc_status cc_run(cc_graph *g, const uint32_t *edges_dev, uint64_t n_edges, uint32_t *L_out_dev,
                  cc_stream_t stream);
 

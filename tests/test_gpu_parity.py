@@ -719,3 +719,34 @@ def test_sampled_leader_is_not_the_exact_m(flt):
                 assert g.root_vertex() == m_want
                 assert g.num_components() == oracle.num_components(want)
                 np.testing.assert_array_equal(h_L.numpy().view(np.uint32), want_l)
+
+
+@pytest.mark.parametrize("mode", [cc.CC_ROOT_MAXDEG, cc.CC_ROOT_IDENTITY])
+def test_cc_run_replays_from_a_cuda_graph(mode):
+    """cc_run captured once into a CUDA graph and replayed: each replay reads
+    the edge buffer as it is at replay time, and its labels, count and m equal
+    the oracle's on that content (three different graphs of the same size)."""
+    n, E = 1 << 14, 1 << 18
+    graphs = [graphgen.rmat(14, E, 900 + k, scramble=True) for k in range(2)] + [graphgen.er(n, E, 903)]
+    e_dev = torch.empty((E, 2), dtype=torch.int32, device="cuda")
+    L = torch.empty(n, dtype=torch.int32, device="cuda")
+    e_dev.copy_(torch.from_numpy(graphs[0].view(np.int32)))
+    s = torch.cuda.Stream()
+    with cc.Graph(n, mode=mode) as g:
+        with torch.cuda.stream(s):
+            g.run(e_dev, L, s)       # first use allocates the handle's scratch outside the capture
+            s.synchronize()
+            gr = torch.cuda.CUDAGraph()
+            gr.capture_begin()
+            g.run(e_dev, L, s)
+            gr.capture_end()
+        for e in graphs:
+            e_dev.copy_(torch.from_numpy(e.view(np.int32)))
+            torch.cuda.synchronize()
+            gr.replay()
+            torch.cuda.synchronize()
+            want = oracle.min_labels(n, e)
+            np.testing.assert_array_equal(L.cpu().numpy().view(np.uint32), want)
+            assert g.num_components() == oracle.num_components(want)
+            if mode == cc.CC_ROOT_MAXDEG:
+                assert g.root_vertex() == oracle.max_degree_vertex(n, e)
