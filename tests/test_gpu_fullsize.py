@@ -151,3 +151,47 @@ def test_fullsize_csr_rmat24_equals_coo_labels():
         lens = (off[1:] - off[:-1])
         assert g.root_vertex() == int(torch.argmax(lens).item())  # first index of the maximum
 
+
+
+def test_fullsize_serving_rmat26_against_oracle_values():
+    """The serving configuration at full size: resident R-MAT scale 26 (1.07G
+    edges) in the bench's server setup, then the bench's executor insert burst
+    (512 batches of 2^17 pairs, one submission call) and four side-path
+    inserts of 2^20 pairs; a snapshot must equal the oracle's labels of the
+    union, bit for bit, and queries must agree with the snapshot."""
+    path = os.path.join(GOLDEN, "serving_rmat26.json")
+    with open(path) as f:
+        gold = json.load(f)
+    w = graphgen.RMAT26
+    n = w.n_vertices
+    e = w.device_edges()
+    pool = graphgen.pairs_dev(n, gold["pool_pairs"], gold["pool_seed"])
+    torch.cuda.synchronize()
+    assert e.shape[0] == gold["n_edges"]
+    assert sha_chunked(e) == gold["edges_sha256"], "device generator drifted from the host generator"
+    assert sha_tensor(pool) == gold["pool_sha256"]
+    batches = [pool[o:o + c] for o, c in gold["inserts"]]
+    with cc.Server(24 << 30, idle_timeout_us=200000) as srv:
+        t, gid = srv.new_graph(n, e)
+        assert srv.wait(t, 120) == cc.CC_OK
+        small = [b for b in batches if b.shape[0] < (1 << 18)]
+        large = [b for b in batches if b.shape[0] >= (1 << 18)]
+        assert len(small) == 512 and len(large) == 4
+        tickets = srv.insert_many(gid, small) + [srv.insert(gid, b) for b in large]
+        for tk in tickets:
+            assert srv.wait(tk, 120) == cc.CC_OK
+        L = torch.empty(n, dtype=torch.int32, device="cuda")
+        t = srv.snapshot(gid, L)
+        assert srv.wait(t, 120) == cc.CC_OK
+        assert sha_tensor(L) == gold["labels_min_id_sha256"]
+        sample = torch.tensor(gold["sample_vertices"], dtype=torch.int64, device="cuda")
+        assert L[sample].cpu().tolist() == gold["sample_min_id_labels"]
+        q = graphgen.pairs_dev(n, 1 << 20, 78)
+        out = torch.empty(q.shape[0], dtype=torch.uint8, device="cuda")
+        t = srv.query(gid, q, out)
+        assert srv.wait(t, 120) == cc.CC_OK
+        Ll, ql = L.long(), q.long()
+        assert bool((out.bool() == (Ll[ql[:, 0]] == Ll[ql[:, 1]])).all())
+        assert srv.stats()["executor_timeouts"] == 0
+    del e, pool, batches, L
+    torch.cuda.empty_cache()
