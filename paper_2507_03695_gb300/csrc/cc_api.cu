@@ -46,6 +46,8 @@ struct cc_graph {
   cudaEvent_t pk_ev[2] = {nullptr, nullptr};  // a slot's last unpack has run
   uint32_t *push = nullptr;  // Initial Push list (push_cap entries), or null
   uint32_t push_cap = 0;
+  uint32_t *cand_list = nullptr;  // listed candidates of the root selection (cand_cap entries), f = R only
+  uint32_t cand_cap = 0;
   uint32_t *z = nullptr;   // zero-tree bitmap (one bit per name), or null
   size_t z_bytes = 0;
   bool z_forced = false;   // CC_FILTER_BITMAP: always used
@@ -197,7 +199,7 @@ cc_status root_select(cc_graph *g, const uint32_t *edges, uint64_t n_edges, cons
     return CC_OK;
   }
   CC_TRY(cc::launch_root_select_certified(edges, n_edges, span, g->cnt, wide, n, g->cert, g->ctrl, s, g->push,
-                                         g->push_cap));
+                                         g->push_cap, g->cand_list, g->cand_cap));
   return CC_OK;
 }
 
@@ -279,7 +281,8 @@ cc_status cc_create(uint64_t n_vertices, uint64_t n_edges_capacity, const cc_opt
   // host-side checks first: they need no device
   const bool rf = o.mode == CC_ROOT_MAXDEG;
   const size_t need = p_bytes(n_vertices) +
-                      (rf ? (size_t)n_vertices * 4 + sizeof(cc::CertScratch) : 0) + sizeof(Ctrl) +
+                      (rf ? (size_t)n_vertices * 4 + sizeof(cc::CertScratch) + (size_t)cc::cand_list_cap(n_vertices) * 4
+                          : 0) + sizeof(Ctrl) +
                       (size_t)n_edges_capacity * 8 + (wants_z(o, n_vertices) ? z_bytes_for(n_vertices) : 0) +
                       (wants_push(o) ? (size_t)push_cap_for(n_vertices) * 4 : 0);
   if (o.hbm_budget_bytes && need > o.hbm_budget_bytes) return CC_ERR_OOM;
@@ -310,6 +313,8 @@ cc_status cc_create(uint64_t n_vertices, uint64_t n_edges_capacity, const cc_opt
       if ((e = dev_alloc(g, &g->cnt, (size_t)n_vertices * 4)) != cudaSuccess) break;
       g->cnt_bytes = (size_t)n_vertices * 4;
       if ((e = dev_alloc(g, (void **)&g->cert, sizeof(cc::CertScratch))) != cudaSuccess) break;
+      g->cand_cap = cc::cand_list_cap(n_vertices);
+      if ((e = dev_alloc(g, (void **)&g->cand_list, (size_t)g->cand_cap * 4)) != cudaSuccess) break;
     }
     if (n_edges_capacity) {
       if ((e = dev_alloc(g, (void **)&g->staging, (size_t)n_edges_capacity * 8)) != cudaSuccess) break;
@@ -353,6 +358,7 @@ void cc_destroy(cc_graph *g) {
   dev_free(g, g->P, p_bytes(g->n));
   dev_free(g, g->cnt, g->cnt_bytes);
   dev_free(g, g->cert, sizeof(cc::CertScratch));
+  dev_free(g, g->cand_list, (size_t)g->cand_cap * 4);
   dev_free(g, g->ctrl, sizeof(Ctrl));
   dev_free(g, g->staging, (size_t)g->capacity * 8);
   dev_free(g, g->label_dev, (size_t)g->n * 4);

@@ -106,6 +106,21 @@ constexpr uint32_t kCertTop = 4;         // candidates whose degree is counted e
 // (vertex + 1); filled by the candidate scan of the root selection.
 constexpr uint32_t kHotBits = 12;
 constexpr uint32_t kHot = 1u << kHotBits;
+// Listed candidates: the sampled pass lists a vertex when its sampled count
+// reaches kListThr, so that the candidate scan reads the list instead of all
+// n counters. A vertex left off the list (its count stayed below kListThr, or
+// the list was full) is still bounded by its bucket's total in the proof, so
+// the list can only make a certificate fail, never make a wrong one.
+// The list is cut into kListSegs segments with a counter each (a block
+// appends to segment blockIdx % kListSegs), so that appends do not all
+// contend on one counter.
+constexpr uint32_t kListThr = 8;
+constexpr uint32_t kListSegs = 256;
+constexpr uint32_t kListCap = 1u << 20;
+inline uint32_t cand_list_cap(uint64_t n) {
+  const uint64_t c = n < kListCap ? n : kListCap;
+  return (uint32_t)((c + kListSegs - 1) / kListSegs * kListSegs);  // whole segments
+}
 // The sampled pass keeps 1 group of 1024 edges in cert_sample_stride(E):
 // kCertSample, or more from 2^30 edges up, so that it samples about 2^23
 // edges at most (its random atomics into the n counters cost more than the
@@ -122,6 +137,7 @@ struct CertScratch {
   unsigned long long bucket[kCertBuckets];  // endpoint occurrences of all vertices of the bucket
   unsigned long long hot[kHot];             // the hot-vertex table (see kHotBits)
   unsigned int sel_done;                    // candidate-selection blocks finished (the last one ranks)
+  unsigned int list_n[kListSegs];           // per list segment, vertices appended (may exceed its room)
   unsigned int blocks_done;                 // counting blocks finished (the last one decides)
   // Initial Push (Algorithm 4): neighbours of the sampled argmax m', appended
   // through kPushLanes counters, each owning a segment of the push buffer
@@ -162,10 +178,13 @@ cudaError_t chunked_select_end(const EdgeSpan &all, void *cnt, bool wide, uint32
 // encodes m ((deg << 32) | ~m for the init kernel).
 // push_buf (push_cap entries, a multiple of kPushLanes), when not null,
 // receives the neighbours of the sampled argmax during the counting pass, for
-// launch_initial_push after init.
+// launch_initial_push after init. list (list_cap entries), when not null,
+// receives the listed candidates (kListThr) and the candidate scan reads it
+// instead of the n counters.
 cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges, const EdgeSpan &e,
                                          void *cnt, bool wide, uint32_t n, CertScratch *cs, Ctrl *ctrl,
-                                         cudaStream_t s, uint32_t *push_buf = nullptr, uint32_t push_cap = 0);
+                                         cudaStream_t s, uint32_t *push_buf = nullptr, uint32_t push_cap = 0,
+                                         uint32_t *list = nullptr, uint32_t list_cap = 0);
 // Initial Push (Algorithm 4): right after init, when the planted m is the
 // vertex whose neighbours were gathered, every gathered neighbour x != m gets
 // P[x] = 0 (name 0 is m): x, still a root, is hooked under m.
@@ -184,10 +203,13 @@ cudaError_t launch_edge_pass_csr(bool rf, const uint64_t *off, const uint32_t *n
 // Unpacks n_edges edges of 3-byte ids (cc_pack.cu; src 16-byte aligned) into
 // uint32 pairs at dst (16-byte aligned).
 cudaError_t launch_unpack3(const uint8_t *src, uint64_t n_edges, uint32_t *dst, cudaStream_t s);
-// track: also put the largest sampled count in the high half of track->maxkey
+// track: also put the largest sampled count in the high half of track->maxkey;
+// list (list_cap entries, a multiple of kListSegs, with the segment counters
+// list_n): list the vertices whose sampled count reaches kListThr.
 cudaError_t launch_degree_sampled_u32(const uint2 *edges, uint64_t n_edges, uint64_t edge_base,
                                       uint32_t stride, uint32_t *cnt, uint32_t n, cudaStream_t s,
-                                      Ctrl *track = nullptr);
+                                      Ctrl *track = nullptr, uint32_t *list = nullptr,
+                                      unsigned int *list_n = nullptr, uint32_t list_cap = 0);
 cudaError_t launch_argmax_u32(const uint32_t *cnt, uint32_t n, Ctrl *ctrl, cudaStream_t s);
 // Z: the zero-tree bitmap (one bit per name, zeroed at every init), or null.
 // With Z and zsel null only the zero-tree instance runs; with both, the device

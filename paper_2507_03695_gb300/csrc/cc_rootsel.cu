@@ -92,10 +92,24 @@ __global__ void __launch_bounds__(256) k_degree(const uint4 *__restrict__ e4, ui
 // goes to the high half of track->maxkey (from the atomics' old values: the
 // last increment of a counter sees its final value), which spares an argmax
 // pass over the counters when only the largest count is needed.
+// With list, a vertex whose count reaches kListThr is appended to it (once:
+// the atomics' old values are distinct), to the block's segment; the segment
+// counters list_n may go beyond the segment's room (list_cap / kListSegs).
 __global__ void __launch_bounds__(256) k_degree_sampled(const uint2 *__restrict__ e, uint64_t n_edges,
                                                         uint64_t edge_base, uint32_t stride,
-                                                        uint32_t *__restrict__ cnt, uint32_t n, Ctrl *track) {
+                                                        uint32_t *__restrict__ cnt, uint32_t n, Ctrl *track,
+                                                        uint32_t *list, unsigned int *list_n, uint32_t list_cap) {
   uint32_t top = 0;
+  const uint32_t seg = blockIdx.x % kListSegs, seg_room = list_cap / kListSegs;
+  auto bump = [&](uint32_t v) {
+    if (v >= n) return;
+    const uint32_t c = atomicAdd(cnt + v, 1u) + 1u;
+    top = max(top, c);
+    if (c == kListThr) {
+      const unsigned int i = atomicAdd(list_n + seg, 1u);
+      if (i < seg_room) list[seg * seg_room + i] = v;
+    }
+  };
   const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t g_first = edge_base / 1024u;
   const uint64_t g_last = (edge_base + n_edges + 1023u) / 1024u;  // exclusive
@@ -106,7 +120,10 @@ __global__ void __launch_bounds__(256) k_degree_sampled(const uint2 *__restrict_
     const uint64_t gi = grp * 1024u + (k % 1024u);
     if (gi < edge_base || gi >= edge_base + n_edges) continue;
     const uint2 x = ld_edge(e + (gi - edge_base));
-    if (!track) {
+    if (list) {
+      bump(x.x);
+      bump(x.y);
+    } else if (!track) {
       count_edge(cnt, n, x.x, x.y);
     } else {
       if (x.x < n) top = max(top, atomicAdd(cnt + x.x, 1u) + 1u);
@@ -189,8 +206,12 @@ static_assert(kCertBuckets == 8192, "13-bit buckets");
 // than kCertCand candidates are seen: so many near-maximal vertices leave no
 // room for a proof, and the full histogram runs. The last block to finish
 // ranks the owners and keeps the kCertTop best for the counting pass.
+// kList: the vertices are those appended to the list's segments (as many as
+// each segment holds), else every vertex 0 .. n-1.
+template <bool kList>
 __global__ void __launch_bounds__(256) k_select_candidates(const uint32_t *__restrict__ cnt, uint32_t n,
-                                                           Ctrl *ctrl, CertScratch *cs) {
+                                                           Ctrl *ctrl, CertScratch *cs,
+                                                           const uint32_t *__restrict__ list, uint32_t list_cap) {
   const uint32_t cmax = (uint32_t)(*(volatile unsigned long long *)&ctrl->maxkey >> 32);
   if (cmax < 64u) return;  // uniform over the grid: no block ranks, top stays empty
   const uint32_t thr = cmax >> 5;
@@ -198,9 +219,18 @@ __global__ void __launch_bounds__(256) k_select_candidates(const uint32_t *__res
   const int lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   const uint64_t w0 = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-  for (uint64_t base = w0 * 32; base < n; base += warps * 32) {
-    const uint64_t v = base + (uint64_t)lane;
-    const uint32_t c = v < n ? cnt[v] : 0u;
+  const uint64_t count = kList ? list_cap : n;
+  const uint32_t seg_room = kList ? list_cap / kListSegs : 0u;
+  for (uint64_t base = w0 * 32; base < count; base += warps * 32) {
+    const uint64_t i = base + (uint64_t)lane;
+    bool have = i < count;
+    uint64_t v = i;
+    if (kList && have) {
+      const uint32_t seg = (uint32_t)(i / seg_room), k = (uint32_t)(i % seg_room);
+      have = k < __ldcg(&cs->list_n[seg]);
+      v = have ? list[i] : 0u;
+    }
+    const uint32_t c = have ? cnt[v] : 0u;
     if (c >= hot_thr && c != 0u)
       atomicMax(&cs->hot[hot_slot((uint32_t)v)], ((unsigned long long)c << 32) | (uint32_t)(v + 1u));
     const bool q = c >= thr && c != 0u;
@@ -497,12 +527,13 @@ cudaError_t launch_degree_u32(const EdgeSpan &e, uint32_t *cnt, uint32_t n, cuda
 }
 
 cudaError_t launch_degree_sampled_u32(const uint2 *edges, uint64_t n_edges, uint64_t edge_base,
-                                      uint32_t stride, uint32_t *cnt, uint32_t n, cudaStream_t s, Ctrl *track) {
+                                      uint32_t stride, uint32_t *cnt, uint32_t n, cudaStream_t s, Ctrl *track,
+                                      uint32_t *list, unsigned int *list_n, uint32_t list_cap) {
   if (n_edges == 0) return cudaSuccess;
   if (stride == 0) stride = 1;
   const uint64_t groups = (n_edges + 1023) / 1024 / stride + 2;
   const unsigned g = clamp_grid(groups * 1024 / 256, persistent_cap((const void *)k_degree_sampled, 256, 0));
-  k_degree_sampled<<<g, 256, 0, s>>>(edges, n_edges, edge_base, stride, cnt, n, track);
+  k_degree_sampled<<<g, 256, 0, s>>>(edges, n_edges, edge_base, stride, cnt, n, track, list, list_n, list_cap);
   note_launch();
   return cudaGetLastError();
 }
@@ -516,8 +547,10 @@ cudaError_t launch_argmax_u32(const uint32_t *cnt, uint32_t n, Ctrl *ctrl, cudaS
 
 cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges, const EdgeSpan &e,
                                          void *cnt, bool wide, uint32_t n, CertScratch *cs, Ctrl *ctrl,
-                                         cudaStream_t s, uint32_t *push_buf, uint32_t push_cap) {
+                                         cudaStream_t s, uint32_t *push_buf, uint32_t push_cap,
+                                         uint32_t *list, uint32_t list_cap) {
   cudaError_t err;
+  if (!list || list_cap < kListSegs || list_cap % kListSegs) list = nullptr;
   // 0. reset the sampled counters, the scratch and the control fields
   if ((err = cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(uint32_t), s)) != cudaSuccess) return err;
   if ((err = cudaMemsetAsync(cs, 0, sizeof(CertScratch), s)) != cudaSuccess) return err;
@@ -529,12 +562,19 @@ cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges
   // vertex holding it (the argmax pass)
   const uint32_t stride = cert_sample_stride(n_edges);
   if ((err = launch_degree_sampled_u32(reinterpret_cast<const uint2 *>(edges), n_edges, 0, stride, c32, n, s,
-                                       push_buf ? nullptr : ctrl)) != cudaSuccess)
+                                       push_buf ? nullptr : ctrl, list, cs->list_n, list_cap)) != cudaSuccess)
     return err;
   if (push_buf && (err = launch_argmax_u32(c32, n, ctrl, s)) != cudaSuccess) return err;
-  // 2. candidates: the owners of their buckets
-  const unsigned gsel = clamp_grid(((uint64_t)n + 255) / 256, persistent_cap((const void *)k_select_candidates, 256, 0));
-  k_select_candidates<<<gsel, 256, 0, s>>>(c32, n, ctrl, cs);
+  // 2. candidates: the owners of their buckets, from the list when there is one
+  if (list) {
+    const unsigned gsel = clamp_grid(((uint64_t)list_cap + 255) / 256,
+                                     persistent_cap((const void *)k_select_candidates<true>, 256, 0));
+    k_select_candidates<true><<<gsel, 256, 0, s>>>(c32, n, ctrl, cs, list, list_cap);
+  } else {
+    const unsigned gsel = clamp_grid(((uint64_t)n + 255) / 256,
+                                     persistent_cap((const void *)k_select_candidates<false>, 256, 0));
+    k_select_candidates<false><<<gsel, 256, 0, s>>>(c32, n, ctrl, cs, nullptr, 0u);
+  }
   note_launch();
   // 3. the exact pass in shared memory
   static std::atomic<unsigned long long> smem_set_certify{0};
@@ -638,8 +678,9 @@ cudaError_t chunked_select_begin(const uint32_t *chunk0, uint64_t n0, void *cnt,
       cudaSuccess)
     return err;
   if ((err = launch_argmax_u32(c32, n, ctrl, s)) != cudaSuccess) return err;
-  const unsigned gsel = clamp_grid(((uint64_t)n + 255) / 256, persistent_cap((const void *)k_select_candidates, 256, 0));
-  k_select_candidates<<<gsel, 256, 0, s>>>(c32, n, ctrl, cs);
+  const unsigned gsel = clamp_grid(((uint64_t)n + 255) / 256,
+                                   persistent_cap((const void *)k_select_candidates<false>, 256, 0));
+  k_select_candidates<false><<<gsel, 256, 0, s>>>(c32, n, ctrl, cs, nullptr, 0u);
   note_launch();
   k_spec_begin<<<1, 1, 0, s>>>(ctrl);
   note_launch();
