@@ -553,6 +553,15 @@ struct cc_server {
   Req *held = nullptr;
   unsigned long long held_pub = 0;
   uint64_t held_until = 0;
+  // apply tiles of multi-tile inserts started in this scheduler pass, written
+  // to the ring after every validate tile of the pass (flush_pending_apply)
+  struct PendingApply {
+    Req *r;
+    uint32_t graph, n_work, n_val;
+    uint64_t count, tile;
+    uint32_t *log;
+  };
+  std::vector<PendingApply> pending_apply;
   std::thread thread;
 };
 
@@ -607,9 +616,11 @@ uint64_t tile_for(const cc_server *s, uint64_t count, uint64_t at_least) {
 
 uint64_t n_tiles_of(uint64_t count, uint64_t tile) { return (count + tile - 1) / tile; }
 
+// log: the changed-root log the tiles append to (the graph's current one when null).
 void write_tiles(cc_server *s, const Req &r, uint32_t kind, uint64_t count, const uint32_t *src,
                  const GraphState &g, uint64_t tile, uint32_t n_count, uint32_t n_gate,
-                 unsigned long long &pub) {
+                 unsigned long long &pub, const uint32_t *log = nullptr) {
+  if (!log) log = g.logs[g.cur_log];
   const uint64_t nt = n_tiles_of(count, tile);
   for (uint64_t i = 0; i < nt; ++i) {
     WorkItem &w = s->hs->ring[(pub + i) % cc::srv::kRingCap];
@@ -626,7 +637,7 @@ void write_tiles(cc_server *s, const Req &r, uint32_t kind, uint64_t count, cons
     w.begin = i * tile;
     w.end = w.begin + tile < count ? w.begin + tile : count;
     w.out = (uint64_t)(uintptr_t)r.r.out_dev;
-    w.log = (uint64_t)(uintptr_t)g.logs[g.cur_log];
+    w.log = (uint64_t)(uintptr_t)log;
     w.Z = (uint64_t)(uintptr_t)g.Z;
     w.pad = 0;
   }
@@ -637,7 +648,10 @@ void write_tiles(cc_server *s, const Req &r, uint32_t kind, uint64_t count, cons
 // slot, no ring room, or the executor is being stopped). An insert of one
 // tile validates and applies itself; a longer one publishes validate tiles
 // and then apply tiles that wait on the device until the validation has
-// finished (and apply nothing if it failed).
+// finished (and apply nothing if it failed). The apply tiles are written at
+// the end of the scheduler pass, after the validate tiles of every insert
+// started in it: a burst of inserts is validated first, so that apply tiles
+// rarely find their gate closed (inserts started together commute).
 bool start_exec(cc_server *s, Req *r, GraphState &g) {
   const bool insert = r->r.kind == CC_REQ_INSERT;
   const uint64_t count = insert ? r->r.n_edges : r->r.n_pairs;
@@ -669,8 +683,12 @@ bool start_exec(cc_server *s, Req *r, GraphState &g) {
     write_tiles(s, *r, cc::srv::kItemEdges, count, r->r.edges_dev, g, tile, 1, 0, pub);
   } else {
     write_tiles(s, *r, cc::srv::kItemValidate, count, r->r.edges_dev, g, vtile, (uint32_t)n_work, 0, pub);
-    write_tiles(s, *r, cc::srv::kItemApply, count, r->r.edges_dev, g, tile, (uint32_t)n_work, (uint32_t)n_val,
-                pub);
+    if (s->hold_left)  // the fault injection holds the whole request back
+      write_tiles(s, *r, cc::srv::kItemApply, count, r->r.edges_dev, g, tile, (uint32_t)n_work, (uint32_t)n_val,
+                  pub);
+    else
+      s->pending_apply.push_back({r, r->graph, (uint32_t)n_work, (uint32_t)n_val, count, tile,
+                                  g.logs[g.cur_log]});
   }
   std::atomic_thread_fence(std::memory_order_seq_cst);
   if (s->hold_left) {
@@ -686,6 +704,20 @@ bool start_exec(cc_server *s, Req *r, GraphState &g) {
   s->in_flight_items += need;
   s->tiles_run += need;
   return true;
+}
+
+// Writes and publishes the apply tiles that start_exec deferred in this pass.
+// While the fault injection holds a request's tiles unpublished in the ring,
+// nothing may be published past them: the deferred tiles wait for a later pass.
+void flush_pending_apply(cc_server *s) {
+  if (s->pending_apply.empty() || s->held) return;
+  unsigned long long pub = s->hs->published;
+  for (const cc_server::PendingApply &a : s->pending_apply)
+    write_tiles(s, *a.r, cc::srv::kItemApply, a.count, a.r->r.edges_dev, s->graphs[a.graph], a.tile, a.n_work,
+                a.n_val, pub, a.log);
+  s->pending_apply.clear();
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  *(volatile unsigned long long *)&s->hs->published = pub;
 }
 
 // Root selection (f = R), init, hooking pass and flatten of a new graph on
@@ -1012,8 +1044,10 @@ void executor_departed(cc_server *s) {
         finish_graph_request(s->graphs[r->graph]);
       }
       // tiles held back by the fault injection are never published: the
-      // ring positions after `published` are written again by later requests
+      // ring positions after `published` are written again by later requests;
+      // apply tiles still deferred belong to requests just failed
       s->held = nullptr;
+      s->pending_apply.clear();
     }
     unsigned long long pub = s->hs->published;
     cudaMemcpyAsync(&s->ds->taken, &pub, sizeof(pub), cudaMemcpyHostToDevice, s->exec_stream);
@@ -1127,6 +1161,7 @@ bool scheduler_step(cc_server *s, std::vector<Req *> &incoming) {
   for (uint32_t gid : touched) try_start(s, gid);
   for (uint32_t gid = 0; gid < s->graphs.size(); ++gid)
     if (!s->graphs[gid].fifo.empty() && s->graphs[gid].group == kIdle) try_start(s, gid);
+  flush_pending_apply(s);
   manage_executor(s);
   return progress;
 }
