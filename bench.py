@@ -111,6 +111,18 @@ def device_csr(e, n: int):
     return off, nb
 
 
+def host_memory_available():
+    """MemAvailable of /proc/meminfo in bytes, or None where it cannot be read."""
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        return None
+    return None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -519,7 +531,14 @@ def run_ours(args):
 
     # ---------------- end to end: host buffers through cc_run_host
     e2e = None
-    if not args.no_e2e:
+    # pinned host copies of every graph's edges and labels, for each rank of this node
+    e2e_host_bytes = sum(8 * E + 4 * w.n_vertices for w, _, E in graphs)
+    local_ranks = int(os.environ.get("LOCAL_WORLD_SIZE", "1"))
+    host_avail = host_memory_available()
+    if not args.no_e2e and host_avail is not None and e2e_host_bytes * local_ranks > 0.85 * host_avail:
+        e2e = {"skipped": f"the {local_ranks} rank(s) of this node would pin {e2e_host_bytes * local_ranks / 1e9:.1f} GB "
+                          f"of host memory; {host_avail / 1e9:.1f} GB available"}
+    elif not args.no_e2e:
         host_e = [torch.empty(e.shape, dtype=torch.int32, pin_memory=True) for _, e, _ in graphs]
         for h_e, (_, e, _) in zip(host_e, graphs):
             h_e.copy_(e)
