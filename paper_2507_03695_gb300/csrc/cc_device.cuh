@@ -245,14 +245,20 @@ constexpr uint32_t kNeverDirect = 33;
 // tree of name 0 (the planted vertex m under R). Bits are only ever set, and
 // only after a walk or a parent value proved the fact, which holds for good
 // because name 0 is never hooked; a stale 0 bit only costs the parent load
-// it would have saved.
+// it would have saved. Name 0 itself (the tree's root m) never gets its bit:
+// the many hooks onto m would all send an atomic to the one word that holds
+// it. A lookup of m then loads P of m, which is 0 (the hot-vertex table
+// answers for m first where there is one).
 __device__ __forceinline__ bool zbit(const uint32_t *Z, uint32_t c) {
   uint32_t w;
   asm volatile("ld.global.u32 %0, [%1];" : "=r"(w) : "l"(Z + (c >> 5)) : "memory");
   return (w >> (c & 31u)) & 1u;
 }
 
-__device__ __forceinline__ void zset(uint32_t *Z, uint32_t c) { atomicOr(Z + (c >> 5), 1u << (c & 31u)); }
+// Sets bit c, never for name 0.
+__device__ __forceinline__ void zset(uint32_t *Z, uint32_t c) {
+  if (c != 0u) atomicOr(Z + (c >> 5), 1u << (c & 31u));
+}
 
 // Slot of vertex x in the hot-vertex table (kHot entries).
 __device__ __forceinline__ uint32_t hot_slot(uint32_t x) { return (x * 2654435761u) >> (32 - kHotBits); }

@@ -328,19 +328,30 @@ def test_inserts_overlap_a_snapshot(mode):
     script.append((0, "snapshot", None))
     graphs = {0: n}
     want = expected(script, graphs)
-    with cc.Server(4 * GB, mode=mode) as s:
-        mixed, _ = run_script(s, script, graphs, one_at_a_time=False)
-        st = s.stats()
-        assert st["failed"] == 0
-        assert st["snapshot_overlaps"] >= 1
+    # Whether an insert starts inside a snapshot's window (after its copy of
+    # P, before its labels) depends on timing: up to three mixed runs, each
+    # checked in full, and at least one overlap among them.
+    overlaps = 0
+    for attempt in range(3):
+        with cc.Server(4 * GB, mode=mode) as s:
+            mixed, _ = run_script(s, script, graphs, one_at_a_time=False)
+            st = s.stats()
+            assert st["failed"] == 0
+            overlaps += st["snapshot_overlaps"]
+        for i, (_, kind, _) in enumerate(script):
+            if kind == "query":
+                np.testing.assert_array_equal(mixed[i], want[i])
+            elif kind == "snapshot":
+                np.testing.assert_array_equal(mixed[i].view(np.uint32), want[i])
+        if overlaps:
+            break
+    assert overlaps >= 1
     with cc.Server(4 * GB, mode=mode) as s:
         alone, _ = run_script(s, script, graphs, one_at_a_time=True)
     for i, (_, kind, _) in enumerate(script):
         if kind == "query":
-            np.testing.assert_array_equal(mixed[i], want[i])
             np.testing.assert_array_equal(alone[i], want[i])
         elif kind == "snapshot":
-            np.testing.assert_array_equal(mixed[i].view(np.uint32), want[i])
             np.testing.assert_array_equal(alone[i].view(np.uint32), want[i])
 
 
