@@ -339,9 +339,11 @@ struct WarpRing {
     if (!run) return;
     UniteResult res{false, kNoHook};
     if (mine) res = unite<kCG>(S, a, pa, b, pb);
+    // an endpoint whose parent value was 0 is known to be in the tree of
+    // name 0 already (its bit set, or P = 0): no atomic for it
     if (res.zero && Z) {
-      zset(Z, a);
-      zset(Z, b);
+      if (pa) zset(Z, a);
+      if (pb) zset(Z, b);
     }
     if (log) log_hooks_warp(log, res.hooked, lane, lt_mask);
   }
@@ -352,11 +354,11 @@ struct WarpRing {
     uint32_t hooked = kNoHook;
     if (lane < tail - head) {
       const uint32_t slot = (head + lane) & (kRing - 1);
-      const uint32_t a = cu[slot], b = cv[slot];
-      const UniteResult res = unite<kCG>(S, a, pu[slot], b, pv[slot]);
+      const uint32_t a = cu[slot], b = cv[slot], pa = pu[slot], pb = pv[slot];
+      const UniteResult res = unite<kCG>(S, a, pa, b, pb);
       if (res.zero && Z) {
-        zset(Z, a);
-        zset(Z, b);
+        if (pa) zset(Z, a);
+        if (pb) zset(Z, b);
       }
       hooked = res.hooked;
     }

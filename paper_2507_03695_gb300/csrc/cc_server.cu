@@ -255,6 +255,10 @@ __global__ void __launch_bounds__(256) k_executor(HostShared *hs, DevShared *ds,
             const bool za = Zb && zbit_cg(Zb, na), zb = Zb && zbit_cg(Zb, nb);
             pa[j] = za ? 0u : ldP_cg(P + a[j]);
             pb[j] = zb ? 0u : ldP_cg(P + b[j]);
+            // a parent value 0 proves membership in the tree of name 0: keep
+            // the bit (the warp ring sets none for an endpoint whose parent is 0)
+            if (Zb && !za && pa[j] == 0u) zset(Zb, na);
+            if (Zb && !zb && pb[j] == 0u) zset(Zb, nb);
             a[j] = na;
             b[j] = nb;
           }
