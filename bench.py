@@ -111,6 +111,15 @@ def device_csr(e, n: int):
     return off, nb
 
 
+def guarded(leg):
+    """Runs one secondary leg of the benchmark; an exception is reported in the
+    JSON line instead of ending the run (the headline is measured first)."""
+    try:
+        return leg()
+    except Exception as exc:  # noqa: BLE001 - reported, not hidden
+        return {"error": f"{type(exc).__name__}: {exc}"}
+
+
 def host_memory_available():
     """MemAvailable of /proc/meminfo in bytes, or None where it cannot be read."""
     try:
@@ -715,24 +724,27 @@ def run_ours(args):
                  "request_roofline": request_roofline(cc, x_graphs, x_phase, probe_cache)}
         del x_labels
         if not args.no_csr:
-            csr = bench_csr(args, cc, x_graphs, torch, stream)
+            csr = guarded(lambda: bench_csr(args, cc, x_graphs, torch, stream))
         del x_graphs
         torch.cuda.empty_cache()
-        # secondary row: R-MAT 24 without the id scramble (hubs at low ids)
-        u = graphgen.WORKLOADS["rmat24_ef16_u"]
-        u_graphs = [(u, u.device_edges(), u.n_edges)]
-        torch.cuda.synchronize()
-        u_ms, u_phase, _, _, u_labels = measure_single(cc, torch, u_graphs, stream, args.steps, args.warmup)
-        unscrambled = {"workload": "rmat24u", "graphs": [u.name], "n_vertices": [u.n_vertices],
-                       "n_edges": [u.n_edges], "gteps": u.n_edges * args.steps / (u_ms * 1e-3) / 1e9,
-                       "ms_per_step": u_ms / args.steps, "steps": args.steps,
-                       "phases_ms": phases_dict([u.name], u_phase),
-                       "roofline": edge_pass_roofline(u_graphs, u_phase, "rmat24u", [u.name], peak, peak_kind),
-                       "request_roofline": request_roofline(cc, u_graphs, u_phase, probe_cache)}
-        del u_graphs, u_labels
+
+        def unscrambled_leg():
+            # secondary row: R-MAT 24 without the id scramble (hubs at low ids)
+            u = graphgen.WORKLOADS["rmat24_ef16_u"]
+            u_graphs = [(u, u.device_edges(), u.n_edges)]
+            torch.cuda.synchronize()
+            u_ms, u_phase, _, _, _ = measure_single(cc, torch, u_graphs, stream, args.steps, args.warmup)
+            return {"workload": "rmat24u", "graphs": [u.name], "n_vertices": [u.n_vertices],
+                    "n_edges": [u.n_edges], "gteps": u.n_edges * args.steps / (u_ms * 1e-3) / 1e9,
+                    "ms_per_step": u_ms / args.steps, "steps": args.steps,
+                    "phases_ms": phases_dict([u.name], u_phase),
+                    "roofline": edge_pass_roofline(u_graphs, u_phase, "rmat24u", [u.name], peak, peak_kind),
+                    "request_roofline": request_roofline(cc, u_graphs, u_phase, probe_cache)}
+
+        unscrambled = guarded(unscrambled_leg)
         torch.cuda.empty_cache()
-        c1 = bench_c1(cc, graphgen, torch)
-    batched = None if args.no_batched else bench_batched(args, cc, graphgen, torch, stream)
+        c1 = guarded(lambda: bench_c1(cc, graphgen, torch))
+    batched = None if args.no_batched else guarded(lambda: bench_batched(args, cc, graphgen, torch, stream))
     serving = None
     if not args.no_serving:
         try:

@@ -66,3 +66,12 @@ def test_profiled_traffic_follows_the_kernel_source():
 def test_host_memory_available():
     m = bench.host_memory_available()
     assert m is None or m > 0
+
+
+def test_guarded_reports_a_failing_leg():
+    assert bench.guarded(lambda: {"ok": 1}) == {"ok": 1}
+
+    def bad():
+        raise ValueError("leg failed")
+    out = bench.guarded(bad)
+    assert out == {"error": "ValueError: leg failed"}
