@@ -558,133 +558,136 @@ def run_ours(args):
         e2e = {"skipped": f"the {local_ranks} rank(s) of this node would pin {e2e_host_bytes * local_ranks / 1e9:.1f} GB "
                           f"of host memory; {host_avail / 1e9:.1f} GB available"}
     elif not args.no_e2e:
-        host_e = [torch.empty(e.shape, dtype=torch.int32, pin_memory=True) for _, e, _ in graphs]
-        for h_e, (_, e, _) in zip(host_e, graphs):
-            h_e.copy_(e)
-        host_L = [torch.empty(w.n_vertices, dtype=torch.int32, pin_memory=True) for w, _, _ in graphs]
-        # Two sets of handles, streams and label buffers; step i uses set i % 2,
-        # so that one step's label read-back overlaps the next step's upload
-        # (the host link carries both directions at once). Within a set, one
-        # stream per graph. cc_sync waits for a set before it is used again,
-        # and reports errors.
-        e2e_sets = []
-        for k in range(2):
-            hs = [cc.Graph(w.n_vertices, E, **BENCH_OPTIONS) for w, _, E in graphs]
-            sts = [torch.cuda.Stream() for _ in graphs]
-            hls = host_L if k == 0 else [torch.empty(w.n_vertices, dtype=torch.int32, pin_memory=True)
-                                         for w, _, _ in graphs]
-            e2e_sets.append((hs, sts, hls))
+        try:
+            host_e = [torch.empty(e.shape, dtype=torch.int32, pin_memory=True) for _, e, _ in graphs]
+            for h_e, (_, e, _) in zip(host_e, graphs):
+                h_e.copy_(e)
+            host_L = [torch.empty(w.n_vertices, dtype=torch.int32, pin_memory=True) for w, _, _ in graphs]
+            # Two sets of handles, streams and label buffers; step i uses set i % 2,
+            # so that one step's label read-back overlaps the next step's upload
+            # (the host link carries both directions at once). Within a set, one
+            # stream per graph. cc_sync waits for a set before it is used again,
+            # and reports errors.
+            e2e_sets = []
+            for k in range(2):
+                hs = [cc.Graph(w.n_vertices, E, **BENCH_OPTIONS) for w, _, E in graphs]
+                sts = [torch.cuda.Stream() for _ in graphs]
+                hls = host_L if k == 0 else [torch.empty(w.n_vertices, dtype=torch.int32, pin_memory=True)
+                                             for w, _, _ in graphs]
+                e2e_sets.append((hs, sts, hls))
 
-        def e2e_steps(count):
-            pending = []
-            for i in range(count):
-                k = i % 2
-                if len(pending) == 2:
-                    for h in e2e_sets[pending.pop(0)][0]:
+            def e2e_steps(count):
+                pending = []
+                for i in range(count):
+                    k = i % 2
+                    if len(pending) == 2:
+                        for h in e2e_sets[pending.pop(0)][0]:
+                            cc.cc_sync(h.h)
+                    hs, sts, hls = e2e_sets[k]
+                    for h, h_e, h_l, st, (_, _, E) in zip(hs, host_e, hls, sts, graphs):
+                        cc.cc_run_host_async(h.h, h_e, E, h_l, st)
+                    pending.append(k)
+                for k in pending:
+                    for h in e2e_sets[k][0]:
                         cc.cc_sync(h.h)
-                hs, sts, hls = e2e_sets[k]
-                for h, h_e, h_l, st, (_, _, E) in zip(hs, host_e, hls, sts, graphs):
-                    cc.cc_run_host_async(h.h, h_e, E, h_l, st)
-                pending.append(k)
-            for k in pending:
-                for h in e2e_sets[k][0]:
-                    cc.cc_sync(h.h)
 
-        def link_rates():
-            """Plain copies of the same bytes over the host link, timed with CUDA
-            events: the pinned edges into the device edge arrays (same values)
-            and the device labels into the pinned label buffers."""
-            st = torch.cuda.Stream()
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            torch.cuda.synchronize()
-            with torch.cuda.stream(st):
-                ev[0].record(st)
-                for h_e, (_, e, _) in zip(host_e, graphs):
-                    e.copy_(h_e, non_blocking=True)
-                ev[1].record(st)
-                for h_l, L in zip(host_L, labels):
-                    h_l.copy_(L, non_blocking=True)
-                ev[2].record(st)
-            st.synchronize()
-            h2d = sum(8 * E for _, _, E in graphs) / (ev[0].elapsed_time(ev[1]) * 1e-3) / 1e9
-            d2h = sum(4 * w.n_vertices for w, _, _ in graphs) / (ev[1].elapsed_time(ev[2]) * 1e-3) / 1e9
-            return h2d, d2h
+            def link_rates():
+                """Plain copies of the same bytes over the host link, timed with CUDA
+                events: the pinned edges into the device edge arrays (same values)
+                and the device labels into the pinned label buffers."""
+                st = torch.cuda.Stream()
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                torch.cuda.synchronize()
+                with torch.cuda.stream(st):
+                    ev[0].record(st)
+                    for h_e, (_, e, _) in zip(host_e, graphs):
+                        e.copy_(h_e, non_blocking=True)
+                    ev[1].record(st)
+                    for h_l, L in zip(host_L, labels):
+                        h_l.copy_(L, non_blocking=True)
+                    ev[2].record(st)
+                st.synchronize()
+                h2d = sum(8 * E for _, _, E in graphs) / (ev[0].elapsed_time(ev[1]) * 1e-3) / 1e9
+                d2h = sum(4 * w.n_vertices for w, _, _ in graphs) / (ev[1].elapsed_time(ev[2]) * 1e-3) / 1e9
+                return h2d, d2h
 
-        e2e_steps(max(2, min(args.warmup, 3)))  # both sets warmed up
-        link_before = link_rates()
-        barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        k_e2e = max(1, min(args.steps, 10))
-        e2e_steps(k_e2e)
-        torch.cuda.synchronize()
-        t_e2e = max_over_ranks(time.perf_counter() - t0)
-        barrier()
-        # the host labels of both sets must equal the device-resident run's labels
-        for _, _, hls in e2e_sets:
-            for h_l, L in zip(hls, labels):
-                if not torch.equal(h_l, L.cpu()):
-                    raise RuntimeError("cc_run_host labels differ from cc_run labels")
-        link_after = link_rates()  # overwrites host_L with the same labels
-        e2e = {"value": world * E_total * k_e2e / t_e2e / 1e9, "unit": "GTEPS",
-               "h2d_bytes_per_step": int(sum(8 * E for _, _, E in graphs)),
-               "d2h_bytes_per_step": int(sum(4 * w.n_vertices for w, _, _ in graphs)),
-               "steps": k_e2e,
-               "api": "cc_run_host_async per graph (pinned host buffers); steps alternate between two sets of "
-                      "handles, so that one step's label read-back overlaps the next step's upload; cc_sync "
-                      "before a set is reused"}
-        h2d_gbs = (link_before[0] + link_after[0]) / 2
-        d2h_gbs = (link_before[1] + link_after[1]) / 2
-        t_h2d = e2e["h2d_bytes_per_step"] / (h2d_gbs * 1e9)
-        t_link = t_h2d + e2e["d2h_bytes_per_step"] / (d2h_gbs * 1e9)
-        ceiling = E_total / max(t_h2d, e2e["d2h_bytes_per_step"] / (d2h_gbs * 1e9)) / 1e9  # directions overlap
-        e2e["host_link"] = {
-            "h2d_gbs": h2d_gbs, "d2h_gbs": d2h_gbs,
-            "h2d_gbs_before_after": [link_before[0], link_after[0]],
-            "d2h_gbs_before_after": [link_before[1], link_after[1]],
-            "ceiling_gteps": ceiling, "frac_of_ceiling": e2e["value"] / world / ceiling,
-            "ceiling_gteps_serial": E_total / t_link / 1e9,
-            "note": "plain copies of the step's bytes (edges in, labels out) timed just before and after the "
-                    "e2e loop; the ceiling is the step's bytes over those rates with no compute, the two "
-                    "directions overlapped (serial: one after the other)"}
-        # the same through the compact encoding: 3-byte ids where they suffice
-        idb = [3 if w.n_vertices <= (1 << 24) else 4 for w, _, _ in graphs]
-        if any(b == 3 for b in idb):
-            host_pk = [torch.from_numpy(graphgen.pack_ids(h_e.numpy().view(np.uint32), b)).pin_memory()
-                       for h_e, b in zip(host_e, idb)]
-
-            pk_handles, pk_streams, _ = e2e_sets[0]  # one set: the packed leg keeps per-step waits
-
-            def e2e_packed_step():
-                for h, pk, b, h_l, st, (_, _, E) in zip(pk_handles, host_pk, idb, host_L, pk_streams, graphs):
-                    cc.cc_run_host_packed_async(h.h, pk, E, b, h_l, st)
-                for h in pk_handles:
-                    cc.cc_sync(h.h)
-
-            for _ in range(max(1, min(args.warmup, 3))):
-                e2e_packed_step()
+            e2e_steps(max(2, min(args.warmup, 3)))  # both sets warmed up
+            link_before = link_rates()
             barrier()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            for _ in range(k_e2e):
-                e2e_packed_step()
+            k_e2e = max(1, min(args.steps, 10))
+            e2e_steps(k_e2e)
             torch.cuda.synchronize()
-            t_pk = max_over_ranks(time.perf_counter() - t0)
+            t_e2e = max_over_ranks(time.perf_counter() - t0)
             barrier()
-            for h_l, L in zip(host_L, labels):
-                if not torch.equal(h_l, L.cpu()):
-                    raise RuntimeError("cc_run_host_packed labels differ from cc_run labels")
-            e2e["packed"] = {"value": world * E_total * k_e2e / t_pk / 1e9, "unit": "GTEPS",
-                             "h2d_bytes_per_step": int(sum(2 * b * E for b, (_, _, E) in zip(idb, graphs))),
-                             "id_bytes": idb,
-                             "api": "cc_run_host_packed_async per graph, one stream each (compact ids, Section V)"}
-            del host_pk
-        else:
-            e2e["packed"] = {"skipped": "every graph needs 4-byte ids (more than 2^24 vertices)"}
-        for hs, _, _ in e2e_sets:
-            for h in hs:
-                h.close()
-        del host_e, host_L, e2e_sets
+            # the host labels of both sets must equal the device-resident run's labels
+            for _, _, hls in e2e_sets:
+                for h_l, L in zip(hls, labels):
+                    if not torch.equal(h_l, L.cpu()):
+                        raise RuntimeError("cc_run_host labels differ from cc_run labels")
+            link_after = link_rates()  # overwrites host_L with the same labels
+            e2e = {"value": world * E_total * k_e2e / t_e2e / 1e9, "unit": "GTEPS",
+                   "h2d_bytes_per_step": int(sum(8 * E for _, _, E in graphs)),
+                   "d2h_bytes_per_step": int(sum(4 * w.n_vertices for w, _, _ in graphs)),
+                   "steps": k_e2e,
+                   "api": "cc_run_host_async per graph (pinned host buffers); steps alternate between two sets of "
+                          "handles, so that one step's label read-back overlaps the next step's upload; cc_sync "
+                          "before a set is reused"}
+            h2d_gbs = (link_before[0] + link_after[0]) / 2
+            d2h_gbs = (link_before[1] + link_after[1]) / 2
+            t_h2d = e2e["h2d_bytes_per_step"] / (h2d_gbs * 1e9)
+            t_link = t_h2d + e2e["d2h_bytes_per_step"] / (d2h_gbs * 1e9)
+            ceiling = E_total / max(t_h2d, e2e["d2h_bytes_per_step"] / (d2h_gbs * 1e9)) / 1e9  # directions overlap
+            e2e["host_link"] = {
+                "h2d_gbs": h2d_gbs, "d2h_gbs": d2h_gbs,
+                "h2d_gbs_before_after": [link_before[0], link_after[0]],
+                "d2h_gbs_before_after": [link_before[1], link_after[1]],
+                "ceiling_gteps": ceiling, "frac_of_ceiling": e2e["value"] / world / ceiling,
+                "ceiling_gteps_serial": E_total / t_link / 1e9,
+                "note": "plain copies of the step's bytes (edges in, labels out) timed just before and after the "
+                        "e2e loop; the ceiling is the step's bytes over those rates with no compute, the two "
+                        "directions overlapped (serial: one after the other)"}
+            # the same through the compact encoding: 3-byte ids where they suffice
+            idb = [3 if w.n_vertices <= (1 << 24) else 4 for w, _, _ in graphs]
+            if any(b == 3 for b in idb):
+                host_pk = [torch.from_numpy(graphgen.pack_ids(h_e.numpy().view(np.uint32), b)).pin_memory()
+                           for h_e, b in zip(host_e, idb)]
+
+                pk_handles, pk_streams, _ = e2e_sets[0]  # one set: the packed leg keeps per-step waits
+
+                def e2e_packed_step():
+                    for h, pk, b, h_l, st, (_, _, E) in zip(pk_handles, host_pk, idb, host_L, pk_streams, graphs):
+                        cc.cc_run_host_packed_async(h.h, pk, E, b, h_l, st)
+                    for h in pk_handles:
+                        cc.cc_sync(h.h)
+
+                for _ in range(max(1, min(args.warmup, 3))):
+                    e2e_packed_step()
+                barrier()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(k_e2e):
+                    e2e_packed_step()
+                torch.cuda.synchronize()
+                t_pk = max_over_ranks(time.perf_counter() - t0)
+                barrier()
+                for h_l, L in zip(host_L, labels):
+                    if not torch.equal(h_l, L.cpu()):
+                        raise RuntimeError("cc_run_host_packed labels differ from cc_run labels")
+                e2e["packed"] = {"value": world * E_total * k_e2e / t_pk / 1e9, "unit": "GTEPS",
+                                 "h2d_bytes_per_step": int(sum(2 * b * E for b, (_, _, E) in zip(idb, graphs))),
+                                 "id_bytes": idb,
+                                 "api": "cc_run_host_packed_async per graph, one stream each (compact ids, Section V)"}
+                del host_pk
+            else:
+                e2e["packed"] = {"skipped": "every graph needs 4-byte ids (more than 2^24 vertices)"}
+            for hs, _, _ in e2e_sets:
+                for h in hs:
+                    h.close()
+            del host_e, host_L, e2e_sets
+        except Exception as exc:  # noqa: BLE001 - reported in the line, the headline stands
+            e2e = {"error": f"{type(exc).__name__}: {exc}"}
 
     # ---------------- CPU baseline: the oracle on a bounded sample (rank 0, N=1)
     cpu = None
