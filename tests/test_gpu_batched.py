@@ -99,7 +99,7 @@ def test_tune_then_run(small_batch):
         # the candidate table: every block size x edges per thread x filter x
         # tile size, the kept one being the fastest
         table = cc.cc_batch_tune_results(bt.h)
-        assert len(table) == 2 * 3 * 2 * 3
+        assert len(table) == 2 * 3 * 2 * 4
         assert min(t for _, t in table) == ms
         assert [c for c, t in table if t == ms][0] == best
         L.fill_(-1)
