@@ -143,13 +143,16 @@ def measured_peaks():
 
 
 def kernel_source_sha() -> str:
-    """Hash of the edge-pass kernel's device code: csrc/cc_device.cuh and the
-    text of the k_edge_pass_filtered definition in csrc/cc_kernels.cu (host
-    launch code elsewhere in that file does not change the kernel's traffic)."""
+    """Hash of the code that sets the edge pass's traffic: csrc/cc_device.cuh,
+    the root selection (csrc/cc_rootsel.cu and csrc/cc_internal.h: its sample
+    fills the hot-vertex table the pass reads), and the text of the
+    k_edge_pass_filtered definition and of grab_for in csrc/cc_kernels.cu
+    (other host launch code in that file does not change the traffic)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2507_03695_gb300", "csrc")
-    with open(os.path.join(csrc, "cc_device.cuh"), "rb") as f:
-        h.update(f.read())
+    for name in ("cc_device.cuh", "cc_rootsel.cu", "cc_internal.h"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
     with open(os.path.join(csrc, "cc_kernels.cu")) as f:
         text = f.read()
     start = text.index("k_edge_pass_filtered(const uint4")  # the definition, not a launch
@@ -443,7 +446,8 @@ def request_roofline(cc, graphs, phase_ms, cache) -> dict:
     return {"bound": "l2_random_requests", "achieved": lookups / t / 1e9, "peak": peak, "unit": "G lookups/s",
             "frac": lookups / t / 1e9 / peak, "by_graph": by_graph,
             "algorithmic_requests": "2 endpoint lookups per edge (random 4-byte reads, one L2 request each); "
-                                    "R-MAT graphs only",
+                                    "R-MAT graphs only. The edge pass answers some lookups from its "
+                                    "shared-memory table of hot vertices, so frac can exceed 1",
             "peak_source": "measured in this run: cc_measure_random_loads on an array of the lookup array's "
                            "size rounded up to a power of two (best of 4 launch shapes)"}
 

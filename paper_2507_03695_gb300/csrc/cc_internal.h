@@ -102,7 +102,7 @@ constexpr uint32_t kCertBuckets = 8192;  // hash buckets of the degree bound
 constexpr uint32_t kCertTop = 4;         // candidates whose degree is counted exactly
 // The hot-vertex table of the edge pass: per slot (a multiplicative hash of
 // the vertex id, kHotBits bits) the vertex with the largest sampled count
-// among those with at least 1/64 of the largest, packed (count << 32) |
+// among those with at least 1/256 of the largest, packed (count << 32) |
 // (vertex + 1); filled by the candidate scan of the root selection.
 constexpr uint32_t kHotBits = 12;
 constexpr uint32_t kHot = 1u << kHotBits;
@@ -122,12 +122,16 @@ inline uint32_t cand_list_cap(uint64_t n) {
   return (uint32_t)((c + kListSegs - 1) / kListSegs * kListSegs);  // whole segments
 }
 // The sampled pass keeps 1 group of 1024 edges in cert_sample_stride(E):
-// kCertSample, or more from 2^30 edges up, so that it samples about 2^23
-// edges at most (its random atomics into the n counters cost more than the
-// candidates they find need: R-MAT scale 28 root select 7.6 -> 6.1 ms).
+// kCertSample, or E / 2^19 from 2^26 edges up (about 2^19 sampled edges), at
+// most 4096 (2^20 sampled edges on R-MAT scale 28). Its random atomics into
+// the n counters cost more than the candidates they find need (R-MAT scale
+// 28 root select: 1 in 128 7.6 ms, E / 2^23 6.0 ms, this 5.6 ms). A thinner
+// sample lists fewer hubs for the hot-vertex table, and the edge pass loses
+// more than the root selection gains (R-MAT scale 28 at E / 2^18 with a cap
+// of 16384: root select -0.1 ms, edge pass +0.5 ms).
 constexpr uint32_t kCertSample = 128;
 inline uint32_t cert_sample_stride(uint64_t n_edges) {
-  const uint64_t s = n_edges >> 23;
+  const uint64_t s = n_edges >> 19;
   return s > kCertSample ? (uint32_t)(s < 4096 ? s : 4096) : kCertSample;
 }
 struct CertScratch {

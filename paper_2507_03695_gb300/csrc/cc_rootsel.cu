@@ -6,8 +6,8 @@
 // A global histogram needs one random atomic per endpoint, which on R-MAT
 // graphs is slower than the edge pass itself. The default exact selection is
 // therefore certified instead:
-//   1. a histogram over 1 group of 1024 edges in 128 (more above 2^30 edges:
-//      cert_sample_stride; global atomics) gives
+//   1. a histogram over 1 group of 1024 edges in 128 (more from 2^26 edges
+//      up: cert_sample_stride; global atomics) gives
 //      candidate hubs: every vertex with at least 1/32 of the largest sampled
 //      count (at most kCertCand of them); the best per hash bucket of vertex
 //      ids competes, and the kCertTop best of those are kept;
@@ -215,7 +215,11 @@ __global__ void __launch_bounds__(256) k_select_candidates(const uint32_t *__res
   const uint32_t cmax = (uint32_t)(*(volatile unsigned long long *)&ctrl->maxkey >> 32);
   if (cmax < 64u) return;  // uniform over the grid: no block ranks, top stays empty
   const uint32_t thr = cmax >> 5;
-  const uint32_t hot_thr = cmax >> 6;  // the hot-vertex table takes vertices from 1/64 of the largest count
+  // The hot-vertex table takes vertices from 1/256 of the largest count. On
+  // R-MAT the list's own threshold (kListThr) is then the tighter one, so
+  // every listed vertex competes for its slot (R-MAT scale 24 edge pass: 1/64
+  // 1.75 ms, 1/128 to 1/2048 1.70 ms).
+  const uint32_t hot_thr = cmax >> 8;
   const int lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   const uint64_t w0 = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);

@@ -595,8 +595,9 @@ def test_phase_times_and_budget():
 
 def _hidden_hub_graph(extra: int):
     """Visible hub A = 500 in every 5th edge; hidden hub B = 100 only in edge
-    groups the root-selection sample skips (groups of 1024, one in 32 sampled),
-    with deg(B) = deg(A) + extra. Other endpoints avoid both hubs."""
+    groups the root-selection sample skips (groups of 1024; B avoids every
+    32nd group, which covers the one in 128 that a graph of this size
+    samples), with deg(B) = deg(A) + extra. Other endpoints avoid both hubs."""
     n, E = 1 << 16, 1024 * 32 * 8
     rng = np.random.default_rng(11)
     e = rng.integers(1000, n, size=(E, 2)).astype(np.uint32)
