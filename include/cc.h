@@ -77,7 +77,7 @@ typedef enum cc_root_mode {
  * self-loop counts twice, duplicates count); ties go to the smaller id. */
 typedef enum cc_root_select {
   CC_ROOT_SELECT_EXACT = 0,  /* degree histogram over all edges                     */
-  CC_ROOT_SELECT_SAMPLED = 1 /* histogram over every k-th group of 1024 edges       */
+  CC_ROOT_SELECT_SAMPLED = 1 /* histogram over every k-th group of 4 edges          */
 } cc_root_select;
 
 /* Warp-level pre-filter of the edge pass: an edge whose endpoints already

@@ -6,8 +6,8 @@
 // A global histogram needs one random atomic per endpoint, which on R-MAT
 // graphs is slower than the edge pass itself. The default exact selection is
 // therefore certified instead:
-//   1. a histogram over 1 group of 1024 edges in 128 (more from 2^26 edges
-//      up: cert_sample_stride; global atomics) gives
+//   1. a histogram over 1 group of kSampleGroup edges in 128 (more from 2^26
+//      edges up: cert_sample_stride; global atomics) gives
 //      candidate hubs: every vertex with at least 1/32 of the largest sampled
 //      count (at most kCertCand of them); the best per hash bucket of vertex
 //      ids competes, and the kCertTop best of those are kept;
@@ -51,10 +51,11 @@ __global__ void __launch_bounds__(256) k_zero_cnt(C *cnt, uint32_t n, const uint
     cnt[v] = (C)0;
 }
 
-// Edge idx lies in a sampled group of k_degree_sampled (1 group of 1024 in
-// stride, counted from the start of the edge array); stride 0: never.
+// Edge idx lies in a sampled group of k_degree_sampled (1 group of
+// kSampleGroup in stride, counted from the start of the edge array); stride
+// 0: never.
 __device__ __forceinline__ bool in_sample(uint64_t idx, uint32_t stride) {
-  return stride != 0u && ((idx >> 10) % stride) == 0u;
+  return stride != 0u && ((idx >> kSampleGroupShift) % stride) == 0u;
 }
 
 // Degree histogram. With stride nonzero, the edges of the sampled groups are
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(256) k_degree(const uint4 *__restrict__ e4, ui
 }
 
 // Sampled histogram: edge i (global index edge_base + i) is counted iff
-// ((edge_base + i) / 1024) % stride == 0. With track, the largest count also
+// ((edge_base + i) / kSampleGroup) % stride == 0. With track, the largest count also
 // goes to the high half of track->maxkey (from the atomics' old values: the
 // last increment of a counter sees its final value), which spares an argmax
 // pass over the counters when only the largest count is needed.
@@ -111,13 +112,13 @@ __global__ void __launch_bounds__(256) k_degree_sampled(const uint2 *__restrict_
     }
   };
   const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
-  const uint64_t g_first = edge_base / 1024u;
-  const uint64_t g_last = (edge_base + n_edges + 1023u) / 1024u;  // exclusive
+  const uint64_t g_first = edge_base >> kSampleGroupShift;
+  const uint64_t g_last = (edge_base + n_edges + kSampleGroup - 1u) >> kSampleGroupShift;  // exclusive
   const uint64_t g0 = (g_first + stride - 1) / stride * stride;    // first sampled group
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;; k += T) {
-    const uint64_t grp = g0 + (k / 1024u) * stride;
+    const uint64_t grp = g0 + (k >> kSampleGroupShift) * stride;
     if (grp >= g_last) break;
-    const uint64_t gi = grp * 1024u + (k % 1024u);
+    const uint64_t gi = (grp << kSampleGroupShift) + (k & (kSampleGroup - 1u));
     if (gi < edge_base || gi >= edge_base + n_edges) continue;
     const uint2 x = ld_edge(e + (gi - edge_base));
     if (list) {
@@ -535,8 +536,8 @@ cudaError_t launch_degree_sampled_u32(const uint2 *edges, uint64_t n_edges, uint
                                       uint32_t *list, unsigned int *list_n, uint32_t list_cap) {
   if (n_edges == 0) return cudaSuccess;
   if (stride == 0) stride = 1;
-  const uint64_t groups = (n_edges + 1023) / 1024 / stride + 2;
-  const unsigned g = clamp_grid(groups * 1024 / 256, persistent_cap((const void *)k_degree_sampled, 256, 0));
+  const uint64_t groups = ((n_edges + kSampleGroup - 1) >> kSampleGroupShift) / stride + 2;
+  const unsigned g = clamp_grid(groups * kSampleGroup / 256, persistent_cap((const void *)k_degree_sampled, 256, 0));
   k_degree_sampled<<<g, 256, 0, s>>>(edges, n_edges, edge_base, stride, cnt, n, track, list, list_n, list_cap);
   note_launch();
   return cudaGetLastError();
@@ -621,7 +622,7 @@ cudaError_t launch_root_select_certified(const uint32_t *edges, uint64_t n_edges
 // ------------------------------------------------- chunked root selection
 
 namespace {
-constexpr uint32_t kChunk0Sample = 16;  // the first chunk keeps 1 group of 1024 edges in 16
+constexpr uint32_t kChunk0Sample = 16;  // the first chunk keeps 1 group of kSampleGroup edges in 16
 
 cudaError_t launch_histogram(const EdgeSpan &e, void *cnt, bool wide, uint32_t n, const uint32_t *skip,
                              cudaStream_t s) {

@@ -595,16 +595,17 @@ def test_phase_times_and_budget():
 
 def _hidden_hub_graph(extra: int):
     """Visible hub A = 500 in every 5th edge; hidden hub B = 100 only in edge
-    groups the root-selection sample skips (groups of 1024; B avoids every
-    32nd group, which covers the one in 128 that a graph of this size
-    samples), with deg(B) = deg(A) + extra. Other endpoints avoid both hubs."""
+    groups the root-selection sample skips (groups of 4 edges; B avoids
+    every 16th group, which covers the one in 128 that the sample of a graph
+    of this size keeps, and the one in 16 of a first host chunk), with
+    deg(B) = deg(A) + extra. Other endpoints avoid both hubs."""
     n, E = 1 << 16, 1024 * 32 * 8
     rng = np.random.default_rng(11)
     e = rng.integers(1000, n, size=(E, 2)).astype(np.uint32)
     idx = np.arange(E)
     e[idx % 5 == 0, 0] = 500
     dA = int((idx % 5 == 0).sum())
-    hidden_slots = idx[((idx // 1024) % 32 != 0) & ((idx % 5 == 1) | (idx % 5 == 2))]
+    hidden_slots = idx[((idx // 4) % 16 != 0) & ((idx % 5 == 1) | (idx % 5 == 2))]
     e[hidden_slots[: dA + extra], 1] = 100
     deg = np.bincount(e.ravel(), minlength=n)
     assert deg[100] - deg[500] == extra
@@ -619,6 +620,24 @@ def test_root_select_hidden_hub(extra):
     got, _, m = run_labels(n, e, mode=cc.CC_ROOT_MAXDEG, label_space=cc.CC_LABEL_ROOT_VALUE)
     assert m == want_m
     np.testing.assert_array_equal(got, oracle.root_value_labels(n, e, want_m))
+
+
+@pytest.mark.parametrize("order", ["by_source", "by_source_bucket"])
+@pytest.mark.parametrize("flt", [cc.CC_FILTER_AUTO, cc.CC_FILTER_BITMAP])
+def test_edges_sorted_by_source(order, flt):
+    """Edges sorted by their first endpoint, as edge-list files often come
+    (whole rows contiguous), or grouped by its top bits: the root selection's
+    sample must still be an even spread of the array, and m and the labels
+    must match the oracle."""
+    n = 1 << 20
+    e = graphgen.rmat(20, 1 << 24, 91, scramble=True)
+    key = e[:, 0] if order == "by_source" else e[:, 0] >> 8
+    e = np.ascontiguousarray(e[np.argsort(key, kind="stable")])
+    want = oracle.min_labels(n, e)
+    got, ncomp, m = run_labels(n, e, mode=cc.CC_ROOT_MAXDEG, filter=flt)
+    assert m == oracle.max_degree_vertex(n, e)
+    assert ncomp == oracle.num_components(want)
+    np.testing.assert_array_equal(got, want)
 
 
 def _push_case(case):
