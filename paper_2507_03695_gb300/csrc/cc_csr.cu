@@ -97,15 +97,32 @@ __global__ void __launch_bounds__(256) k_csr_tile_rows(const uint64_t *__restric
   }
 }
 
+// Chunks of 32 entries a warp handles per iteration: their neighbour loads,
+// then their row searches, then all their parent loads are issued before any
+// of them is used, so that a warp keeps 2 * kCsrChunks parent loads in flight.
+// Edge pass, ms, for 1 / 2 / 4 / 8 chunks: R-MAT 24 1.40 / 1.35 / 1.40 / 1.70,
+// the 8192^2 grid 1.44 / 1.44 / 1.46 / 2.36, R-MAT 26 (P larger than L2)
+// 11.0 / 10.6 / 10.9 / 9.9. More loads in flight per warp barely help: the
+// pass is bound by its random parent requests, which the COO pass cuts with
+// the zero-tree bitmap and the hot-vertex table.
+#ifndef CC_CSR_CHUNKS
+#define CC_CSR_CHUNKS 2
+#endif
+constexpr int kCsrChunks = CC_CSR_CHUNKS;
+
 // The edge pass over CSR: warp-sized chunks of consecutive entries, the row
 // of each lane found by walking the offsets forward from the warp's current
 // row (bounded by n), the filter and the warp ring as in the COO pass. Warps
 // claim tiles one at a time from *work (the dynamic schedule of the COO pass).
+// The filter may read parent values older than the pushes of earlier chunks
+// of the same iteration: equal values still mean that the endpoints were
+// already joined, and different ones only send the edge to the union.
 template <class F>
 __global__ void __launch_bounds__(512) k_edge_pass_csr(const uint64_t *__restrict__ off,
                                                        const uint32_t *__restrict__ nb, uint64_t n_entries,
                                                        uint32_t n, uint32_t tile, const uint32_t *tile_row,
                                                        uint32_t *P, Ctrl *ctrl, unsigned long long *work) {
+  constexpr int K = kCsrChunks;
   extern __shared__ uint32_t ring_smem[];
   const F fn = F::load(ctrl);
   uint32_t *const S = slots<F>(P);
@@ -122,43 +139,60 @@ __global__ void __launch_bounds__(512) k_edge_pass_csr(const uint64_t *__restric
     if (t >= n_tiles) break;
     uint32_t r = tile_row[t];  // warp-uniform: the row of the tile's first entry
     const uint64_t end = (t + 1) * tile < n_entries ? (t + 1) * tile : n_entries;
-    for (uint64_t base = t * tile; base < end; base += 32u) {
-      const uint64_t j = base + ring.lane;
-      const bool live = j < end;
-      // The row of entry j: lane k holds the boundary off[r + 1 + k], and each
-      // lane counts, by a binary search over the 32 boundaries in registers,
-      // the rows that end at or before its entry.
-      const uint64_t bnd = r + 1u + ring.lane <= n ? off[r + 1u + ring.lane] : ~0ull;
-      uint32_t lo = 0, hi = 32;  // answer in [0, 32]: six halvings settle it
-      const uint64_t last_j = (end - base < 32u ? end : base + 32u) - 1u;
-      if (__shfl_sync(0xFFFFFFFFu, bnd, 0) <= last_j) {  // else the whole chunk lies in row r
+    for (uint64_t base = t * tile; base < end; base += 32u * K) {
+      uint32_t u[K], v[K];
+      bool live[K];
 #pragma unroll
-        for (int step = 0; step < 6; ++step) {
-          const uint32_t mid = (lo + hi) >> 1;
-          const uint64_t b = __shfl_sync(0xFFFFFFFFu, bnd, (int)(mid < 32u ? mid : 31u));
-          if (live && mid < 32u && b <= j)
-            lo = mid + 1u;
-          else
-            hi = mid;
-        }
+      for (int c = 0; c < K; ++c) {
+        const uint64_t j = base + 32u * c + ring.lane;
+        live[c] = j < end;
+        v[c] = live[c] ? ld_nc_u32(nb + j, pol) : 0u;
       }
-      uint32_t u = r + lo < n ? r + lo : n - 1u;
-      uint32_t v = 0;
-      if (live) {
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        const uint64_t cb = base + 32u * c;  // the chunk's first entry
+        u[c] = r;
+        if (cb >= end) continue;  // warp-uniform: the tile ended in an earlier chunk
+        const uint64_t j = cb + ring.lane;
+        // The row of entry j: lane k holds the boundary off[r + 1 + k], and
+        // each lane counts, by a binary search over the 32 boundaries in
+        // registers, the rows that end at or before its entry.
+        const uint64_t bnd = r + 1u + ring.lane <= n ? off[r + 1u + ring.lane] : ~0ull;
+        uint32_t lo = 0, hi = 32;  // answer in [0, 32]: six halvings settle it
+        const uint64_t last_j = (end - cb < 32u ? end : cb + 32u) - 1u;
+        if (__shfl_sync(0xFFFFFFFFu, bnd, 0) <= last_j) {  // else the whole chunk lies in row r
+#pragma unroll
+          for (int step = 0; step < 6; ++step) {
+            const uint32_t mid = (lo + hi) >> 1;
+            const uint64_t b = __shfl_sync(0xFFFFFFFFu, bnd, (int)(mid < 32u ? mid : 31u));
+            if (live[c] && mid < 32u && b <= j)
+              lo = mid + 1u;
+            else
+              hi = mid;
+          }
+        }
+        uint32_t uu = r + lo < n ? r + lo : n - 1u;
         // more than 32 rows (empty ones) end inside this chunk: walk on
-        while (u + 1u < n && off[u + 1] <= j) ++u;
-        v = ld_nc_u32(nb + j, pol);
-        if (v >= n) {
-          set_err(ctrl, kErrRange);
-          v = u;  // a self-loop: no effect
-        }
+        if (live[c])
+          while (uu + 1u < n && off[uu + 1] <= j) ++uu;
+        u[c] = uu;
+        // the next chunk starts in the row of this chunk's last entry
+        const int last = (int)((end - cb < 32u ? end - cb : 32u) - 1u);
+        r = __shfl_sync(0xFFFFFFFFu, uu, last);
       }
-      const uint32_t pu = live ? ldP(P + u) : 0u;
-      const uint32_t pv = live ? ldP(P + v) : 0u;
-      ring.push(S, live && pu != pv, fn.f(u), pu, fn.f(v), pv);
-      // the next chunk starts in the row of this chunk's last entry
-      const int last = (int)((end - base < 32u ? end - base : 32u) - 1u);
-      r = __shfl_sync(0xFFFFFFFFu, u, last);
+      uint32_t pu[K], pv[K];
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        if (live[c] && v[c] >= n) {
+          set_err(ctrl, kErrRange);
+          v[c] = u[c];  // a self-loop: no effect
+        }
+        pu[c] = live[c] ? ldP(P + u[c]) : 0u;
+        pv[c] = live[c] ? ldP(P + v[c]) : 0u;
+      }
+#pragma unroll
+      for (int c = 0; c < K; ++c)
+        ring.push(S, live[c] && pu[c] != pv[c], fn.f(u[c]), pu[c], fn.f(v[c]), pv[c]);
     }
   }
   ring.drain(S);
