@@ -454,10 +454,11 @@ def request_roofline(cc, graphs, phase_ms, cache) -> dict:
 
 def bench_c1(cc, graphgen, torch, runs: int = 200) -> dict:
     """R-MAT scale 16 (2^20 edges) as its configuration states it: f = id,
-    min-id labels. A launch-bound size, so it is timed two ways: cc_run
-    launched per call, and the same call captured once in a CUDA graph and
-    replayed (cc_run enqueues only stream work, so it can be captured). Mean
-    over `runs` back-to-back runs after 10 warm-up runs, CUDA events."""
+    min-id labels. At this size host and launch costs are a fifth of a call,
+    so it is timed two ways: cc_run launched per call, and the same call
+    captured once in a CUDA graph and replayed (cc_run enqueues only stream
+    work, so it can be captured). Mean over `runs` back-to-back runs after 10
+    warm-up runs, CUDA events."""
     w = graphgen.WORKLOADS["rmat16_ef16"]
     n, E = w.n_vertices, w.n_edges
     e = w.device_edges()
