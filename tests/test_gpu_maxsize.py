@@ -95,3 +95,33 @@ def test_max_vertex_count_matches_the_oracle():
         assert int(L[v].item()) == v + 1
     del L, e_dev
     torch.cuda.empty_cache()
+
+
+def test_wide_histogram_without_a_hub():
+    """2^31 + 5 edges (i mod n, (i + 1) mod n) on n = 2^20 vertices: a cycle
+    wound 2048 times. No vertex stands out in the sample, so the certificate
+    finds no candidate and the exact selection falls back to the full
+    histogram, in 64-bit counters (2^31 edges or more). Closed form, pinned
+    against the oracle in tests/test_oracle_pins.py::test_wound_cycle_closed_form:
+    vertices 1 .. 4 have the largest degree, so m = 1; one component, min-id
+    label 0 (root value 0 under f = R)."""
+    n = 1 << 20
+    E = (1 << 31) + 5
+    e = torch.empty((E, 2), dtype=torch.int32, device="cuda")
+    step = 1 << 28
+    for a in range(0, E, step):
+        b = min(E, a + step)
+        i = torch.arange(a, b, dtype=torch.int64, device="cuda")
+        e[a:b, 0] = (i % n).to(torch.int32)
+        e[a:b, 1] = ((i + 1) % n).to(torch.int32)
+        del i
+    L = torch.empty(n, dtype=torch.int32, device="cuda")
+    for label_space in (cc.CC_LABEL_MIN_ID, cc.CC_LABEL_ROOT_VALUE):
+        with cc.Graph(n, label_space=label_space) as g:
+            g.run(e, L)
+            g.sync()
+            assert g.root_vertex() == 1
+            assert g.num_components() == 1
+            assert int(L.min().item()) == 0 and int(L.max().item()) == 0
+    del e, L
+    torch.cuda.empty_cache()

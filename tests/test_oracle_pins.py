@@ -182,6 +182,24 @@ def test_max_degree_vertex():
         assert oracle.max_degree_vertex(n, e) == int(np.flatnonzero(cnt == cnt.max())[0])
 
 
+def test_wound_cycle_closed_form():
+    """Edges (i mod n, (i + 1) mod n) for i < q n + r wind a cycle q times
+    and r edges more. Vertex v is a first endpoint q + [v < r] times and a
+    second endpoint q + [1 <= v <= r] times, so for 2 <= r < n the largest
+    degree 2q + 2 belongs to vertices 1 .. r - 1 and m = 1; one component,
+    min-id label 0. The GPU test of the 64-bit histogram (2^31 + 5 edges)
+    relies on this form."""
+    for n, q, r in ((64, 8, 5), (1000, 3, 2), (4096, 2, 4095)):
+        E = q * n + r
+        i = np.arange(E, dtype=np.int64)
+        e = np.stack([i % n, (i + 1) % n], axis=1).astype(np.uint32)
+        v = np.arange(n)
+        want = 2 * q + (v < r) + ((v >= 1) & (v <= r))
+        assert np.array_equal(np.bincount(e.ravel().astype(np.int64), minlength=n), want)
+        assert oracle.max_degree_vertex(n, e) == 1
+        assert (oracle.min_labels(n, e) == 0).all()
+
+
 def test_degree_add_chunked():
     """The streaming degree count (the maximum-degree vertex of Algorithm 4's
     max_degree() for inputs fed in chunks) against numpy's bincount of both
