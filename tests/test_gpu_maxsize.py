@@ -123,5 +123,18 @@ def test_wide_histogram_without_a_hub():
             assert g.root_vertex() == 1
             assert g.num_components() == 1
             assert int(L.min().item()) == 0 and int(L.max().item()) == 0
+    # the same edges from pinned host memory: the chunked selection of
+    # cc_run_host sees no hub in its first chunk and builds the full
+    # histogram, 64-bit, chunk by chunk
+    h = torch.empty((E, 2), dtype=torch.int32, pin_memory=True)
+    h.copy_(e)
     del e, L
+    torch.cuda.empty_cache()
+    Lh = torch.full((n,), -1, dtype=torch.int32, pin_memory=True)
+    with cc.Graph(n, E) as g:
+        cc.cc_run_host(g.h, h, E, Lh)
+        assert g.root_vertex() == 1
+        assert g.num_components() == 1
+        assert int(Lh.min().item()) == 0 and int(Lh.max().item()) == 0
+    del h, Lh
     torch.cuda.empty_cache()
