@@ -230,10 +230,12 @@ __global__ void __launch_bounds__(256) k_select_candidates(const uint32_t *__res
     const uint64_t i = base + (uint64_t)lane;
     bool have = i < count;
     uint64_t v = i;
-    if (kList && have) {
-      const uint32_t seg = (uint32_t)(i / seg_room), k = (uint32_t)(i % seg_room);
-      have = k < __ldcg(&cs->list_n[seg]);
-      v = have ? list[i] : 0u;
+    if constexpr (kList) {
+      if (have) {
+        const uint32_t seg = (uint32_t)(i / seg_room), k = (uint32_t)(i % seg_room);
+        have = k < __ldcg(&cs->list_n[seg]);
+        v = have ? list[i] : 0u;
+      }
     }
     const uint32_t c = have ? cnt[v] : 0u;
     if (c >= hot_thr && c != 0u)
